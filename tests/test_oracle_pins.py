@@ -1,0 +1,271 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each check is independent of the oracle's own code: closed forms, a brute-force enumeration, a
+second formula (pair-sum form of Eq. 1, exact rationals), a library routine (networkx), or a
+published test vector.  A dropped term, a wrong sign or a transposed index in the oracle fails
+at least one of them.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import (brute_force_max_q, canonical, cliques, dense_adjacency, q_exact, q_pairsum, random_graph,
+                     same_partition)
+
+
+# ---------------------------------------------------------------- counter hash (published vector)
+def test_splitmix64_published_vector():
+    # SplitMix64 seeded with 1234567: the first outputs of the reference C implementation.
+    assert gg.splitmix64_nth(1234567, 0) == 6457827717110365317
+    assert gg.splitmix64_nth(1234567, 1) == 3203168211198807973
+    assert gg.splitmix64_nth(1234567, 2) == 9817491932198370423
+
+
+def test_oracle_hash_matches_generator_hash():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        a, b, c = (int(x) for x in rng.integers(0, 2**63, size=3, dtype=np.int64))
+        assert oracle.hash3(a, b, c) == gg.hash3(a, b, c)
+
+
+# ---------------------------------------------------------------- Eq. 1 (modularity)
+@pytest.mark.parametrize("seed", range(6))
+def test_modularity_vs_pairsum_int(seed):
+    rng = np.random.default_rng(seed)
+    g = random_graph(11, 0.35, rng)
+    a = dense_adjacency(g)
+    for _ in range(20):
+        mem = rng.integers(0, 4, size=g.n).astype(np.int32)
+        q = oracle.modularity(g.offsets, g.targets, g.weights, mem)
+        exact = q_exact(a, mem)
+        assert q == float(exact)  # one correctly rounded division of exact integers
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_modularity_vs_pairsum_fp(seed):
+    rng = np.random.default_rng(100 + seed)
+    g = random_graph(12, 0.4, rng, weights="fp")
+    a = dense_adjacency(g)
+    for _ in range(10):
+        mem = rng.integers(0, 5, size=g.n).astype(np.int32)
+        assert oracle.modularity(g.offsets, g.targets, g.weights, mem) == pytest.approx(q_pairsum(a, mem), abs=1e-12)
+
+
+def test_modularity_vs_networkx():
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(7)
+    g = random_graph(30, 0.2, rng)
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    for i in range(g.n):
+        for e in range(g.offsets[i], g.offsets[i + 1]):
+            j = int(g.targets[e])
+            if i < j:
+                G.add_edge(i, j, weight=int(g.weights[e]))
+    for _ in range(10):
+        mem = rng.integers(0, 6, size=g.n).astype(np.int32)
+        comms = [set(np.flatnonzero(mem == c).tolist()) for c in np.unique(mem)]
+        ref = nx.algorithms.community.modularity(G, comms, weight="weight")
+        assert oracle.modularity(g.offsets, g.targets, g.weights, mem) == pytest.approx(ref, abs=1e-12)
+
+
+@pytest.mark.parametrize("k,s", [(2, 5), (3, 4), (7, 6), (10, 3)])
+def test_modularity_disjoint_cliques(k, s):
+    g = cliques(k, s)
+    mem = np.repeat(np.arange(k), s).astype(np.int32)
+    # Q = 1 - 1/k, i.e. the rational (k-1)/k, correctly rounded
+    assert oracle.modularity(g.offsets, g.targets, g.weights, mem) == (k - 1) / k
+
+
+@pytest.mark.parametrize("k,s", [(3, 4), (4, 5), (9, 3)])
+def test_modularity_ring_of_cliques(k, s):
+    g = cliques(k, s, ring=True)
+    mem = np.repeat(np.arange(k), s).astype(np.int32)
+    closed = Fraction(s * (s - 1), s * (s - 1) + 2) - Fraction(1, k)
+    assert oracle.modularity(g.offsets, g.targets, g.weights, mem) == float(closed)
+
+
+def test_modularity_singletons_closed_form():
+    rng = np.random.default_rng(3)
+    g = random_graph(15, 0.3, rng)
+    k = np.array([int(g.weights[g.offsets[i]:g.offsets[i + 1]].sum()) for i in range(g.n)])
+    two_m = int(k.sum())
+    q = oracle.modularity(g.offsets, g.targets, g.weights, np.arange(g.n, dtype=np.int32))
+    assert q == float(Fraction(-int((k * k).sum()), two_m * two_m))
+
+
+# ---------------------------------------------------------------- Eq. 2 (delta modularity)
+@pytest.mark.parametrize("seed,loops", [(0, False), (1, False), (2, True), (3, True)])
+def test_move_score_equals_exact_delta_q(seed, loops):
+    """2N/(2m)^2 equals Q(after) - Q(before) exactly for every single-vertex move."""
+    rng = np.random.default_rng(seed)
+    g = random_graph(9, 0.45, rng, self_loops=loops)
+    a = dense_adjacency(g)
+    two_m = int(a.sum())
+    for _ in range(4):
+        mem = rng.integers(0, 4, size=g.n).astype(np.int32)
+        q0 = q_exact(a, mem)
+        for i in range(g.n):
+            for c in range(g.n):
+                if c == mem[i]:
+                    continue
+                nscore = oracle.move_score(g.offsets, g.targets, g.weights, mem, i, c)
+                m2 = mem.copy()
+                m2[i] = c
+                assert Fraction(2 * nscore, two_m * two_m) == q_exact(a, m2) - q0
+
+
+# ---------------------------------------------------------------- colouring (deterministic schedule)
+def _greedy_reference(g, seed, pass_index):
+    order = sorted(range(g.n), key=lambda v: (gg.hash3(seed, pass_index, v), v), reverse=True)
+    col = [-1] * g.n
+    for v in order:
+        used = {col[int(u)] for u in g.targets[g.offsets[v]:g.offsets[v + 1]] if u != v and col[int(u)] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[v] = c
+    return np.array(col, dtype=np.int32)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_colouring_is_proper_and_greedy(seed):
+    rng = np.random.default_rng(seed)
+    g = random_graph(40, 0.15, rng, self_loops=True)
+    col, nc = oracle.colour(g.offsets, g.targets, seed=11 + seed, pass_index=seed)
+    for i in range(g.n):
+        for u in g.targets[g.offsets[i]:g.offsets[i + 1]]:
+            if u != i:
+                assert col[i] != col[u]
+    assert nc == col.max() + 1
+    assert np.array_equal(col, _greedy_reference(g, 11 + seed, seed))
+
+
+def test_colouring_complete_graph():
+    g = cliques(1, 9)
+    col, nc = oracle.colour(g.offsets, g.targets, 5, 0)
+    assert nc == 9 and sorted(col.tolist()) == list(range(9))
+
+
+# ---------------------------------------------------------------- Algorithm 3 (aggregation)
+@pytest.mark.parametrize("seed,fp", [(0, False), (1, False), (2, True)])
+def test_aggregate_vs_dense_scatter(seed, fp):
+    rng = np.random.default_rng(seed)
+    g = random_graph(25, 0.2, rng, weights="fp" if fp else "int", self_loops=True)
+    nc = 6
+    mem = rng.integers(0, nc, size=g.n).astype(np.int32)
+    mem[:nc] = np.arange(nc)  # every community occupied
+    oo, ot, ow = oracle.aggregate(g.offsets, g.targets, g.weights, mem, nc)
+    src = np.repeat(np.arange(g.n), np.diff(g.offsets))
+    ref = np.zeros((nc, nc), dtype=np.float64)
+    np.add.at(ref, (mem[src], mem[g.targets]), g.weights.astype(np.float64))
+    got = np.zeros((nc, nc), dtype=np.float64)
+    for c in range(nc):
+        row = ot[oo[c]:oo[c + 1]]
+        assert np.all(np.diff(row) > 0)  # sorted, unique
+        got[c, row] = ow[oo[c]:oo[c + 1]]
+    assert np.allclose(got, ref, rtol=0, atol=1e-9 if fp else 0)
+    assert np.count_nonzero(ref) == len(ot)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_aggregate_preserves_modularity_and_2m(seed):
+    rng = np.random.default_rng(seed)
+    g = random_graph(30, 0.2, rng, self_loops=(seed == 2))
+    mem = canonical(rng.integers(0, 7, size=g.n))
+    nc = int(mem.max()) + 1
+    oo, ot, ow = oracle.aggregate(g.offsets, g.targets, g.weights, mem, nc)
+    assert int(ow.sum()) == int(g.weights.sum())
+    q_orig = oracle.modularity(g.offsets, g.targets, g.weights, mem)
+    q_super = oracle.modularity(oo, ot, ow.astype(np.int32), np.arange(nc, dtype=np.int32))
+    assert q_super == q_orig
+    assert Fraction(q_orig) == Fraction(float(q_exact(dense_adjacency(g), mem)))
+
+
+# ---------------------------------------------------------------- Algorithms 1-2 (full method)
+def test_two_vertices_hand_traced():
+    g = gg.from_edges(2, [(0, 1)])
+    mem, q, passes, stats = oracle.louvain(g.offsets, g.targets, g.weights)
+    # pass 0: one vertex joins the other (N = 2m*1 - 1*1 = 1 > 0), second iteration converges
+    assert stats[0]["iterations"] == 2 and stats[0]["moves"] == 1
+    # pass 1: the single super-vertex has only its self-loop, so l_i = 1 and the passes stop
+    assert passes == 2 and stats[1]["iterations"] == 1
+    assert mem.tolist() == [0, 0] and q == 0.0
+
+
+def test_isolated_and_empty():
+    g = gg.from_edges(5, [])
+    mem, q, passes, _ = oracle.louvain(g.offsets, g.targets, g.weights)
+    assert mem.tolist() == [0, 1, 2, 3, 4] and q == 0.0 and passes == 1
+    g0 = gg.from_edges(0, [])
+    mem, q, passes, _ = oracle.louvain(g0.offsets, g0.targets, g0.weights)
+    assert len(mem) == 0 and q == 0.0
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_louvain_never_beats_brute_force(seed, schedule):
+    rng = np.random.default_rng(seed)
+    g = random_graph(8, 0.4, rng)
+    if g.n_arcs == 0:
+        pytest.skip("empty draw")
+    mem, q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params(schedule=schedule))
+    a = dense_adjacency(g)
+    assert q == pytest.approx(q_pairsum(a, mem), abs=1e-12)
+    assert q <= brute_force_max_q(a) + 1e-12
+
+
+def test_two_cliques_with_bridge_reach_optimum():
+    g = cliques(2, 5, ring=False)
+    g = gg.from_edges(10, [(i, j) for i in range(5) for j in range(i + 1, 5)] +
+                      [(5 + i, 5 + j) for i in range(5) for j in range(i + 1, 5)] + [(4, 5)])
+    mem, q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights)
+    assert same_partition(mem, [0] * 5 + [1] * 5)
+    assert q == pytest.approx(brute_force_max_q(dense_adjacency(g)), abs=1e-12)
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_ring_of_cliques_recovered(schedule):
+    k, s = 4, 5
+    g = cliques(k, s, ring=True)
+    mem, q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights,
+                                  oracle.default_params(schedule=schedule, max_passes=100))
+    assert same_partition(mem, np.repeat(np.arange(k), s))
+    assert q == float(Fraction(s * (s - 1), s * (s - 1) + 2) - Fraction(1, k))
+
+
+def test_planted_partition_sbm_10k():
+    g = gg.sbm(10000, 100, 0.1, 0.0005, 1)
+    planted = gg.planted_blocks(10000, 100)
+    q_planted = oracle.modularity(g.offsets, g.targets, g.weights, planted)
+    mem, q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params(max_passes=100))
+    assert q > q_planted - 0.005
+    # most vertices sit with the majority of their planted block
+    agree = 0
+    for b in range(100):
+        ids = mem[planted == b]
+        agree += np.bincount(ids).max()
+    assert agree / g.n > 0.97
+
+
+def test_fp_and_int_instantiations_agree_on_integral_weights():
+    rng = np.random.default_rng(5)
+    g = random_graph(60, 0.08, rng)
+    gf = gg.Graph(g.n, g.offsets, g.targets, g.weights.astype(np.float32))
+    for schedule in (0, 1):
+        p = oracle.default_params(schedule=schedule)
+        mi, qi, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, p)
+        mf, qf, _, _ = oracle.louvain(gf.offsets, gf.targets, gf.weights, p)
+        assert np.array_equal(mi, mf)
+        assert qi == pytest.approx(qf, abs=1e-12)
+
+
+def test_overflow_rejected():
+    g = gg.from_edges(2, [(0, 1)], [2**30])
+    with pytest.raises(OverflowError):
+        oracle.louvain(g.offsets, g.targets, g.weights)

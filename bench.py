@@ -1,0 +1,268 @@
+"""Benchmark: Louvain edges/s on one GB300 (R-MAT scale 22, edge factor 16, int32 weights 1..8).
+
+One step = one full louvain_run (all passes: local moving, renumbering, aggregation, compaction,
+final modularity) on the device-resident CSR.  value = arcs / step time (arcs counted both
+directions, as the paper's Table 2 does).  e2e = the same through louvain_run_host from pinned
+host buffers (CSR upload and membership download inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fast|deterministic]
+    python bench.py --impl reference      # the CPU oracle on a bounded sample (reference arm)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator kwargs, description)
+    "rmat22": (dict(kind="rmat", scale=22), "R-MAT scale 22, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+                                           "int32 weights 1..8, seed 22"),
+    "rmat20": (dict(kind="rmat", scale=20), "R-MAT scale 20, edge factor 16, int32 weights 1..8, seed 22"),
+    "rmat18": (dict(kind="rmat", scale=18), "R-MAT scale 18, edge factor 16, int32 weights 1..8, seed 22"),
+    "sbm10k": (dict(kind="sbm"), "planted-partition SBM, 10k vertices, 100 blocks, p_in 0.1, p_out 0.0005"),
+}
+CPU_SAMPLE = "rmat19"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def make_graph(name):
+    import graphgen as gg
+    if name.startswith("rmat"):
+        return gg.rmat(int(name[4:]), 16, 0.57, 0.19, 0.19, 22, gg.W_INT8)
+    if name == "sbm10k":
+        return gg.sbm(10000, 100, 0.1, 0.0005, 1)
+    raise KeyError(name)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                for line in out.stdout.strip().splitlines():
+                    self.samples.append([x.strip() for x in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                mx.append(float(s[2]))
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+def cpu_baseline(sample: str = CPU_SAMPLE, repeats: int = 1):
+    """The CPU oracle (single-threaded C++, as it stands) on a bounded sample of the workload."""
+    import oracle
+    g = make_graph(sample)
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params())
+    dt = (time.perf_counter() - t0) / repeats
+    return {"value": g.n_arcs / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample}: full deterministic Louvain on R-MAT scale {sample[4:]} "
+                      f"({g.n_arcs} arcs), {repeats} run(s), 1 of {os.cpu_count()} host cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    g = make_graph(CPU_SAMPLE)
+    oracle.build()
+    p = oracle.default_params()
+    for _ in range(args.warmup):
+        oracle.louvain(g.offsets, g.targets, g.weights, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.louvain(g.offsets, g.targets, g.weights, p)
+    dt = time.perf_counter() - t0
+    v = args.steps * g.n_arcs / dt
+    line = {"impl": "reference", "metric": "louvain_edges_per_second", "value": v, "unit": "edges/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"{CPU_SAMPLE} (bounded sample of {args.workload})", "mode": "deterministic"},
+            "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"R-MAT scale {CPU_SAMPLE[4:]} ({g.n_arcs} arcs), full Louvain per step"},
+            "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--mode", default="fast", choices=["fast", "deterministic"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_2312_04876_gb300 as lv
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    g = make_graph(args.workload)
+    offs = torch.from_numpy(g.offsets).to(dev)
+    tg = torch.from_numpy(g.targets).to(dev)
+    w = torch.from_numpy(g.weights).to(dev)
+    L = lv.Louvain(local)
+    params = lv.default_params(mode=args.mode, validate=0)
+    mem = torch.empty(g.n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
+        L.run(offs, tg, w, params, membership=mem)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    results = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, r = L.run(offs, tg, w, params, membership=mem)
+            results.append(r)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * args.steps * g.n_arcs / (ms / 1e3)
+    launches = sum(r.kernel_launches for r in results)
+    last = results[-1]
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        ho = torch.from_numpy(g.offsets).pin_memory()
+        ht = torch.from_numpy(g.targets).pin_memory()
+        hw = torch.from_numpy(g.weights).pin_memory()
+        hm = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        L.run_host(ho, ht, hw, params, membership=hm)
+        k2 = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            L.run_host(ho, ht, hw, params, membership=hm)
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * k2 * g.n_arcs / dt, "unit": "edges/s",
+               "h2d_bytes_per_step": int(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes),
+               "d2h_bytes_per_step": int(4 * g.n), "steps": k2}
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    s0 = last.stats[0] if last.stats else {}
+    roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
+            "peak_kind": peak_kind}
+    line = {
+        "metric": "louvain_edges_per_second", "value": value, "unit": "edges/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload][1], "n": g.n, "arcs": g.n_arcs, "mode": args.mode,
+                   "parallelism": "replicas" if ws > 1 else "single", "l2": "inputs larger than L2 "
+                   f"(CSR {(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes) / 1e9:.2f} GB vs 0.13 GB L2)"},
+        "modularity": last.modularity, "passes": last.passes, "iterations": last.total_iterations,
+        "communities": last.n_communities, "gpu_launches": launches,
+        "pass_ms": [{k: round(v, 3) if isinstance(v, float) else v for k, v in s.items()} for s in last.stats],
+        "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,180 @@
+/*
+ * louvain.h -- C ABI of the GB300 Louvain library (liblouvain.so).
+ *
+ * The library computes the Louvain method as GVE-Louvain (arXiv 2312.04876) describes it:
+ * passes of a local-moving phase (Algorithm 2, move score Eq. 2) and an aggregation phase
+ * (Algorithm 3), driven by the pass loop of Algorithm 1, with modularity by Eq. 1.  Every step
+ * runs in hand-written CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are symmetric weighted CSR (Section 3: both arcs of every undirected edge are
+ *     stored; a self-loop is stored once and counts once in K_i, sigma_c and 2m):
+ *       offsets  int64 [n + 1], offsets[0] = 0, non-decreasing, offsets[n] = n_arcs
+ *       targets  int32 [n_arcs], each in [0, n)
+ *       weights  int32 (> 0) or float32 (> 0, finite) [n_arcs], as `wtype` says
+ *     0 <= n < 2^31 - 1.  Duplicate arcs are summed.  Rows need not be sorted.
+ *   - Pointers named `d_*` are DEVICE pointers on the handle's device; `h_*` are host pointers.
+ *     The library never frees caller memory; inputs are read-only; outputs are written in place.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Device outputs are complete
+ *     when the call returns (the call synchronises the stream before returning).
+ *   - Every call returns a louvain_status and never aborts, traps or prints.  On failure the
+ *     handle keeps a message for louvain_last_error(); outputs are then unspecified.
+ *   - Integer mode (LOUVAIN_W_INT32) computes exactly in integers and requires
+ *     2m = sum of all arc weights < 2^31 (else LOUVAIN_ERR_OVERFLOW).  FP32 mode accumulates
+ *     the per-vertex community sums in fp32 and keeps K, Sigma, 2m and scores in fp64.
+ *   - A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef LOUVAIN_H
+#define LOUVAIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct louvain_handle_s* louvain_handle;
+
+typedef enum {
+  LOUVAIN_OK = 0,
+  LOUVAIN_ERR_INVALID = 1,   /* bad argument or malformed graph */
+  LOUVAIN_ERR_OOM = 2,       /* device/host allocation failed or HBM budget exceeded */
+  LOUVAIN_ERR_OVERFLOW = 3,  /* integer mode with 2m >= 2^31 */
+  LOUVAIN_ERR_TIMEOUT = 4,   /* a bounded device wait gave up */
+  LOUVAIN_ERR_CUDA = 5,      /* CUDA runtime error (message in louvain_last_error) */
+  LOUVAIN_ERR_BUSY = 6       /* resource in use (serving: no free slot / ticket not ready) */
+} louvain_status;
+
+typedef enum { LOUVAIN_W_INT32 = 0, LOUVAIN_W_FP32 = 1 } louvain_wtype;
+
+typedef enum {
+  /* Colour-synchronous schedule: per pass a Jones-Plassmann colouring with priorities
+   * hash(seed, pass, v); within a colour class every flagged vertex decides against the
+   * class-start community totals, then all moves apply.  Integer mode is bit-exact and
+   * run-to-run identical (the colouring-based ordering cited in Section 2). */
+  LOUVAIN_MODE_DETERMINISTIC = 0,
+  /* Asynchronous: vertices read and update live state with atomics (Section 4.1,
+   * "asynchronous version"), with a singleton-swap guard against the GPU community-swap
+   * pattern noted in Section 2.  Not reproducible run to run. */
+  LOUVAIN_MODE_FAST = 1
+} louvain_mode;
+
+typedef struct {
+  int32_t max_passes;            /* MAX_PASSES of Algorithm 1; unstated in the paper, default 10 */
+  int32_t max_iterations;        /* MAX_ITERATIONS of Algorithm 2; Section 4.1.2: 20 */
+  double tolerance;              /* initial per-iteration tolerance tau; Section 4.1.4: 0.01 */
+  double tolerance_drop;         /* threshold scaling divisor; Section 4.1.3: 10 */
+  double aggregation_tolerance;  /* tau_agg; Section 4.1.5: 0.8 (stop when |Gamma|/|V'| > tau_agg) */
+  int32_t pruning;               /* vertex pruning (Section 4.1.6): 1 on (default), 0 off */
+  int32_t mode;                  /* louvain_mode */
+  uint64_t seed;                 /* colouring priority seed (deterministic mode) */
+  int32_t validate;              /* 1: check the CSR (offsets, ranges, weights, symmetry, 2m) */
+  int32_t compact;               /* 1: compact each super-vertex graph to dense CSR (default);
+                                    0: run later passes on the holey CSR with degrees */
+  int32_t pass_modularity;       /* 1: fill louvain_pass_stats.modularity (extra arc sweep) */
+  int32_t reserved;
+} louvain_params;
+
+typedef struct {
+  int32_t pass;
+  int32_t iterations;            /* l_i of the pass */
+  int64_t moves;                 /* vertex moves performed in the pass */
+  int64_t n_vertices;            /* |V'| at the start of the pass */
+  int64_t n_arcs;                /* arcs of G' at the start of the pass */
+  int64_t n_communities;         /* |Gamma| after the local-moving phase */
+  double modularity;             /* Q after the local-moving phase (NaN unless pass_modularity) */
+  float ms_colour, ms_move, ms_aggregate, ms_other;
+} louvain_pass_stats;
+
+typedef struct {
+  double modularity;             /* Eq. 1 of the returned membership on the input graph */
+  int32_t passes;
+  int32_t total_iterations;
+  int64_t n_communities;
+  float ms_total;                /* device time of the whole run (CUDA events) */
+  int32_t kernel_launches;       /* kernels this call launched */
+  int32_t reserved;
+} louvain_result;
+
+/* Create a handle on CUDA device `device`.  hbm_budget_bytes caps the workspace the handle may
+ * allocate (0 = no cap).  Returns LOUVAIN_ERR_CUDA if the device is unusable. */
+louvain_status louvain_create(louvain_handle* h, int device, size_t hbm_budget_bytes);
+
+/* Release the handle's workspace and events.  NULL is a no-op. */
+void louvain_destroy(louvain_handle h);
+
+/* Defaults from Section 4.1: max_iterations 20, tolerance 0.01, tolerance_drop 10,
+ * aggregation_tolerance 0.8, pruning on; max_passes 10; deterministic mode; seed 0;
+ * validate 1; compact 1; pass_modularity 0. */
+louvain_status louvain_default_params(louvain_params* p);
+
+/* Message of the last failure on this handle ("" if none).  Valid until the next call. */
+const char* louvain_last_error(louvain_handle h);
+
+/* Static name of a status code. */
+const char* louvain_status_string(louvain_status s);
+
+/* Algorithm 1 on a device-resident CSR.  Writes d_membership[n] (device, caller-owned) with the
+ * community of every vertex, renumbered densely in order of the smallest member id's community
+ * rank (id = rank of the community among occupied ids after the final dendrogram lookup).
+ * res (optional) receives modularity (Eq. 1 on the input graph), passes, totals, device time;
+ * stats (optional, host array of stats_cap) receives one entry per pass, *n_stats their count. */
+louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                           const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                           const louvain_params* p, void* stream, int32_t* d_membership,
+                           louvain_result* res, louvain_pass_stats* stats, int32_t stats_cap,
+                           int32_t* n_stats);
+
+/* louvain_run for HOST buffers: copies the CSR to the device (through the handle's workspace),
+ * runs, and copies the membership back to h_membership[n].  Pinned host memory gives the
+ * fastest copies; pageable memory works.  The copies are part of the call. */
+louvain_status louvain_run_host(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* h_offsets,
+                                const int32_t* h_targets, const void* h_weights, louvain_wtype wtype,
+                                const louvain_params* p, void* stream, int32_t* h_membership,
+                                louvain_result* res, louvain_pass_stats* stats, int32_t stats_cap,
+                                int32_t* n_stats);
+
+/* Eq. 1 (second form) of a membership on a CSR.  d_membership[n] ids must lie in [0, n).
+ * Integer mode: Q = (2m sum sigma_c - sum Sigma_c^2) / (2m)^2 from exact int64 sums, one
+ * division in double; FP32 mode: fp64 sums.  Q = 0 when 2m = 0.  Result in *q (host). */
+louvain_status louvain_modularity(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                  const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                  const int32_t* d_membership, void* stream, double* q);
+
+/* Jones-Plassmann colouring used by the deterministic schedule: colour(v) = smallest colour not
+ * taken by a neighbour u != v of higher priority, priority (hash3(seed, pass, v), v).  Equals
+ * greedy colouring in decreasing priority.  Writes d_colour[n], *n_colours (host). */
+louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                              const int32_t* d_targets, uint64_t seed, int32_t pass, void* stream,
+                              int32_t* d_colour, int32_t* n_colours);
+
+/* One local-moving phase (Algorithm 2) from singleton communities on a CSR, with the colouring
+ * of pass `pass` (deterministic mode) and tolerance `tau`.  Writes d_cprime[n] (community ids,
+ * not renumbered), *iterations (l_i) and *moves (host). */
+louvain_status louvain_local_move(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                  const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                  const louvain_params* p, int32_t pass, double tau, void* stream,
+                                  int32_t* d_cprime, int32_t* iterations, int64_t* moves);
+
+/* Algorithm 3: super-vertex graph of a dense membership d_membership[n] in [0, n_comm).
+ * Writes the compacted CSR: d_out_offsets[n_comm + 1], d_out_targets / d_out_weights (capacity
+ * n_arcs each; weights in the input's wtype: int32 sums in integer mode, fp32 sums in FP32
+ * mode) and *out_arcs (host).  Self-loops hold the intra-community weight.  Row order within a
+ * super-vertex is unspecified. */
+louvain_status louvain_aggregate(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                 const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                 const int32_t* d_membership, int64_t n_comm, void* stream,
+                                 int64_t* d_out_offsets, int32_t* d_out_targets, void* d_out_weights,
+                                 int64_t* out_arcs);
+
+/* Exclusive prefix sum (Algorithm 3's exclusiveScan) of d_in[count] int64 into d_out[count + 1]
+ * (d_out[count] = total); d_in == d_out is allowed.  *total (host, optional). */
+louvain_status louvain_exclusive_scan(louvain_handle h, const int64_t* d_in, int64_t* d_out, int64_t count,
+                                      void* stream, int64_t* total);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOUVAIN_H */

@@ -1,0 +1,206 @@
+"""GB300-native Louvain community detection (GVE-Louvain, arXiv 2312.04876).
+
+Python binding of liblouvain.so (include/louvain.h).  Every step of the method runs in the
+library's CUDA kernels; this module only marshals arguments.  PyTorch supplies device memory
+and streams.  If the library is missing the calls raise -- there is no CPU fallback.
+
+    import torch, paper_2312_04876_gb300 as lv
+    L = lv.Louvain(device=0)
+    membership, result, stats = L.run(offsets, targets, weights, mode="fast")
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+from . import _native
+from ._native import MODE_DETERMINISTIC, MODE_FAST, W_FP32, W_INT32, Params, PassStats, Result
+
+__all__ = ["Louvain", "LouvainError", "default_params", "MODE_DETERMINISTIC", "MODE_FAST"]
+
+
+class LouvainError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+def _status_name(s: int) -> str:
+    lib = _native.load()
+    return lib.louvain_status_string(s).decode()
+
+
+def default_params(**overrides) -> Params:
+    """Defaults of Section 4.1 (louvain_default_params); keyword overrides, mode by name allowed."""
+    lib = _native.load()
+    p = Params()
+    lib.louvain_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "mode" and isinstance(v, str):
+            v = {"deterministic": MODE_DETERMINISTIC, "fast": MODE_FAST}[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+@dataclass
+class RunResult:
+    modularity: float
+    passes: int
+    total_iterations: int
+    n_communities: int
+    ms_total: float
+    kernel_launches: int
+    stats: list = field(default_factory=list)
+
+
+def _wtype(t) -> int:
+    import torch
+    if t.dtype == torch.int32:
+        return W_INT32
+    if t.dtype == torch.float32:
+        return W_FP32
+    raise TypeError("weights must be int32 or float32")
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _stats_list(st, n) -> list:
+    return [dict(pass_=s.pass_, iterations=s.iterations, moves=s.moves, n_vertices=s.n_vertices, n_arcs=s.n_arcs,
+                 n_communities=s.n_communities, modularity=s.modularity, ms_colour=s.ms_colour, ms_move=s.ms_move,
+                 ms_aggregate=s.ms_aggregate, ms_other=s.ms_other) for s in st[:n]]
+
+
+class Louvain:
+    """A library handle on one CUDA device (owns the reusable workspace)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._lib = _native.load()
+        self._h = ctypes.c_void_p()
+        st = self._lib.louvain_create(ctypes.byref(self._h), device, hbm_budget_bytes)
+        if st != _native.OK:
+            raise LouvainError(st, f"louvain_create(device={device}) failed")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            self._lib.louvain_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != _native.OK:
+            raise LouvainError(st, self._lib.louvain_last_error(self._h).decode())
+
+    # ---------------------------------------------------------------- full method
+    def run(self, offsets, targets, weights, params: Params | None = None, membership=None, stream=None,
+            stats_cap: int = 64, **overrides):
+        """louvain_run on device tensors (int64 offsets, int32 targets, int32/float32 weights).
+        Returns (membership int32 tensor, RunResult)."""
+        import torch
+        p = params if params is not None else default_params(**overrides)
+        n = offsets.numel() - 1
+        if membership is None:
+            membership = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+        res = Result()
+        st = (PassStats * max(stats_cap, 1))()
+        nst = ctypes.c_int32(0)
+        rc = self._lib.louvain_run(self._h, n, targets.numel(), offsets.data_ptr(), targets.data_ptr(),
+                                   weights.data_ptr(), _wtype(weights), ctypes.byref(p), _stream_ptr(stream),
+                                   membership.data_ptr(), ctypes.byref(res), st, stats_cap, ctypes.byref(nst))
+        self._check(rc)
+        return membership, RunResult(res.modularity, res.passes, res.total_iterations, res.n_communities,
+                                     res.ms_total, res.kernel_launches, _stats_list(st, nst.value))
+
+    def run_host(self, offsets, targets, weights, params: Params | None = None, membership=None, stream=None,
+                 stats_cap: int = 64, **overrides):
+        """louvain_run_host on host arrays (numpy or CPU tensors; pinned memory is fastest)."""
+        import numpy as np
+        p = params if params is not None else default_params(**overrides)
+
+        def ptr(a):
+            return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+        n = (offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1
+        na = targets.numel() if hasattr(targets, "numel") else len(targets)
+        wdt = weights.dtype
+        fp = str(wdt) in ("torch.float32", "float32")
+        if membership is None:
+            membership = np.empty(max(n, 0), dtype=np.int32)
+        res = Result()
+        st = (PassStats * max(stats_cap, 1))()
+        nst = ctypes.c_int32(0)
+        rc = self._lib.louvain_run_host(self._h, n, na, ptr(offsets), ptr(targets), ptr(weights),
+                                        W_FP32 if fp else W_INT32, ctypes.byref(p), _stream_ptr(stream),
+                                        ptr(membership), ctypes.byref(res), st, stats_cap, ctypes.byref(nst))
+        self._check(rc)
+        return membership, RunResult(res.modularity, res.passes, res.total_iterations, res.n_communities,
+                                     res.ms_total, res.kernel_launches, _stats_list(st, nst.value))
+
+    # ---------------------------------------------------------------- steps
+    def modularity(self, offsets, targets, weights, membership, stream=None) -> float:
+        q = ctypes.c_double()
+        rc = self._lib.louvain_modularity(self._h, offsets.numel() - 1, targets.numel(), offsets.data_ptr(),
+                                          targets.data_ptr(), weights.data_ptr(), _wtype(weights),
+                                          membership.data_ptr(), _stream_ptr(stream), ctypes.byref(q))
+        self._check(rc)
+        return float(q.value)
+
+    def colour(self, offsets, targets, seed: int, pass_index: int, stream=None):
+        import torch
+        n = offsets.numel() - 1
+        col = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+        nc = ctypes.c_int32()
+        rc = self._lib.louvain_colour(self._h, n, targets.numel(), offsets.data_ptr(), targets.data_ptr(), seed,
+                                      pass_index, _stream_ptr(stream), col.data_ptr(), ctypes.byref(nc))
+        self._check(rc)
+        return col, int(nc.value)
+
+    def local_move(self, offsets, targets, weights, params: Params | None = None, pass_index: int = 0,
+                   tau: float | None = None, stream=None, **overrides):
+        import torch
+        p = params if params is not None else default_params(**overrides)
+        n = offsets.numel() - 1
+        cp = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+        it = ctypes.c_int32()
+        mv = ctypes.c_int64()
+        rc = self._lib.louvain_local_move(self._h, n, targets.numel(), offsets.data_ptr(), targets.data_ptr(),
+                                          weights.data_ptr(), _wtype(weights), ctypes.byref(p), pass_index,
+                                          p.tolerance if tau is None else tau, _stream_ptr(stream), cp.data_ptr(),
+                                          ctypes.byref(it), ctypes.byref(mv))
+        self._check(rc)
+        return cp, int(it.value), int(mv.value)
+
+    def aggregate(self, offsets, targets, weights, membership, n_comm: int, stream=None):
+        import torch
+        dev = offsets.device
+        oo = torch.empty(n_comm + 1, dtype=torch.int64, device=dev)
+        ot = torch.empty(max(targets.numel(), 1), dtype=torch.int32, device=dev)
+        ow = torch.empty(max(targets.numel(), 1), dtype=weights.dtype, device=dev)
+        na = ctypes.c_int64()
+        rc = self._lib.louvain_aggregate(self._h, offsets.numel() - 1, targets.numel(), offsets.data_ptr(),
+                                         targets.data_ptr(), weights.data_ptr(), _wtype(weights),
+                                         membership.data_ptr(), n_comm, _stream_ptr(stream), oo.data_ptr(),
+                                         ot.data_ptr(), ow.data_ptr(), ctypes.byref(na))
+        self._check(rc)
+        a = int(na.value)
+        return oo, ot[:a], ow[:a]
+
+    def exclusive_scan(self, values, stream=None):
+        import torch
+        out = torch.empty(values.numel() + 1, dtype=torch.int64, device=values.device)
+        tot = ctypes.c_int64()
+        rc = self._lib.louvain_exclusive_scan(self._h, values.data_ptr(), out.data_ptr(), values.numel(),
+                                              _stream_ptr(stream), ctypes.byref(tot))
+        self._check(rc)
+        return out, int(tot.value)

@@ -1,0 +1,75 @@
+"""ctypes declarations of include/louvain.h (liblouvain.so).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblouvain.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_OVERFLOW, ERR_TIMEOUT, ERR_CUDA, ERR_BUSY = range(7)
+W_INT32, W_FP32 = 0, 1
+MODE_DETERMINISTIC, MODE_FAST = 0, 1
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("max_passes", ctypes.c_int32), ("max_iterations", ctypes.c_int32),
+                ("tolerance", ctypes.c_double), ("tolerance_drop", ctypes.c_double),
+                ("aggregation_tolerance", ctypes.c_double), ("pruning", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("validate", ctypes.c_int32),
+                ("compact", ctypes.c_int32), ("pass_modularity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class PassStats(ctypes.Structure):
+    _fields_ = [("pass_", ctypes.c_int32), ("iterations", ctypes.c_int32), ("moves", ctypes.c_int64),
+                ("n_vertices", ctypes.c_int64), ("n_arcs", ctypes.c_int64), ("n_communities", ctypes.c_int64),
+                ("modularity", ctypes.c_double), ("ms_colour", ctypes.c_float), ("ms_move", ctypes.c_float),
+                ("ms_aggregate", ctypes.c_float), ("ms_other", ctypes.c_float)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("modularity", ctypes.c_double), ("passes", ctypes.c_int32), ("total_iterations", ctypes.c_int32),
+                ("n_communities", ctypes.c_int64), ("ms_total", ctypes.c_float),
+                ("kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_V = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+SIGNATURES = {
+    "louvain_create": (_I32, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_size_t]),
+    "louvain_destroy": (None, [_V]),
+    "louvain_default_params": (_I32, [ctypes.POINTER(Params)]),
+    "louvain_last_error": (ctypes.c_char_p, [_V]),
+    "louvain_status_string": (ctypes.c_char_p, [_I32]),
+    "louvain_run": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V, _V, ctypes.POINTER(Result),
+                           ctypes.POINTER(PassStats), _I32, ctypes.POINTER(_I32)]),
+    "louvain_run_host": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V, _V,
+                                ctypes.POINTER(Result), ctypes.POINTER(PassStats), _I32, ctypes.POINTER(_I32)]),
+    "louvain_modularity": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, _V, _V, ctypes.POINTER(ctypes.c_double)]),
+    "louvain_colour": (_I32, [_V, _I64, _I64, _V, _V, ctypes.c_uint64, _I32, _V, _V, ctypes.POINTER(_I32)]),
+    "louvain_local_move": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _I32, ctypes.c_double,
+                                  _V, _V, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
+    "louvain_aggregate": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, _V, _I64, _V, _V, _V, _V, ctypes.POINTER(_I64)]),
+    "louvain_exclusive_scan": (_I32, [_V, _V, _V, _I64, _V, ctypes.POINTER(_I64)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblouvain.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2312_04876_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,281 @@
+// aggregate.cu -- the aggregation phase of Algorithm 3 on the GPU.
+//
+//  1. community-vertex CSR: member counts and community total degrees by atomics, exclusive
+//     scans (host side), then an unordered scatter of the members (countCommunityVertices /
+//     exclusiveScan / "add edge (C'[i], i) atomically");
+//  2. super-vertex graph: the holey offsets are the scan of the community total degrees (an
+//     over-estimate of every super-degree, as the paper does); one group per community (G by
+//     total-degree bucket) streams the arcs of all members -- flattened so that G lanes always
+//     work on G arcs even when members have tiny rows -- and sums the arc weight per
+//     neighbouring community, its own included (scanCommunities with self = true), in an
+//     open-addressing table; the group then writes the (d, w) pairs at the start of its holey
+//     row and records the row end;
+//  3. compaction (optional): scan of the super-degrees, then a block-flat copy of the rows.
+#include "internal.cuh"
+
+namespace lv {
+
+__global__ void k_comm_count(const int32_t* Cp, const int64_t* rbeg, const int64_t* rend, int64_t n, int32_t* counts,
+                             int64_t* cdeg) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = Cp[i];
+    atomicAdd(&counts[c], 1);
+    const int64_t d = rend[i] - rbeg[i];
+    if (d) atomicAdd(reinterpret_cast<unsigned long long*>(&cdeg[c]), (unsigned long long)d);
+  }
+}
+void community_count(Ctx& c, const int32_t* Cp, const int64_t* rbeg, const int64_t* rend, int64_t n, int32_t* counts,
+                     int64_t* cdeg) {
+  if (n <= 0) return;
+  k_comm_count<<<grid_for(n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(Cp, rbeg, rend, n, counts, cdeg);
+  c.launches++;
+}
+
+__global__ void k_comm_fill(const int32_t* Cp, int64_t n, const int64_t* coff, int32_t* cursor, int32_t* cverts) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = Cp[i];
+    cverts[coff[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
+  }
+}
+void community_fill(Ctx& c, const int32_t* Cp, int64_t n, const int64_t* coff, int32_t* cursor, int32_t* cverts) {
+  if (n <= 0) return;
+  k_comm_fill<<<grid_for(n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(Cp, n, coff, cursor, cverts);
+  c.launches++;
+}
+
+// Owner of flat index f among W lanes holding inclusive prefix sums `incl` (non-decreasing):
+// the number of lanes whose prefix is <= f.  All W lanes of the (sub-)warp must call it.
+template <int W>
+__device__ __forceinline__ int flat_owner(int64_t incl, int64_t f, unsigned mask) {
+  int lo = 0;
+#pragma unroll
+  for (int step = W / 2; step >= 1; step >>= 1) {
+    const int64_t v = __shfl_sync(mask, incl, lo + step - 1, W);
+    if (v <= f) lo += step;
+  }
+  return lo;
+}
+
+// Inclusive scan over W lanes.
+template <int W>
+__device__ __forceinline__ int64_t lanes_incl_scan(int64_t x, unsigned mask) {
+  const int l = threadIdx.x & (W - 1);
+#pragma unroll
+  for (int o = 1; o < W; o <<= 1) {
+    const int64_t y = __shfl_up_sync(mask, x, o, W);
+    if (l >= o) x += y;
+  }
+  return x;
+}
+
+// Insert the arcs of members [k0, k1) of a community, W lanes flattening W members at a time.
+template <class M, int W>
+__device__ __forceinline__ bool merge_members(const MergeArgs<M>& a, int64_t k0, int64_t k1, int64_t kstride,
+                                              int32_t* tk, typename M::h_t* tv, unsigned size, int shift,
+                                              unsigned mask) {
+  typedef typename M::h_t H;
+  const int l = threadIdx.x & (W - 1);
+  bool ok = true;
+  for (int64_t kb = k0; kb < k1; kb += kstride) {
+    const int64_t k = kb + l;
+    int64_t b = 0, len = 0;
+    if (k < k1) {
+      const int32_t i = a.cverts[k];
+      b = a.g.rbeg[i];
+      len = a.g.rend[i] - b;
+    }
+    const int64_t incl = lanes_incl_scan<W>(len, mask);
+    const int64_t total = __shfl_sync(mask, incl, W - 1, W);
+    const int64_t excl = incl - len;
+    for (int64_t f0 = 0; f0 < total; f0 += W) {
+      const int64_t f = f0 + l;
+      const int o = flat_owner<W>(incl, f, mask);
+      const int64_t ob = __shfl_sync(mask, b, o, W);
+      const int64_t oe = __shfl_sync(mask, excl, o, W);
+      if (f < total) {
+        const int64_t e = ob + (f - oe);
+        ok &= tbl_add(tk, tv, size, shift, a.Cp[a.g.tg[e]], (H)a.g.w[e]);
+      }
+    }
+  }
+  return ok;
+}
+
+template <class M, int G, int LOG, bool GLOBAL>
+__global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int32_t* list, int64_t count,
+                                                       int32_t* gkeys, typename M::h_t* gvals, int64_t gslots,
+                                                       int glog) {
+  typedef typename M::h_t H;
+  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  constexpr int SL = GLOBAL ? 1 : (1 << LOG);
+  __shared__ int32_t skeys[GPB * SL];
+  __shared__ H svals[GPB * SL];
+  __shared__ unsigned long long s_cnt;
+  const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
+  const unsigned lane = Grp<G>::lane();
+  int32_t* tk;
+  H* tv;
+  if (GLOBAL) {
+    tk = gkeys + (int64_t)blockIdx.x * gslots;
+    tv = gvals + (int64_t)blockIdx.x * gslots;
+  } else {
+    for (int t = threadIdx.x; t < GPB * SL; t += kBlock) { skeys[t] = kEmpty; svals[t] = H(0); }
+    __syncthreads();
+    tk = skeys + gib * SL;
+    tv = svals + gib * SL;
+  }
+  for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
+    const int32_t c = list[idx];
+    const int64_t m0 = a.coff[c], m1 = a.coff[c + 1];
+    const int64_t D = a.cdeg[c];
+    const int lg = GLOBAL ? tbl_log2(D < a.nc ? D : a.nc, 6, glog) : tbl_log2(D, 1, LOG);
+    const unsigned size = 1u << lg;
+    const int shift = 32 - lg;
+    bool ok;
+    if (G <= 32) {
+      ok = merge_members<M, (G <= 32 ? G : 32)>(a, m0, m1, G, tk, tv, size, shift, Grp<G>::mask());
+    } else {
+      const int warp = threadIdx.x >> 5;
+      ok = merge_members<M, 32>(a, m0 + 32 * warp, m1, 32 * (G / 32), tk, tv, size, shift, 0xffffffffu);
+    }
+    if (!ok) atomicOr(&a.ctrl->error, kErrTableFull);
+    Grp<G>::sync();
+    // emit the (community, weight) pairs at the start of the holey row of c
+    const int64_t base = a.hoff[c];
+    if (G <= 32) {
+      const unsigned gm = Grp<G>::mask();
+      unsigned cnt = 0;
+      for (unsigned s0 = 0; s0 < size; s0 += G) {
+        const unsigned s = s0 + lane;
+        int32_t key = kEmpty;
+        H val = H(0);
+        if (s < size) { key = tk[s]; val = tv[s]; }
+        const bool occ = key != kEmpty;
+        const unsigned ball = __ballot_sync(gm, occ) & gm;
+        if (occ) {
+          const int64_t p = base + cnt + __popc(ball & lanemask_lt());
+          a.otg[p] = key;
+          a.ow[p] = (typename M::w_t)val;
+          tk[s] = kEmpty;
+          tv[s] = H(0);
+        }
+        cnt += __popc(ball);
+      }
+      if (lane == 0) a.hend[c] = base + cnt;
+    } else {
+      if (threadIdx.x == 0) s_cnt = 0;
+      __syncthreads();
+      for (unsigned s0 = 0; s0 < size; s0 += G) {
+        const unsigned s = s0 + threadIdx.x;
+        int32_t key = kEmpty;
+        H val = H(0);
+        if (s < size) { key = tk[s]; val = tv[s]; }
+        const bool occ = key != kEmpty;
+        const unsigned ball = __ballot_sync(0xffffffffu, occ);
+        unsigned long long wb = 0;
+        if ((threadIdx.x & 31) == 0 && ball) wb = atomicAdd(&s_cnt, (unsigned long long)__popc(ball));
+        wb = __shfl_sync(0xffffffffu, wb, 0);
+        if (occ) {
+          const int64_t p = base + (int64_t)wb + __popc(ball & lanemask_lt());
+          a.otg[p] = key;
+          a.ow[p] = (typename M::w_t)val;
+          tk[s] = kEmpty;
+          tv[s] = H(0);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) a.hend[c] = base + (int64_t)s_cnt;
+      __syncthreads();
+    }
+  }
+}
+
+template <class M, int G, int LOG, bool GLOBAL>
+static void launch_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt,
+                         int max_blocks) {
+  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  int glog = 0;
+  while (((int64_t)1 << glog) < gt.slots_per_block) glog++;
+  merge_kernel<M, G, LOG, GLOBAL><<<grid_for(count, GPB, max_blocks), kBlock, 0, c.s>>>(
+      a, list, count, gt.keys, reinterpret_cast<typename M::h_t*>(gt.vals), gt.slots_per_block, glog);
+  c.launches++;
+}
+
+template <class M>
+void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt) {
+  if (count <= 0) return;
+  const int cap = c.num_sms * 16;
+  switch (bucket) {
+    case 0: launch_merge<M, 4, 3, false>(c, a, list, count, gt, cap); break;
+    case 1: launch_merge<M, 8, 5, false>(c, a, list, count, gt, cap); break;
+    case 2: launch_merge<M, 32, 8, false>(c, a, list, count, gt, cap); break;
+    case 3: launch_merge<M, 256, 12, false>(c, a, list, count, gt, cap); break;
+    default: launch_merge<M, 256, 0, true>(c, a, list, count, gt, gt.blocks > 0 ? gt.blocks : 1); break;
+  }
+}
+
+// ---------------------------------------------------------------- compaction
+__global__ void k_row_len(int64_t n, const int64_t* hbeg, const int64_t* hend, int64_t* len) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    len[r] = hend[r] - hbeg[r];
+}
+void row_lengths(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, int64_t* len) {
+  if (n <= 0) return;
+  k_row_len<<<grid_for(n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(n, hbeg, hend, len);
+  c.launches++;
+}
+
+// A block copies the rows [r0, r0 + 256): the flat index space over their arcs is shared by all
+// threads (owner row by binary search over the block's prefix sums), so one long row does not
+// serialise on one warp.  Output positions are contiguous from doff[r0].
+template <class W>
+__global__ void __launch_bounds__(kBlock) k_compact(int64_t n, const int64_t* hbeg, const int64_t* hend,
+                                                    const int64_t* doff, const int32_t* itg, const W* iw,
+                                                    int32_t* otg, W* ow) {
+  __shared__ int64_t excl[kBlock + 1];
+  __shared__ int64_t sbeg[kBlock];
+  for (int64_t r0 = (int64_t)blockIdx.x * kBlock; r0 < n; r0 += (int64_t)gridDim.x * kBlock) {
+    const int64_t r = r0 + threadIdx.x;
+    int64_t len = 0, b = 0;
+    if (r < n) { b = hbeg[r]; len = hend[r] - b; }
+    sbeg[threadIdx.x] = b;
+    excl[threadIdx.x + 1] = len;
+    if (threadIdx.x == 0) excl[0] = 0;
+    __syncthreads();
+    for (int o = 1; o < kBlock; o <<= 1) {
+      int64_t v = threadIdx.x + 1 > (unsigned)o ? excl[threadIdx.x + 1 - o] : 0;
+      __syncthreads();
+      excl[threadIdx.x + 1] += v;
+      __syncthreads();
+    }
+    const int64_t total = excl[kBlock];
+    const int64_t dbase = doff[r0];
+    for (int64_t f = threadIdx.x; f < total; f += kBlock) {
+      int lo = 0, hi = kBlock - 1;  // last row with excl <= f
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (excl[mid] <= f) lo = mid; else hi = mid - 1;
+      }
+      const int64_t src = sbeg[lo] + (f - excl[lo]);
+      otg[dbase + f] = itg[src];
+      ow[dbase + f] = iw[src];
+    }
+    __syncthreads();
+  }
+}
+template <class W>
+void compact_rows(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, const int64_t* doff, const int32_t* itg,
+                  const W* iw, int32_t* otg, W* ow) {
+  if (n <= 0) return;
+  k_compact<W><<<grid_for(n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(n, hbeg, hend, doff, itg, iw, otg, ow);
+  c.launches++;
+}
+
+template void merge_bucket<IntMode>(Ctx&, int, const MergeArgs<IntMode>&, const int32_t*, int64_t, const GlobalTable&);
+template void merge_bucket<FpMode>(Ctx&, int, const MergeArgs<FpMode>&, const int32_t*, int64_t, const GlobalTable&);
+template void compact_rows<int32_t>(Ctx&, int64_t, const int64_t*, const int64_t*, const int64_t*, const int32_t*,
+                                    const int32_t*, int32_t*, int32_t*);
+template void compact_rows<float>(Ctx&, int64_t, const int64_t*, const int64_t*, const int64_t*, const int32_t*,
+                                  const float*, int32_t*, float*);
+
+}  // namespace lv

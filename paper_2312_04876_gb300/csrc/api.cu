@@ -1,0 +1,882 @@
+// api.cu -- the C ABI of liblouvain.so and the host side of Algorithm 1.
+//
+// The pass loop runs on the host and drives device kernels on the caller's stream; the local
+// moving iterations are enqueued in small batches and stop on a device-side convergence flag,
+// so the host only synchronises a few times per pass (bucket counts, community count, end of
+// the local-moving phase).  All scratch belongs to the handle, is allocated on first use and
+// reused (the paper's preallocated CSRs, Section 4.1.7-8): two arc buffers (a holey merge target
+// and a dense compaction target), two sets of row descriptors, and per-vertex state.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace lv;
+
+namespace {
+
+struct DevAlloc {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+};
+
+struct RowSet {
+  int64_t* hoff = nullptr;  // [n+1] holey offsets (scan of community total degree)
+  int64_t* hend = nullptr;  // [n]   holey row ends
+  int64_t* doff = nullptr;  // [n+1] dense offsets after compaction
+};
+
+struct Workspace {
+  int64_t n_cap = -1, a_cap = -1;
+  DevAlloc core;
+  // per vertex
+  void *K0 = nullptr, *K = nullptr, *Sig = nullptr, *tot = nullptr;  // 8-byte accumulators
+  int32_t *Cp = nullptr, *colour = nullptr, *csize = nullptr, *mv_from = nullptr, *mv_to = nullptr;
+  int32_t *perm = nullptr, *cperm = nullptr, *occ = nullptr, *counts = nullptr, *cursor = nullptr;
+  int32_t *cverts = nullptr, *jcnt = nullptr, *jl0 = nullptr, *jl1 = nullptr, *tmp_mem = nullptr;
+  uint8_t* flags = nullptr;
+  int64_t *newid = nullptr, *coff = nullptr, *cdeg = nullptr, *len = nullptr, *tile_tmp = nullptr;
+  RowSet rows[2];
+  // arcs
+  int32_t *tgA = nullptr, *tgB = nullptr;
+  void *wA = nullptr, *wB = nullptr;
+  Ctrl* ctrl = nullptr;
+  // lazily sized
+  DevAlloc keys_alloc;
+  int64_t key_cap = 0;
+  int64_t* keyoffs = nullptr;
+  int32_t* keycur = nullptr;
+  DevAlloc gt_alloc;
+  int64_t gt_slots_total = 0;
+  GlobalTable gt;
+  DevAlloc in_alloc;
+  int64_t in_n = -1, in_a = -1;
+  int64_t* in_offs = nullptr;
+  int32_t* in_tg = nullptr;
+  void* in_w = nullptr;
+  int32_t* in_mem = nullptr;
+};
+
+}  // namespace
+
+struct louvain_handle_s {
+  int device = 0;
+  int num_sms = 152;
+  size_t budget = 0;
+  std::string err;
+  Workspace ws;
+  unsigned long long* pin = nullptr;  // pinned host staging
+  size_t pin_bytes = 0;
+  std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+size_t total_bytes(const Workspace& ws) {
+  return ws.core.bytes + ws.keys_alloc.bytes + ws.gt_alloc.bytes + ws.in_alloc.bytes;
+}
+
+void free_all(DevAlloc& a) {
+  for (void* p : a.ptrs) cudaFree(p);
+  a.ptrs.clear();
+  a.bytes = 0;
+}
+
+louvain_status set_err(louvain_handle h, louvain_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+louvain_status cuda_err(louvain_handle h, cudaError_t e, const char* where) {
+  return set_err(h, LOUVAIN_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+bool dalloc(louvain_handle h, DevAlloc& a, T** p, int64_t count) {
+  size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (h->budget && total_bytes(h->ws) + bytes > h->budget) return false;
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  a.ptrs.push_back(q);
+  a.bytes += bytes;
+  *p = reinterpret_cast<T*>(q);
+  return true;
+}
+
+louvain_status ensure_pinned(louvain_handle h, size_t bytes) {
+  if (h->pin_bytes >= bytes) return LOUVAIN_OK;
+  if (h->pin) cudaFreeHost(h->pin);
+  h->pin = nullptr;
+  size_t nb = bytes < 65536 ? 65536 : bytes * 2;
+  if (cudaMallocHost(&h->pin, nb) != cudaSuccess) {
+    cudaGetLastError();
+    h->pin_bytes = 0;
+    return set_err(h, LOUVAIN_ERR_OOM, "pinned host allocation failed");
+  }
+  h->pin_bytes = nb;
+  return LOUVAIN_OK;
+}
+
+louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
+  Workspace& ws = h->ws;
+  if (ws.n_cap >= n && ws.a_cap >= a && ws.ctrl) return LOUVAIN_OK;
+  int64_t nc = n > ws.n_cap ? n : ws.n_cap;
+  int64_t ac = a > ws.a_cap ? a : ws.a_cap;
+  free_all(ws.core);
+  ws.n_cap = ws.a_cap = -1;
+  DevAlloc& d = ws.core;
+  const int64_t n1 = nc + 1;
+  bool ok = true;
+  ok = ok && dalloc(h, d, (long long**)&ws.K0, n1) && dalloc(h, d, (long long**)&ws.K, n1) &&
+       dalloc(h, d, (long long**)&ws.Sig, n1) && dalloc(h, d, (long long**)&ws.tot, n1);
+  ok = ok && dalloc(h, d, &ws.Cp, n1) && dalloc(h, d, &ws.colour, n1) && dalloc(h, d, &ws.csize, n1) &&
+       dalloc(h, d, &ws.mv_from, n1) && dalloc(h, d, &ws.mv_to, n1) && dalloc(h, d, &ws.perm, n1) &&
+       dalloc(h, d, &ws.cperm, n1) && dalloc(h, d, &ws.occ, n1) && dalloc(h, d, &ws.counts, n1) &&
+       dalloc(h, d, &ws.cursor, n1) && dalloc(h, d, &ws.cverts, n1) && dalloc(h, d, &ws.jcnt, n1) &&
+       dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.tmp_mem, n1);
+  ok = ok && dalloc(h, d, &ws.flags, n1);
+  ok = ok && dalloc(h, d, &ws.newid, n1 + 1) && dalloc(h, d, &ws.coff, n1 + 1) && dalloc(h, d, &ws.cdeg, n1 + 1) &&
+       dalloc(h, d, &ws.len, n1 + 1) &&
+       dalloc(h, d, &ws.tile_tmp, scan_tmp_elems((int64_t)kNumBuckets * n1 + 8) + 8);  // class sort scans 5 n keys
+  for (int r = 0; r < 2 && ok; r++)
+    ok = dalloc(h, d, &ws.rows[r].hoff, n1 + 1) && dalloc(h, d, &ws.rows[r].hend, n1) &&
+         dalloc(h, d, &ws.rows[r].doff, n1 + 1);
+  ok = ok && dalloc(h, d, &ws.tgA, ac) && dalloc(h, d, &ws.tgB, ac) && dalloc(h, d, (int32_t**)&ws.wA, ac) &&
+       dalloc(h, d, (int32_t**)&ws.wB, ac) && dalloc(h, d, &ws.ctrl, 1);
+  if (!ok) {
+    free_all(ws.core);
+    return set_err(h, LOUVAIN_ERR_OOM, "workspace allocation failed or exceeds the HBM budget");
+  }
+  ws.n_cap = nc;
+  ws.a_cap = ac;
+  return LOUVAIN_OK;
+}
+
+louvain_status ensure_keys(louvain_handle h, int64_t nkeys) {
+  Workspace& ws = h->ws;
+  if (ws.key_cap >= nkeys) return LOUVAIN_OK;
+  free_all(ws.keys_alloc);
+  ws.key_cap = 0;
+  int64_t cap = nkeys < 4096 ? 4096 : nkeys * 2;
+  if (!dalloc(h, ws.keys_alloc, &ws.keyoffs, cap + 1) || !dalloc(h, ws.keys_alloc, &ws.keycur, cap)) {
+    free_all(ws.keys_alloc);
+    return set_err(h, LOUVAIN_ERR_OOM, "key-offset allocation failed");
+  }
+  ws.key_cap = cap;
+  return ensure_pinned(h, (size_t)(cap + 1) * sizeof(int64_t) + 4096);
+}
+
+// Global-memory hash tables for the largest bucket: `slots` per block for up to `want_blocks`.
+louvain_status ensure_gtable(louvain_handle h, Ctx& c, int64_t max_distinct, int64_t want_blocks) {
+  Workspace& ws = h->ws;
+  int64_t slots = 64;
+  while (slots < 2 * max_distinct) slots <<= 1;
+  int64_t blocks = want_blocks < (int64_t)c.num_sms * 4 ? want_blocks : (int64_t)c.num_sms * 4;
+  const int64_t limit = ((int64_t)1 << 31) / 8;  // at most 2 GiB of table slots in total
+  if (blocks * slots > limit) blocks = limit / slots > 0 ? limit / slots : 1;
+  if (blocks < 1) blocks = 1;
+  if (slots * blocks > ws.gt_slots_total) {
+    free_all(ws.gt_alloc);
+    ws.gt_slots_total = 0;
+    int64_t total = slots * blocks;
+    int32_t* k = nullptr;
+    int32_t* v = nullptr;
+    if (!dalloc(h, ws.gt_alloc, &k, total) || !dalloc(h, ws.gt_alloc, &v, total)) {
+      free_all(ws.gt_alloc);
+      return set_err(h, LOUVAIN_ERR_OOM, "global hash-table allocation failed");
+    }
+    cudaMemsetAsync(k, 0xFF, (size_t)total * 4, c.s);
+    cudaMemsetAsync(v, 0, (size_t)total * 4, c.s);
+    ws.gt.keys = k;
+    ws.gt.vals = v;
+    ws.gt_slots_total = total;
+  }
+  ws.gt.slots_per_block = slots;
+  ws.gt.blocks = (int)blocks;
+  return LOUVAIN_OK;
+}
+
+louvain_status sync(louvain_handle h, Ctx& c, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(c.s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_err(h, e, where);
+  return LOUVAIN_OK;
+}
+
+// Reads `count` int64 from device into the pinned buffer (synchronising) and returns it.
+const int64_t* read_i64(louvain_handle h, Ctx& c, const int64_t* d, int64_t count, louvain_status* st,
+                        const char* where) {
+  *st = ensure_pinned(h, (size_t)count * sizeof(int64_t) + 4096);
+  if (*st != LOUVAIN_OK) return nullptr;
+  int64_t* p = reinterpret_cast<int64_t*>(h->pin) + 64;  // first 512 bytes reserved for Ctrl copies
+  cudaMemcpyAsync(p, d, (size_t)count * sizeof(int64_t), cudaMemcpyDeviceToHost, c.s);
+  *st = sync(h, c, where);
+  return *st == LOUVAIN_OK ? p : nullptr;
+}
+
+const Ctrl* read_ctrl(louvain_handle h, Ctx& c, louvain_status* st, const char* where) {
+  *st = ensure_pinned(h, 65536);
+  if (*st != LOUVAIN_OK) return nullptr;
+  cudaMemcpyAsync(h->pin, h->ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c.s);
+  *st = sync(h, c, where);
+  return *st == LOUVAIN_OK ? reinterpret_cast<const Ctrl*>(h->pin) : nullptr;
+}
+
+cudaEvent_t event_at(louvain_handle h, size_t k) {
+  while (h->events.size() <= k) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->events.push_back(e);
+  }
+  return h->events[k];
+}
+
+float elapsed(louvain_handle h, size_t a, size_t b) {
+  float ms = 0.f;
+  if (a < h->events.size() && b < h->events.size()) cudaEventElapsedTime(&ms, h->events[a], h->events[b]);
+  return ms;
+}
+
+bool valid_params(const louvain_params* p) {
+  return p && p->max_passes >= 0 && p->max_iterations >= 0 && p->tolerance >= 0.0 && p->tolerance_drop > 0.0 &&
+         p->aggregation_tolerance >= 0.0 && (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
+}
+
+// Full CSR validation on the device.  Returns OK / INVALID / OVERFLOW.
+louvain_status validate_graph(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, const int64_t* offs,
+                              const int32_t* tg, const void* w, bool fp) {
+  Ctrl* ctrl = h->ws.ctrl;
+  validate_reset(c, ctrl);
+  validate_offsets(c, n, n_arcs, offs, ctrl);
+  louvain_status st;
+  const Ctrl* hc = read_ctrl(h, c, &st, "validate offsets");
+  if (!hc) return st;
+  if (hc->cnt[0]) return set_err(h, LOUVAIN_ERR_INVALID, "offsets are not a monotone CSR offset array ending at n_arcs");
+  validate_arcs(c, n, offs, tg, w, fp, ctrl);
+  hc = read_ctrl(h, c, &st, "validate arcs");
+  if (!hc) return st;
+  if (hc->cnt[1]) return set_err(h, LOUVAIN_ERR_INVALID, "arc target outside [0, n)");
+  if (hc->cnt[2]) return set_err(h, LOUVAIN_ERR_INVALID, "arc weight not positive (or not finite)");
+  if (hc->cnt[3]) return set_err(h, LOUVAIN_ERR_INVALID, "graph is not symmetric (w_ij != w_ji)");
+  if (!fp && (unsigned long long)hc->acc_i[0] >= (1ULL << 31))
+    return set_err(h, LOUVAIN_ERR_OVERFLOW, "integer mode needs 2m < 2^31");
+  return LOUVAIN_OK;
+}
+
+// ------------------------------------------------------------------ Algorithm 1 on the device
+struct RunOut {
+  double q = 0.0;
+  int32_t passes = 0, total_iterations = 0;
+  int64_t n_communities = 0;
+};
+
+// Per-pass degree buckets of graph g into ws.perm with host offsets hb[kNumBuckets + 1].
+template <class W>
+louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, int64_t hb[kNumBuckets + 1],
+                              int64_t* max_deg) {
+  Workspace& ws = h->ws;
+  louvain_status st = ensure_keys(h, kNumBuckets);
+  if (st != LOUVAIN_OK) return st;
+  cudaMemsetAsync(&ws.ctrl->cnt[6], 0, sizeof(unsigned long long), c.s);
+  bucket_sort(c, 0, g.n, g.rbeg, g.rend, nullptr, nullptr, kNumBuckets, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
+              &ws.ctrl->cnt[6]);
+  const int64_t* p = read_i64(h, c, ws.keyoffs, kNumBuckets + 1, &st, "degree buckets");
+  if (!p) return st;
+  for (int b = 0; b <= kNumBuckets; b++) hb[b] = p[b];
+  const Ctrl* hc = read_ctrl(h, c, &st, "degree buckets");
+  if (!hc) return st;
+  *max_deg = (int64_t)hc->cnt[6];
+  return LOUVAIN_OK;
+}
+
+// One local-moving phase (Algorithm 2) on g from the state in ws (K, Sig, Cp, flags set).
+// Fills *li and *moves.  Deterministic mode colours g first.
+template <class M>
+louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const int64_t hb[],
+                                int64_t max_deg, const louvain_params& p, int32_t pass, double tau, int32_t* li,
+                                int64_t* moves, size_t ev_colour_done) {
+  Workspace& ws = h->ws;
+  PassState<M> st{reinterpret_cast<typename M::a_t*>(ws.K), reinterpret_cast<typename M::a_t*>(ws.Sig), ws.Cp,
+                  ws.flags, ws.csize, ws.mv_from, ws.mv_to, ws.ctrl};
+  const bool det = p.mode == LOUVAIN_MODE_DETERMINISTIC;
+  louvain_status s;
+  std::vector<int64_t> ho;  // class-bucket offsets (deterministic) or bucket offsets (fast)
+  int32_t ncol = 1;
+  if (det) {
+    GraphView<int32_t> gs{g.n, g.rbeg, g.rend, g.tg, nullptr};
+    JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1};
+    if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
+    cudaError_t ce;
+    ncol = jp_colour(c, gs, ws.perm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce);
+    if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
+    if (ncol < 0) return set_err(h, LOUVAIN_ERR_CUDA, "internal: colouring did not finish");
+    const int64_t nkeys = (int64_t)ncol * kNumBuckets;
+    if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
+    bucket_sort(c, 1, g.n, g.rbeg, g.rend, ws.colour, nullptr, nkeys, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
+                nullptr);
+    const int64_t* q = read_i64(h, c, ws.keyoffs, nkeys + 1, &s, "class buckets");
+    if (!q) return s;
+    ho.assign(q, q + nkeys + 1);
+  } else {
+    ho.assign(hb, hb + kNumBuckets + 1);
+  }
+  if (event_at(h, ev_colour_done)) cudaEventRecord(h->events[ev_colour_done], c.s);
+  // global tables for hubs
+  int64_t n_hub = 0;
+  for (int k = 0; k < ncol; k++) n_hub += ho[(size_t)k * kNumBuckets + 5] - ho[(size_t)k * kNumBuckets + 4];
+  if (n_hub > 0) {
+    if ((s = ensure_gtable(h, c, max_deg < g.n ? max_deg : g.n, n_hub)) != LOUVAIN_OK) return s;
+  }
+  move_setup(c, ws.ctrl, tau, p.max_iterations);
+  const bool pruning = p.pruning != 0;
+  int enq = 0;
+  const int batch = det ? 2 : 4;
+  while (true) {
+    for (int k = 0; k < batch && enq < p.max_iterations; k++, enq++) {
+      for (int cl = 0; cl < ncol; cl++) {
+        const size_t base = (size_t)cl * kNumBuckets;
+        for (int b = 0; b < kNumBuckets; b++) {
+          const int64_t cnt = ho[base + b + 1] - ho[base + b];
+          if (cnt > 0) move_bucket<M>(c, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
+        }
+        if (det) move_apply<M>(c, st, ws.perm + ho[base], ho[base + kNumBuckets] - ho[base]);
+      }
+      move_finish<M>(c, ws.ctrl);
+    }
+    const Ctrl* hc = read_ctrl(h, c, &s, "local move");
+    if (!hc) return s;
+    if (hc->error) return set_err(h, LOUVAIN_ERR_CUDA, "internal: hash table overflow in the local-moving phase");
+    if (hc->done || enq >= p.max_iterations) {
+      *li = hc->iterations;
+      *moves = (int64_t)hc->moves_pass;
+      return LOUVAIN_OK;
+    }
+  }
+}
+
+template <class M>
+louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, int64_t nc,
+                               RowSet& rs, int32_t* otg_holey, typename M::w_t* ow_holey) {
+  Workspace& ws = h->ws;
+  louvain_status s;
+  // community-vertex CSR (countCommunityVertices, exclusiveScan, atomic fill)
+  cudaMemsetAsync(ws.counts, 0, (size_t)nc * sizeof(int32_t), c.s);
+  cudaMemsetAsync(ws.cdeg, 0, (size_t)nc * sizeof(int64_t), c.s);
+  community_count(c, ws.Cp, g.rbeg, g.rend, g.n, ws.counts, ws.cdeg);
+  scan_exclusive_i32(c, ws.counts, ws.coff, nc, ws.tile_tmp);
+  cudaMemsetAsync(ws.cursor, 0, (size_t)nc * sizeof(int32_t), c.s);
+  community_fill(c, ws.Cp, g.n, ws.coff, ws.cursor, ws.cverts);
+  // holey offsets (communityTotalDegree, exclusiveScan)
+  scan_exclusive_i64(c, ws.cdeg, rs.hoff, nc, ws.tile_tmp);
+  cudaMemcpyAsync(rs.hend, rs.hoff, (size_t)nc * sizeof(int64_t), cudaMemcpyDeviceToDevice, c.s);
+  // communities by total-degree bucket
+  if ((s = ensure_keys(h, kNumBuckets)) != LOUVAIN_OK) return s;
+  cudaMemsetAsync(&ws.ctrl->cnt[6], 0, sizeof(unsigned long long), c.s);
+  bucket_sort(c, 2, nc, nullptr, nullptr, nullptr, ws.cdeg, kNumBuckets, ws.cperm, ws.keyoffs, ws.keycur, ws.tile_tmp,
+              &ws.ctrl->cnt[6]);
+  const int64_t* q = read_i64(h, c, ws.keyoffs, kNumBuckets + 1, &s, "community buckets");
+  if (!q) return s;
+  int64_t cb[kNumBuckets + 1];
+  for (int b = 0; b <= kNumBuckets; b++) cb[b] = q[b];
+  const Ctrl* hc = read_ctrl(h, c, &s, "community buckets");
+  if (!hc) return s;
+  const int64_t max_cdeg = (int64_t)hc->cnt[6];
+  if (cb[5] - cb[4] > 0)
+    if ((s = ensure_gtable(h, c, max_cdeg < nc ? max_cdeg : nc, cb[5] - cb[4])) != LOUVAIN_OK) return s;
+  MergeArgs<M> a;
+  a.g = g; a.Cp = ws.Cp; a.coff = ws.coff; a.cverts = ws.cverts; a.cdeg = ws.cdeg; a.hoff = rs.hoff; a.hend = rs.hend;
+  a.otg = otg_holey; a.ow = ow_holey; a.nc = nc; a.ctrl = ws.ctrl;
+  for (int b = 0; b < kNumBuckets; b++) merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.gt);
+  return LOUVAIN_OK;
+}
+
+template <class M>
+louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, const int64_t* offs, const int32_t* tg,
+                        const typename M::w_t* w, const louvain_params& p, int32_t* C, RunOut* out,
+                        louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats) {
+  typedef typename M::a_t A;
+  typedef typename M::w_t W;
+  Workspace& ws = h->ws;
+  louvain_status s;
+  if (n_stats) *n_stats = 0;
+  iota_i32(c, C, n);
+  GraphView<W> g0{n, offs, offs + 1, tg, w};
+  GraphView<W> g = g0;
+  PassState<M> st{reinterpret_cast<A*>(ws.K), reinterpret_cast<A*>(ws.Sig), ws.Cp, ws.flags, ws.csize, ws.mv_from,
+                  ws.mv_to, ws.ctrl};
+  cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), c.s);
+  double tau = p.tolerance;
+  bool pending = false;
+  int64_t g_arcs = n_arcs;
+  for (int32_t lp = 0; lp < p.max_passes; lp++) {
+    const size_t e0 = (size_t)lp * 6 + 1;
+    if (event_at(h, e0 + 5) == nullptr) return set_err(h, LOUVAIN_ERR_CUDA, "event creation failed");
+    cudaEventRecord(h->events[e0], c.s);
+    const int64_t n_cur = g.n;
+    // (a1) pass init: buckets, K' / Sigma' / C' / flags
+    int64_t hb[kNumBuckets + 1], max_deg = 0;
+    if ((s = degree_buckets(h, c, g, hb, &max_deg)) != LOUVAIN_OK) return s;
+    if (lp == 0) {
+      vertex_init<M>(c, st, n_cur, false);
+      row_sums<M>(c, g, ws.perm, hb, st.K, st.Sig, reinterpret_cast<A*>(ws.K0));
+      total_weight<M>(c, st.K, n_cur, ws.ctrl);
+      const Ctrl* hc = read_ctrl(h, c, &s, "pass init");
+      if (!hc) return s;
+      if (!M::is_fp && hc->two_m_i >= (1LL << 31))
+        return set_err(h, LOUVAIN_ERR_OVERFLOW, "integer mode needs 2m < 2^31");
+    } else {
+      vertex_init<M>(c, st, n_cur, true);
+    }
+    cudaEventRecord(h->events[e0 + 1], c.s);
+    // (a2-a5) local-moving phase
+    int32_t li = 0;
+    int64_t moves = 0;
+    if ((s = local_move_phase<M>(h, c, g, hb, max_deg, p, lp, tau, &li, &moves, e0 + 2)) != LOUVAIN_OK) return s;
+    cudaEventRecord(h->events[e0 + 3], c.s);
+    pending = true;
+    out->passes = lp + 1;
+    out->total_iterations += li;
+    // communities after the local-moving phase
+    mark_occupied(c, ws.Cp, n_cur, ws.occ, n_cur);
+    scan_exclusive_i32(c, ws.occ, ws.newid, n_cur, ws.tile_tmp);
+    const int64_t* q = read_i64(h, c, ws.newid + n_cur, 1, &s, "community count");
+    if (!q) return s;
+    const int64_t nc = q[0];
+    double pass_q = __builtin_nan("");
+    if (p.pass_modularity) {
+      modularity<M>(c, g, ws.Cp, reinterpret_cast<A*>(ws.tot), ws.ctrl);
+      const Ctrl* hc = read_ctrl(h, c, &s, "pass modularity");
+      if (!hc) return s;
+      pass_q = hc->q;
+    }
+    louvain_pass_stats* ps = (stats && lp < stats_cap) ? &stats[lp] : nullptr;
+    if (ps) {
+      ps->pass = lp; ps->iterations = li; ps->moves = moves; ps->n_vertices = n_cur; ps->n_arcs = g_arcs;
+      ps->n_communities = nc; ps->modularity = pass_q;
+      if (n_stats) *n_stats = lp + 1;
+    }
+    const bool stop = li <= 1 || (double)nc / (double)n_cur > p.aggregation_tolerance;
+    if (!stop) {
+      // (a6) renumber C', dendrogram lookup, K of the next pass = Sigma by new id
+      relabel(c, ws.Cp, n_cur, ws.newid);
+      dendrogram_lookup(c, C, n, ws.Cp);
+      pending = false;
+      gather_totals<A>(c, st.Sig, ws.occ, ws.newid, n_cur, st.K);
+      cudaEventRecord(h->events[e0 + 4], c.s);
+      // (a7-a9) aggregation
+      RowSet& rs = ws.rows[lp & 1];
+      int32_t* htg = ws.tgA;
+      W* hw = reinterpret_cast<W*>(ws.wA);
+      if (!p.compact && (lp & 1)) { htg = ws.tgB; hw = reinterpret_cast<W*>(ws.wB); }
+      if ((s = aggregate_phase<M>(h, c, g, nc, rs, htg, hw)) != LOUVAIN_OK) return s;
+      if (p.compact) {
+        row_lengths(c, nc, rs.hoff, rs.hend, ws.len);
+        scan_exclusive_i64(c, ws.len, rs.doff, nc, ws.tile_tmp);
+        compact_rows<W>(c, nc, rs.hoff, rs.hend, rs.doff, htg, hw, ws.tgB, reinterpret_cast<W*>(ws.wB));
+        g = GraphView<W>{nc, rs.doff, rs.doff + 1, ws.tgB, reinterpret_cast<W*>(ws.wB)};
+        const int64_t* t = read_i64(h, c, rs.doff + nc, 1, &s, "compaction");
+        if (!t) return s;
+        g_arcs = t[0];
+      } else {
+        g = GraphView<W>{nc, rs.hoff, rs.hend, htg, hw};
+        g_arcs = -1;
+      }
+      cudaEventRecord(h->events[e0 + 5], c.s);
+      tau /= p.tolerance_drop;
+    } else {
+      cudaEventRecord(h->events[e0 + 4], c.s);
+      cudaEventRecord(h->events[e0 + 5], c.s);
+    }
+    if (ps) {
+      // event times become available after the final synchronisation below
+      ps->ms_other = 0.f;
+    }
+    if (stop) break;
+  }
+  if (pending) dendrogram_lookup(c, C, n, ws.Cp);
+  // canonical ids: rank of each occupied community id
+  mark_occupied(c, C, n, ws.occ, g.n);
+  scan_exclusive_i32(c, ws.occ, ws.newid, g.n, ws.tile_tmp);
+  relabel(c, C, n, ws.newid);
+  // (a10) Eq. 1 on the input graph
+  modularity<M>(c, g0, C, reinterpret_cast<A*>(ws.tot), ws.ctrl);
+  const Ctrl* hc = read_ctrl(h, c, &s, "final modularity");
+  if (!hc) return s;
+  if (hc->error) return set_err(h, LOUVAIN_ERR_CUDA, "internal: hash table overflow");
+  out->q = hc->q;
+  const int64_t* q = read_i64(h, c, ws.newid + g.n, 1, &s, "final communities");
+  if (!q) return s;
+  out->n_communities = q[0];
+  if (stats) {
+    for (int32_t lp = 0; lp < out->passes && lp < stats_cap; lp++) {
+      const size_t e0 = (size_t)lp * 6 + 1;
+      stats[lp].ms_other = elapsed(h, e0, e0 + 1) + elapsed(h, e0 + 3, e0 + 4);
+      stats[lp].ms_colour = elapsed(h, e0 + 1, e0 + 2);
+      stats[lp].ms_move = elapsed(h, e0 + 2, e0 + 3);
+      stats[lp].ms_aggregate = elapsed(h, e0 + 4, e0 + 5);
+    }
+  }
+  return LOUVAIN_OK;
+}
+
+louvain_status begin_call(louvain_handle h) {
+  if (!h) return LOUVAIN_ERR_INVALID;
+  h->err.clear();
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_err(h, e, "cudaSetDevice");
+  return LOUVAIN_OK;
+}
+
+louvain_status check_graph_args(louvain_handle h, int64_t n, int64_t n_arcs, const void* offs, const void* tg,
+                                const void* w, louvain_wtype wt) {
+  if (n < 0 || n >= 0x7fffffffLL) return set_err(h, LOUVAIN_ERR_INVALID, "n must be in [0, 2^31 - 1)");
+  if (n_arcs < 0) return set_err(h, LOUVAIN_ERR_INVALID, "n_arcs must be >= 0");
+  if (!offs) return set_err(h, LOUVAIN_ERR_INVALID, "offsets pointer is NULL");
+  if (n_arcs > 0 && (!tg || !w)) return set_err(h, LOUVAIN_ERR_INVALID, "targets / weights pointer is NULL");
+  if (wt != LOUVAIN_W_INT32 && wt != LOUVAIN_W_FP32) return set_err(h, LOUVAIN_ERR_INVALID, "unknown weight type");
+  return LOUVAIN_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* louvain_status_string(louvain_status s) {
+  switch (s) {
+    case LOUVAIN_OK: return "LOUVAIN_OK";
+    case LOUVAIN_ERR_INVALID: return "LOUVAIN_ERR_INVALID";
+    case LOUVAIN_ERR_OOM: return "LOUVAIN_ERR_OOM";
+    case LOUVAIN_ERR_OVERFLOW: return "LOUVAIN_ERR_OVERFLOW";
+    case LOUVAIN_ERR_TIMEOUT: return "LOUVAIN_ERR_TIMEOUT";
+    case LOUVAIN_ERR_CUDA: return "LOUVAIN_ERR_CUDA";
+    case LOUVAIN_ERR_BUSY: return "LOUVAIN_ERR_BUSY";
+  }
+  return "LOUVAIN_UNKNOWN";
+}
+
+louvain_status louvain_default_params(louvain_params* p) {
+  if (!p) return LOUVAIN_ERR_INVALID;
+  std::memset(p, 0, sizeof(*p));
+  p->max_passes = 10;
+  p->max_iterations = 20;
+  p->tolerance = 1e-2;
+  p->tolerance_drop = 10.0;
+  p->aggregation_tolerance = 0.8;
+  p->pruning = 1;
+  p->mode = LOUVAIN_MODE_DETERMINISTIC;
+  p->seed = 0;
+  p->validate = 1;
+  p->compact = 1;
+  p->pass_modularity = 0;
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_create(louvain_handle* out, int device, size_t hbm_budget_bytes) {
+  if (!out) return LOUVAIN_ERR_INVALID;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return LOUVAIN_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return LOUVAIN_ERR_CUDA;
+  }
+  louvain_handle h = new (std::nothrow) louvain_handle_s();
+  if (!h) return LOUVAIN_ERR_OOM;
+  h->device = device;
+  h->budget = hbm_budget_bytes;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) h->num_sms = sms;
+  *out = h;
+  return LOUVAIN_OK;
+}
+
+void louvain_destroy(louvain_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  free_all(h->ws.core);
+  free_all(h->ws.keys_alloc);
+  free_all(h->ws.gt_alloc);
+  free_all(h->ws.in_alloc);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->pin) cudaFreeHost(h->pin);
+  delete h;
+}
+
+const char* louvain_last_error(louvain_handle h) { return h ? h->err.c_str() : "invalid handle"; }
+
+louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                           const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                           const louvain_params* p, void* stream, int32_t* d_membership, louvain_result* res,
+                           louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
+  if (!valid_params(p)) return set_err(h, LOUVAIN_ERR_INVALID, "invalid louvain_params");
+  if (n > 0 && !d_membership) return set_err(h, LOUVAIN_ERR_INVALID, "membership pointer is NULL");
+  if (stats_cap < 0) return set_err(h, LOUVAIN_ERR_INVALID, "stats_cap < 0");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  if (res) std::memset(res, 0, sizeof(*res));
+  if (n_stats) *n_stats = 0;
+  if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
+  if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
+  if (!event_at(h, 0)) return set_err(h, LOUVAIN_ERR_CUDA, "event creation failed");
+  cudaEventRecord(h->events[0], c.s);
+  const bool fp = wtype == LOUVAIN_W_FP32;
+  if (p->validate) {
+    if ((s = validate_graph(h, c, n, n_arcs, d_offsets, d_targets, d_weights, fp)) != LOUVAIN_OK) return s;
+  }
+  RunOut out;
+  if (n > 0) {
+    if (fp)
+      s = run_impl<FpMode>(h, c, n, n_arcs, d_offsets, d_targets, reinterpret_cast<const float*>(d_weights), *p,
+                           d_membership, &out, stats, stats_cap, n_stats);
+    else
+      s = run_impl<IntMode>(h, c, n, n_arcs, d_offsets, d_targets, reinterpret_cast<const int32_t*>(d_weights), *p,
+                            d_membership, &out, stats, stats_cap, n_stats);
+    if (s != LOUVAIN_OK) {
+      cudaStreamSynchronize(c.s);
+      cudaGetLastError();
+      return s;
+    }
+  }
+  size_t e_end = (size_t)(p->max_passes + 1) * 6 + 2;
+  if (!event_at(h, e_end)) return set_err(h, LOUVAIN_ERR_CUDA, "event creation failed");
+  cudaEventRecord(h->events[e_end], c.s);
+  if ((s = sync(h, c, "run end")) != LOUVAIN_OK) return s;
+  if (res) {
+    res->modularity = out.q;
+    res->passes = out.passes;
+    res->total_iterations = out.total_iterations;
+    res->n_communities = out.n_communities;
+    res->ms_total = elapsed(h, 0, e_end);
+    res->kernel_launches = (int32_t)c.launches;
+  }
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_run_host(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* h_offsets,
+                                const int32_t* h_targets, const void* h_weights, louvain_wtype wtype,
+                                const louvain_params* p, void* stream, int32_t* h_membership, louvain_result* res,
+                                louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if ((s = check_graph_args(h, n, n_arcs, h_offsets, h_targets, h_weights, wtype)) != LOUVAIN_OK) return s;
+  if (n > 0 && !h_membership) return set_err(h, LOUVAIN_ERR_INVALID, "membership pointer is NULL");
+  Workspace& ws = h->ws;
+  if (ws.in_n < n || ws.in_a < n_arcs) {
+    free_all(ws.in_alloc);
+    ws.in_n = ws.in_a = -1;
+    if (!dalloc(h, ws.in_alloc, &ws.in_offs, n + 1) || !dalloc(h, ws.in_alloc, &ws.in_tg, n_arcs) ||
+        !dalloc(h, ws.in_alloc, (int32_t**)&ws.in_w, n_arcs) || !dalloc(h, ws.in_alloc, &ws.in_mem, n)) {
+      free_all(ws.in_alloc);
+      return set_err(h, LOUVAIN_ERR_OOM, "input staging allocation failed");
+    }
+    ws.in_n = n;
+    ws.in_a = n_arcs;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaMemcpyAsync(ws.in_offs, h_offsets, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+  if (n_arcs > 0) {
+    cudaMemcpyAsync(ws.in_tg, h_targets, (size_t)n_arcs * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ws.in_w, h_weights, (size_t)n_arcs * 4, cudaMemcpyHostToDevice, st);
+  }
+  s = louvain_run(h, n, n_arcs, ws.in_offs, ws.in_tg, ws.in_w, wtype, p, stream, ws.in_mem, res, stats, stats_cap,
+                  n_stats);
+  if (s != LOUVAIN_OK) return s;
+  if (n > 0) cudaMemcpyAsync(h_membership, ws.in_mem, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_err(h, e, "run_host copy back");
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_modularity(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                  const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                  const int32_t* d_membership, void* stream, double* q) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
+  if (!q || (n > 0 && !d_membership)) return set_err(h, LOUVAIN_ERR_INVALID, "NULL output / membership");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  if ((s = ensure_workspace(h, n, 0)) != LOUVAIN_OK) return s;
+  const bool fp = wtype == LOUVAIN_W_FP32;
+  if ((s = validate_graph(h, c, n, n_arcs, d_offsets, d_targets, d_weights, fp)) != LOUVAIN_OK) return s;
+  validate_range(c, d_membership, n, n, h->ws.ctrl);
+  const Ctrl* hc = read_ctrl(h, c, &s, "membership range");
+  if (!hc) return s;
+  if (hc->cnt[5]) return set_err(h, LOUVAIN_ERR_INVALID, "membership id outside [0, n)");
+  if (fp) {
+    GraphView<float> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const float*>(d_weights)};
+    modularity<FpMode>(c, g, d_membership, reinterpret_cast<double*>(h->ws.tot), h->ws.ctrl);
+  } else {
+    GraphView<int32_t> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const int32_t*>(d_weights)};
+    modularity<IntMode>(c, g, d_membership, reinterpret_cast<long long*>(h->ws.tot), h->ws.ctrl);
+  }
+  hc = read_ctrl(h, c, &s, "modularity");
+  if (!hc) return s;
+  *q = hc->q;
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                              const int32_t* d_targets, uint64_t seed, int32_t pass, void* stream, int32_t* d_colour,
+                              int32_t* n_colours) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if (n < 0 || n >= 0x7fffffffLL || n_arcs < 0 || !d_offsets || (n_arcs > 0 && !d_targets) || !n_colours ||
+      (n > 0 && !d_colour))
+    return set_err(h, LOUVAIN_ERR_INVALID, "invalid arguments");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  if ((s = ensure_workspace(h, n, 0)) != LOUVAIN_OK) return s;
+  *n_colours = 0;
+  if (n == 0) return LOUVAIN_OK;
+  Ctrl* ctrl = h->ws.ctrl;
+  validate_reset(c, ctrl);
+  validate_offsets(c, n, n_arcs, d_offsets, ctrl);
+  const Ctrl* hc = read_ctrl(h, c, &s, "validate offsets");
+  if (!hc) return s;
+  if (hc->cnt[0]) return set_err(h, LOUVAIN_ERR_INVALID, "bad offsets");
+  validate_range(c, d_targets, n_arcs, n, ctrl);
+  hc = read_ctrl(h, c, &s, "validate targets");
+  if (!hc) return s;
+  if (hc->cnt[5]) return set_err(h, LOUVAIN_ERR_INVALID, "arc target outside [0, n)");
+  GraphView<int32_t> g{n, d_offsets, d_offsets + 1, d_targets, nullptr};
+  int64_t hb[kNumBuckets + 1], max_deg;
+  if ((s = degree_buckets(h, c, g, hb, &max_deg)) != LOUVAIN_OK) return s;
+  JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1};
+  cudaError_t ce;
+  int32_t nc = jp_colour(c, g, h->ws.perm, hb, seed, pass, d_colour, jb, ctrl, h->pin, &ce);
+  if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
+  if (nc < 0) return set_err(h, LOUVAIN_ERR_CUDA, "internal: colouring did not finish");
+  *n_colours = nc;
+  return sync(h, c, "colour end");
+}
+
+louvain_status louvain_local_move(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                  const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                  const louvain_params* p, int32_t pass, double tau, void* stream, int32_t* d_cprime,
+                                  int32_t* iterations, int64_t* moves) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
+  if (!valid_params(p) || !iterations || !moves || (n > 0 && !d_cprime) || tau < 0.0)
+    return set_err(h, LOUVAIN_ERR_INVALID, "invalid arguments");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
+  if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
+  const bool fp = wtype == LOUVAIN_W_FP32;
+  if ((s = validate_graph(h, c, n, n_arcs, d_offsets, d_targets, d_weights, fp)) != LOUVAIN_OK) return s;
+  *iterations = 0;
+  *moves = 0;
+  if (n == 0) return LOUVAIN_OK;
+  Workspace& ws = h->ws;
+  cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), c.s);
+  auto body = [&](auto mode_tag) -> louvain_status {
+    typedef decltype(mode_tag) M;
+    typedef typename M::a_t A;
+    typedef typename M::w_t W;
+    GraphView<W> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const W*>(d_weights)};
+    PassState<M> st{reinterpret_cast<A*>(ws.K), reinterpret_cast<A*>(ws.Sig), ws.Cp, ws.flags, ws.csize, ws.mv_from,
+                    ws.mv_to, ws.ctrl};
+    int64_t hb[kNumBuckets + 1], max_deg;
+    louvain_status r = degree_buckets(h, c, g, hb, &max_deg);
+    if (r != LOUVAIN_OK) return r;
+    vertex_init<M>(c, st, n, false);
+    row_sums<M>(c, g, ws.perm, hb, st.K, st.Sig, reinterpret_cast<A*>(ws.K0));
+    total_weight<M>(c, st.K, n, ws.ctrl);
+    if (!event_at(h, 3)) return set_err(h, LOUVAIN_ERR_CUDA, "event creation failed");
+    r = local_move_phase<M>(h, c, g, hb, max_deg, *p, pass, tau, iterations, moves, 3);
+    if (r != LOUVAIN_OK) return r;
+    cudaMemcpyAsync(d_cprime, ws.Cp, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.s);
+    return sync(h, c, "local move end");
+  };
+  return fp ? body(FpMode()) : body(IntMode());
+}
+
+louvain_status louvain_aggregate(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                 const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                 const int32_t* d_membership, int64_t n_comm, void* stream, int64_t* d_out_offsets,
+                                 int32_t* d_out_targets, void* d_out_weights, int64_t* out_arcs) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
+  if (n_comm < 0 || n_comm > n || !d_out_offsets || !out_arcs || (n > 0 && !d_membership) ||
+      (n_arcs > 0 && (!d_out_targets || !d_out_weights)))
+    return set_err(h, LOUVAIN_ERR_INVALID, "invalid arguments");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
+  const bool fp = wtype == LOUVAIN_W_FP32;
+  if ((s = validate_graph(h, c, n, n_arcs, d_offsets, d_targets, d_weights, fp)) != LOUVAIN_OK) return s;
+  Workspace& ws = h->ws;
+  validate_range(c, d_membership, n, n_comm, ws.ctrl);
+  const Ctrl* hc = read_ctrl(h, c, &s, "membership range");
+  if (!hc) return s;
+  if (hc->cnt[5]) return set_err(h, LOUVAIN_ERR_INVALID, "membership id outside [0, n_comm)");
+  *out_arcs = 0;
+  if (n_comm == 0) {
+    cudaMemsetAsync(d_out_offsets, 0, sizeof(int64_t), c.s);
+    return sync(h, c, "aggregate end");
+  }
+  cudaMemcpyAsync(ws.Cp, d_membership, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.s);
+  cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), c.s);
+  auto body = [&](auto mode_tag) -> louvain_status {
+    typedef decltype(mode_tag) M;
+    typedef typename M::w_t W;
+    GraphView<W> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const W*>(d_weights)};
+    RowSet& rs = ws.rows[0];
+    louvain_status r = aggregate_phase<M>(h, c, g, n_comm, rs, ws.tgA, reinterpret_cast<W*>(ws.wA));
+    if (r != LOUVAIN_OK) return r;
+    row_lengths(c, n_comm, rs.hoff, rs.hend, ws.len);
+    scan_exclusive_i64(c, ws.len, d_out_offsets, n_comm, ws.tile_tmp);
+    compact_rows<W>(c, n_comm, rs.hoff, rs.hend, d_out_offsets, ws.tgA, reinterpret_cast<W*>(ws.wA), d_out_targets,
+                    reinterpret_cast<W*>(d_out_weights));
+    const int64_t* t = read_i64(h, c, d_out_offsets + n_comm, 1, &r, "aggregate total");
+    if (!t) return r;
+    *out_arcs = t[0];
+    const Ctrl* cc = read_ctrl(h, c, &r, "aggregate end");
+    if (!cc) return r;
+    if (cc->error) return set_err(h, LOUVAIN_ERR_CUDA, "internal: hash table overflow in aggregation");
+    return LOUVAIN_OK;
+  };
+  return fp ? body(FpMode()) : body(IntMode());
+}
+
+louvain_status louvain_exclusive_scan(louvain_handle h, const int64_t* d_in, int64_t* d_out, int64_t count,
+                                      void* stream, int64_t* total) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if (count < 0 || !d_out || (count > 0 && !d_in)) return set_err(h, LOUVAIN_ERR_INVALID, "invalid arguments");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  if ((s = ensure_workspace(h, count, 0)) != LOUVAIN_OK) return s;
+  scan_exclusive_i64(c, d_in, d_out, count, h->ws.tile_tmp);
+  if (total) {
+    const int64_t* t = read_i64(h, c, d_out + count, 1, &s, "scan total");
+    if (!t) return s;
+    *total = t[0];
+  }
+  return sync(h, c, "scan end");
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// internal.cuh -- host-side launchers shared by the translation units of liblouvain.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lv {
+
+// Launch context: the stream, a kernel-launch counter, the SM count.
+struct Ctx {
+  cudaStream_t s = nullptr;
+  int64_t launches = 0;
+  int num_sms = 152;
+};
+
+inline int grid_for(int64_t work_items, int items_per_block, int cap) {
+  int64_t b = (work_items + items_per_block - 1) / items_per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// A graph as (row begin, row end) descriptors: a dense CSR passes rbeg = offsets,
+// rend = offsets + 1; a holey CSR passes its begin and end arrays.
+template <class W>
+struct GraphView {
+  int64_t n = 0;
+  const int64_t* rbeg = nullptr;
+  const int64_t* rend = nullptr;
+  const int32_t* tg = nullptr;
+  const W* w = nullptr;
+};
+
+// ---------------------------------------------------------------- prims.cu
+// Exclusive scan of in[0, n) into out[0, n) and out[n] = total; tile_tmp needs
+// scan_tmp_elems(n) int64 entries.  in == out allowed for int64 input.
+int64_t scan_tmp_elems(int64_t n);
+void scan_exclusive_i64(Ctx& c, const int64_t* in, int64_t* out, int64_t n, int64_t* tile_tmp);
+void scan_exclusive_i32(Ctx& c, const int32_t* in, int64_t* out, int64_t n, int64_t* tile_tmp);
+
+void fill_i32(Ctx& c, int32_t* p, int32_t v, int64_t n);
+void iota_i32(Ctx& c, int32_t* p, int64_t n);
+
+// Counting sort of vertex ids by key.  key_kind 0: degree bucket of (rend - rbeg); 1: colour *
+// kNumBuckets + degree bucket; 2: degree bucket of deg64[i].  Vertices with a negative key are
+// left out.  hist must hold nkeys + 1 int64; cursor nkeys int32.  Writes perm and offsets[nkeys+1]
+// (device).
+// max_deg (device, optional) receives the largest row length / deg64 value seen (atomicMax).
+void bucket_sort(Ctx& c, int key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
+                 const int64_t* deg64, int64_t nkeys, int32_t* perm, int64_t* offsets, int32_t* cursor,
+                 int64_t* tile_tmp, unsigned long long* max_deg);
+
+// Renumbering (rank among occupied ids): occ[0, n) zeroed then marked from ids[0, m).
+void mark_occupied(Ctx& c, const int32_t* ids, int64_t m, int32_t* occ, int64_t n);
+void relabel(Ctx& c, int32_t* ids, int64_t m, const int64_t* newid);
+void dendrogram_lookup(Ctx& c, int32_t* C, int64_t n0, const int32_t* Cp);
+// K_next[newid[c]] = Sig[c] for occupied c.
+template <class A>
+void gather_totals(Ctx& c, const A* sig, const int32_t* occ, const int64_t* newid, int64_t n_old, A* k_next);
+// Max of an int64 array into *out (device), out zeroed by the caller.
+void max_i64(Ctx& c, const int64_t* p, int64_t n, unsigned long long* out);
+
+// ---------------------------------------------------------------- move.cu
+template <class M>
+struct PassState {
+  typename M::a_t* K;
+  typename M::a_t* Sig;
+  int32_t* Cp;
+  uint8_t* flags;
+  int32_t* csize;
+  int32_t* mv_from;
+  int32_t* mv_to;
+  Ctrl* ctrl;
+};
+
+// Per-pass vertex state: Cp = id, flags = 1, csize = 1, mv_to = -1; Sig = K if from_k else 0 with K = 0.
+template <class M>
+void vertex_init(Ctx& c, const PassState<M>& st, int64_t n, bool from_k);
+// K[i] = Sig[i] = row weight sums for the vertices in the degree-bucketed lists; also K0.
+template <class M>
+void row_sums(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* perm, const int64_t* h_bucket_offs,
+              typename M::a_t* K, typename M::a_t* Sig, typename M::a_t* K0);
+// 2m = sum of K into ctrl.
+template <class M>
+void total_weight(Ctx& c, const typename M::a_t* K, int64_t n, Ctrl* ctrl);
+// Reset the iteration state of a local-moving phase.
+void move_setup(Ctx& c, Ctrl* ctrl, double tau, int max_iterations);
+
+struct GlobalTable {
+  int32_t* keys = nullptr;
+  void* vals = nullptr;
+  int64_t slots_per_block = 0;  // power of two
+  int blocks = 0;
+};
+
+// One bucket's decide (+ apply in fast mode) over list[0, count).
+template <class M>
+void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
+                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning);
+// Deterministic mode: Sigma updates of the moves decided in list[0, count).
+template <class M>
+void move_apply(Ctx& c, const PassState<M>& st, const int32_t* list, int64_t count);
+template <class M>
+void move_finish(Ctx& c, Ctrl* ctrl);
+
+// ---------------------------------------------------------------- colour.cu
+struct JpBuffers {
+  int32_t* cnt;     // [n] uncoloured higher-priority neighbours
+  int32_t* list0;   // [n] ready lists
+  int32_t* list1;
+};
+// Jones-Plassmann colouring of g (self-loops ignored).  Returns the number of colours.
+// Uses ctrl->cnt[0..4]; synchronises the stream a few times.
+int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g_struct, const int32_t* perm, const int64_t* h_bucket_offs,
+                  uint64_t seed, int32_t pass, int32_t* colour, const JpBuffers& jb, Ctrl* ctrl,
+                  unsigned long long* h_pinned, cudaError_t* err);
+
+// ---------------------------------------------------------------- aggregate.cu
+// counts[c] = members, cdeg[c] = sum of member degrees (both zeroed by the caller).
+void community_count(Ctx& c, const int32_t* Cp, const int64_t* rbeg, const int64_t* rend, int64_t n,
+                     int32_t* counts, int64_t* cdeg);
+// cverts[coff[c] + k] = k-th member (unordered); cursor zeroed by the caller.
+void community_fill(Ctx& c, const int32_t* Cp, int64_t n, const int64_t* coff, int32_t* cursor, int32_t* cverts);
+
+template <class M>
+struct MergeArgs {
+  GraphView<typename M::w_t> g;
+  const int32_t* Cp;
+  const int64_t* coff;
+  const int32_t* cverts;
+  const int64_t* cdeg;
+  const int64_t* hoff;
+  int64_t* hend;
+  int32_t* otg;
+  typename M::w_t* ow;
+  int64_t nc;
+  Ctrl* ctrl;
+};
+template <class M>
+void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt);
+
+// Dense copy of holey rows: out arcs at doff[r] for rows [0, n).
+template <class W>
+void compact_rows(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, const int64_t* doff,
+                  const int32_t* itg, const W* iw, int32_t* otg, W* ow);
+// len[r] = hend[r] - hbeg[r]
+void row_lengths(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, int64_t* len);
+
+// ---------------------------------------------------------------- modularity.cu
+// Q of membership C on dense CSR g; tot[n] scratch (zeroed inside); result in ctrl->q (and
+// acc slots).  Integer mode exact.
+template <class M>
+void modularity(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* C, typename M::a_t* tot, Ctrl* ctrl);
+
+// ---------------------------------------------------------------- validate.cu
+// ctrl->cnt[0..3] receive: bad offsets, bad targets, bad weights, asymmetry hash; ctrl->acc_f[0]
+// the weight total (double), ctrl->acc_i[0] the integer weight total (saturating).
+void validate_offsets(Ctx& c, int64_t n, int64_t n_arcs, const int64_t* offs, Ctrl* ctrl);
+void validate_arcs(Ctx& c, int64_t n, const int64_t* offs, const int32_t* tg, const void* w, bool fp, Ctrl* ctrl);
+// ctrl->cnt[5] += number of ids outside [0, hi).
+void validate_range(Ctx& c, const int32_t* ids, int64_t m, int64_t hi, Ctrl* ctrl);
+// zero ctrl->cnt[0..7], acc_i, acc_f
+void validate_reset(Ctx& c, Ctrl* ctrl);
+
+}  // namespace lv

@@ -1,0 +1,386 @@
+// move.cu -- the local-moving phase of Algorithm 2 on the GPU.
+//
+// One group of G threads handles one vertex i (G by degree bucket: 4, 8, 32 lanes or a whole
+// block).  The group streams i's arcs (scanCommunities with self = false), accumulates
+// K_i->c for every neighbouring community c != C'[i] in an open-addressing table (shared
+// memory, or a per-block slice of global memory for hubs) and K_i->d in registers, then scores
+// every candidate with the Eq. 2 numerator
+//     N(c) = 2m (K_i->c - K_i->d) - K_i (Sigma_c - Sigma_d + K_i)
+// (exact int64 for int32 weights), takes the best with ties to the smallest id and moves iff
+// N > 0.  Deterministic mode records the move and defers the Sigma update to move_apply (the
+// colour class decides against class-start totals); fast mode applies it at once with atomics.
+// A moved vertex re-marks its neighbours for processing (vertex pruning, Section 4.1.6).  The
+// sum of the performed N is accumulated exactly (128-bit) and move_finish applies the
+// per-iteration tolerance test of Algorithm 2 on the device, so iterations need no host sync.
+#include "internal.cuh"
+
+namespace lv {
+
+template <class M>
+struct LmArgs {
+  GraphView<typename M::w_t> g;
+  PassState<M> st;
+  const int32_t* list;
+  int64_t count;
+  int32_t* gkeys;
+  typename M::h_t* gvals;
+  int64_t gslots;
+  int glog;
+  int fast;
+  int pruning;
+};
+
+// Block-wide reduction of the per-thread move accumulators into the control block.
+template <bool FP>
+__device__ __forceinline__ void flush_move_acc(Ctrl* ctrl, unsigned long long lo, unsigned long long hi,
+                                               unsigned long long mv, double f, unsigned long long* s_lo,
+                                               unsigned long long* s_hi, unsigned long long* s_mv, double* s_f) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    unsigned long long hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    unsigned long long s = lo + lo2;
+    hi += hi2 + (s < lo ? 1ULL : 0ULL);
+    lo = s;
+    mv += __shfl_xor_sync(0xffffffffu, mv, o);
+    if (FP) f += __shfl_xor_sync(0xffffffffu, f, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    s_lo[threadIdx.x >> 5] = lo; s_hi[threadIdx.x >> 5] = hi; s_mv[threadIdx.x >> 5] = mv; s_f[threadIdx.x >> 5] = f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tl = 0, th = 0, tm = 0;
+    double tf = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      unsigned long long s = tl + s_lo[w];
+      th += s_hi[w] + (s < tl ? 1ULL : 0ULL);
+      tl = s;
+      tm += s_mv[w];
+      tf += s_f[w];
+    }
+    if (tm) {
+      atomicAdd(&ctrl->moves, tm);
+      if (FP) atomicAdd(&ctrl->sum_f, tf);
+      else atomic_add_u128(&ctrl->sum_lo, &ctrl->sum_hi, tl, th);
+    }
+  }
+}
+
+template <class M, int G, int LOG, bool GLOBAL>
+__global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
+  typedef typename M::h_t H;
+  typedef typename M::a_t A;
+  typedef typename M::s_t S;
+  Ctrl* ctrl = a.st.ctrl;
+  if (*(volatile int32_t*)&ctrl->done) return;
+  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  constexpr int SL = GLOBAL ? 1 : (1 << LOG);
+  __shared__ int32_t skeys[GPB * SL];
+  __shared__ H svals[GPB * SL];
+  __shared__ S red_s[32];
+  __shared__ int32_t red_c[32];
+  __shared__ H red_h[32];
+  __shared__ int32_t red_i[32];
+  __shared__ unsigned long long r_lo[32], r_hi[32], r_mv[32];
+  __shared__ double r_f[32];
+
+  const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
+  const unsigned lane = Grp<G>::lane();
+  int32_t* tk;
+  H* tv;
+  if (GLOBAL) {
+    tk = a.gkeys + (int64_t)blockIdx.x * a.gslots;
+    tv = a.gvals + (int64_t)blockIdx.x * a.gslots;
+  } else {
+    for (int t = threadIdx.x; t < GPB * SL; t += kBlock) { skeys[t] = kEmpty; svals[t] = H(0); }
+    __syncthreads();
+    tk = skeys + gib * SL;
+    tv = svals + gib * SL;
+  }
+  const A two_m = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
+  const int64_t n_cur = a.g.n;
+  unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
+  double acc_f = 0.0;
+
+  const int64_t ngroups = (int64_t)gridDim.x * GPB;
+  for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < a.count; idx += ngroups) {
+    const int32_t i = a.list[idx];
+    if (a.pruning) {
+      int f = 0;
+      if (lane == 0) {
+        f = a.st.flags[i];
+        if (f) a.st.flags[i] = 0;  // mark i as processed
+      }
+      f = group_bcast<G>(f, red_i);
+      if (!f) continue;
+    }
+    const int64_t beg = a.g.rbeg[i], end = a.g.rend[i];
+    const int64_t deg = end - beg;
+    const int32_t d = a.st.Cp[i];
+    int lg;
+    if (GLOBAL) lg = tbl_log2(deg < n_cur ? deg : n_cur, 6, a.glog);
+    else lg = tbl_log2(deg, 1, LOG);
+    const unsigned size = 1u << lg;
+    const int shift = 32 - lg;
+
+    // scanCommunities(i, self = false): K_i->c into the table, K_i->d in registers
+    H kid = H(0);
+    bool ok = true;
+    for (int64_t e = beg + lane; e < end; e += G) {
+      const int32_t j = a.g.tg[e];
+      if (j == i) continue;
+      const H wv = (H)a.g.w[e];
+      const int32_t cj = a.st.Cp[j];
+      if (cj == d) kid += wv;
+      else ok &= tbl_add(tk, tv, size, shift, cj, wv);
+    }
+    if (!ok) atomicOr(&ctrl->error, kErrTableFull);
+    Grp<G>::sync();
+    kid = group_sum<G>(kid, red_h);
+
+    // best community by the Eq. 2 numerator; the scan also clears the table
+    const A ki = a.st.K[i];
+    const A sd = a.st.Sig[d];
+    S best = M::lowest();
+    int32_t bc = 0x7fffffff;
+    for (unsigned s = lane; s < size; s += G) {
+      const int32_t c = tk[s];
+      if (c != kEmpty) {
+        const H v = tv[s];
+        tk[s] = kEmpty;
+        tv[s] = H(0);
+        const S sc = M::score(v, kid, ki, a.st.Sig[c], sd, two_m);
+        if (better(sc, c, best, bc)) { best = sc; bc = c; }
+      }
+    }
+    group_argmax<G>(best, bc, red_s, red_c);
+    Grp<G>::sync();
+
+    int mv = (bc != 0x7fffffff && best > S(0)) ? 1 : 0;
+    if (mv && a.fast) {
+      // singleton guard against lock-step swaps: a lone vertex joins another singleton
+      // community only if that community's id is smaller
+      int okm = 1;
+      if (lane == 0 && a.st.csize[d] == 1 && a.st.csize[bc] == 1 && bc > d) okm = 0;
+      mv = group_bcast<G>(okm, red_i);
+    }
+    if (mv) {
+      if (lane == 0) {
+        if (a.fast) {
+          atomic_add_a(&a.st.Sig[d], -ki);
+          atomic_add_a(&a.st.Sig[bc], ki);
+          atomicSub(&a.st.csize[d], 1);
+          atomicAdd(&a.st.csize[bc], 1);
+        } else {
+          a.st.mv_from[i] = d;
+          a.st.mv_to[i] = bc;
+        }
+        a.st.Cp[i] = bc;
+        if (M::is_fp) {
+          acc_f += (double)best;
+        } else {
+          const unsigned long long b = (unsigned long long)best;
+          acc_lo += b;
+          if (acc_lo < b) acc_hi++;
+        }
+        acc_mv++;
+      }
+      if (a.pruning)
+        for (int64_t e = beg + lane; e < end; e += G) {
+          const int32_t j = a.g.tg[e];
+          if (j != i) a.st.flags[j] = 1;  // mark neighbours as unprocessed
+        }
+    }
+  }
+  flush_move_acc<M::is_fp>(ctrl, acc_lo, acc_hi, acc_mv, acc_f, r_lo, r_hi, r_mv, r_f);
+}
+
+template <class M, int G, int LOG, bool GLOBAL>
+static void launch_lm(Ctx& c, const LmArgs<M>& a, int max_blocks) {
+  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  int grid = grid_for(a.count, GPB, max_blocks);
+  lm_kernel<M, G, LOG, GLOBAL><<<grid, kBlock, 0, c.s>>>(a);
+  c.launches++;
+}
+
+template <class M>
+void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
+                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning) {
+  if (count <= 0) return;
+  LmArgs<M> a;
+  a.g = g; a.st = st; a.list = list; a.count = count;
+  a.gkeys = gt.keys; a.gvals = reinterpret_cast<typename M::h_t*>(gt.vals); a.gslots = gt.slots_per_block;
+  a.glog = 0;
+  while (((int64_t)1 << a.glog) < gt.slots_per_block) a.glog++;
+  a.fast = fast ? 1 : 0;
+  a.pruning = pruning ? 1 : 0;
+  const int cap = c.num_sms * 16;
+  switch (bucket) {
+    case 0: launch_lm<M, 4, 3, false>(c, a, cap); break;
+    case 1: launch_lm<M, 8, 5, false>(c, a, cap); break;
+    case 2: launch_lm<M, 32, 8, false>(c, a, cap); break;
+    case 3: launch_lm<M, 256, 12, false>(c, a, cap); break;
+    default: launch_lm<M, 256, 0, true>(c, a, gt.blocks > 0 ? gt.blocks : 1); break;
+  }
+}
+
+// ---------------------------------------------------------------- deterministic apply
+template <class M>
+__global__ void lm_apply(PassState<M> st, const int32_t* list, int64_t count) {
+  if (*(volatile int32_t*)&st.ctrl->done) return;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = list[k];
+    const int32_t t = st.mv_to[i];
+    if (t >= 0) {
+      const typename M::a_t ki = st.K[i];
+      atomic_add_a(&st.Sig[st.mv_from[i]], -ki);
+      atomic_add_a(&st.Sig[t], ki);
+      st.mv_to[i] = -1;
+    }
+  }
+}
+template <class M>
+void move_apply(Ctx& c, const PassState<M>& st, const int32_t* list, int64_t count) {
+  if (count <= 0) return;
+  lm_apply<M><<<grid_for(count, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(st, list, count);
+  c.launches++;
+}
+
+// ---------------------------------------------------------------- iteration control
+// Algorithm 2's tolerance test on the device: converged iff 2 sum N <= tau (2m)^2, with the
+// 128-bit sum rounded once to double (integer mode) and the right side as tau * (t * t).
+template <bool FP>
+__global__ void lm_finish(Ctrl* c) {
+  if (c->done) return;
+  const int it = c->iterations + 1;
+  c->iterations = it;
+  bool conv;
+  if (FP) {
+    conv = __dmul_rn(2.0, c->sum_f) <= __dmul_rn(c->tau, __dmul_rn(c->two_m_f, c->two_m_f));
+  } else {
+    const unsigned long long hi = (c->sum_hi << 1) | (c->sum_lo >> 63), lo = c->sum_lo << 1;
+    const double lhs = u128_to_double_rn(hi, lo);
+    const double t = __ll2double_rn(c->two_m_i);
+    conv = lhs <= __dmul_rn(c->tau, __dmul_rn(t, t));
+  }
+  c->moves_pass += c->moves;
+  c->moves = 0;
+  c->sum_lo = 0;
+  c->sum_hi = 0;
+  c->sum_f = 0.0;
+  if (conv || it >= c->max_iterations) c->done = 1;
+}
+template <class M>
+void move_finish(Ctx& c, Ctrl* ctrl) {
+  lm_finish<M::is_fp><<<1, 1, 0, c.s>>>(ctrl);
+  c.launches++;
+}
+
+__global__ void k_move_setup(Ctrl* c, double tau, int max_iterations) {
+  c->done = max_iterations <= 0 ? 1 : 0;
+  c->iterations = 0;
+  c->max_iterations = max_iterations;
+  c->tau = tau;
+  c->sum_lo = 0;
+  c->sum_hi = 0;
+  c->sum_f = 0.0;
+  c->moves = 0;
+  c->moves_pass = 0;
+}
+void move_setup(Ctx& c, Ctrl* ctrl, double tau, int max_iterations) {
+  k_move_setup<<<1, 1, 0, c.s>>>(ctrl, tau, max_iterations);
+  c.launches++;
+}
+
+// ---------------------------------------------------------------- per-pass vertex state
+template <class M>
+__global__ void k_vertex_init(PassState<M> st, int64_t n, int from_k) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    st.Cp[i] = (int32_t)i;
+    st.flags[i] = 1;
+    st.csize[i] = 1;
+    st.mv_to[i] = -1;
+    if (from_k) {
+      st.Sig[i] = st.K[i];
+    } else {
+      st.K[i] = 0;
+      st.Sig[i] = 0;
+    }
+  }
+}
+template <class M>
+void vertex_init(Ctx& c, const PassState<M>& st, int64_t n, bool from_k) {
+  if (n <= 0) return;
+  k_vertex_init<M><<<grid_for(n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(st, n, from_k ? 1 : 0);
+  c.launches++;
+}
+
+// K_i = sum of row weights (self-loop once), one group per vertex.
+template <class M, int G>
+__global__ void __launch_bounds__(kBlock) k_row_sums(GraphView<typename M::w_t> g, const int32_t* list, int64_t count,
+                                                     typename M::a_t* K, typename M::a_t* Sig, typename M::a_t* K0) {
+  typedef typename M::a_t A;
+  __shared__ A red[32];
+  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
+  const unsigned lane = Grp<G>::lane();
+  for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
+    const int32_t i = list[idx];
+    A s = A(0);
+    for (int64_t e = g.rbeg[i] + lane; e < g.rend[i]; e += G) s += (A)g.w[e];
+    s = group_sum<G>(s, red);
+    if (lane == 0) { K[i] = s; Sig[i] = s; if (K0) K0[i] = s; }
+  }
+}
+template <class M>
+void row_sums(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* perm, const int64_t* hb,
+              typename M::a_t* K, typename M::a_t* Sig, typename M::a_t* K0) {
+  const int cap = c.num_sms * 16;
+  for (int b = 0; b < kNumBuckets; b++) {
+    int64_t cnt = hb[b + 1] - hb[b];
+    if (cnt <= 0) continue;
+    const int32_t* l = perm + hb[b];
+    switch (b) {
+      case 0: k_row_sums<M, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
+      case 1: k_row_sums<M, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
+      case 2: k_row_sums<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
+      default: k_row_sums<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
+    }
+    c.launches++;
+  }
+}
+
+template <class M>
+__global__ void k_total(const typename M::a_t* K, int64_t n, Ctrl* ctrl) {
+  typedef typename M::a_t A;
+  __shared__ A red[32];
+  A s = A(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) s += K[i];
+  s = group_sum<kBlock>(s, red);
+  if (threadIdx.x == 0) {
+    if (M::is_fp) atomicAdd(&ctrl->two_m_f, (double)s);
+    else atomic_add_a(&ctrl->two_m_i, (long long)s);
+  }
+}
+template <class M>
+void total_weight(Ctx& c, const typename M::a_t* K, int64_t n, Ctrl* ctrl) {
+  if (n <= 0) return;
+  k_total<M><<<grid_for(n, kBlock * 8, c.num_sms * 4), kBlock, 0, c.s>>>(K, n, ctrl);
+  c.launches++;
+}
+
+#define LV_MOVE_INST(M)                                                                                           \
+  template void vertex_init<M>(Ctx&, const PassState<M>&, int64_t, bool);                                        \
+  template void row_sums<M>(Ctx&, const GraphView<M::w_t>&, const int32_t*, const int64_t*, M::a_t*, M::a_t*,    \
+                            M::a_t*);                                                                            \
+  template void total_weight<M>(Ctx&, const M::a_t*, int64_t, Ctrl*);                                            \
+  template void move_bucket<M>(Ctx&, int, const GraphView<M::w_t>&, const PassState<M>&, const int32_t*, int64_t, \
+                               const GlobalTable&, bool, bool);                                                  \
+  template void move_apply<M>(Ctx&, const PassState<M>&, const int32_t*, int64_t);                               \
+  template void move_finish<M>(Ctx&, Ctrl*);
+LV_MOVE_INST(IntMode)
+LV_MOVE_INST(FpMode)
+
+}  // namespace lv

@@ -1,0 +1,69 @@
+"""The C ABI library builds, loads and exports every entry point include/louvain.h declares
+(no GPU needed; no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "louvain.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(louvain_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2312_04876_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("louvain_create", "louvain_run", "louvain_run_host", "louvain_modularity", "louvain_destroy",
+                 "louvain_default_params", "louvain_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2312_04876_gb300 import _native
+    assert set(_declared()) == set(_native.SIGNATURES)
+
+
+def test_default_params_are_the_papers():
+    from paper_2312_04876_gb300 import default_params
+    p = default_params()
+    assert (p.max_iterations, p.tolerance, p.tolerance_drop, p.aggregation_tolerance, p.pruning) == (20, 0.01, 10.0,
+                                                                                                      0.8, 1)
+    assert p.max_passes == 10 and p.mode == 0 and p.validate == 1 and p.compact == 1
+
+
+def test_status_strings(lib):
+    lib.louvain_status_string.restype = ctypes.c_char_p
+    assert lib.louvain_status_string(0) == b"LOUVAIN_OK"
+    assert lib.louvain_status_string(3) == b"LOUVAIN_ERR_OVERFLOW"
+
+
+def test_create_without_gpu_returns_status(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    h = ctypes.c_void_p()
+    lib.louvain_create.restype = ctypes.c_int32
+    rc = lib.louvain_create(ctypes.byref(h), 0, ctypes.c_size_t(0))
+    assert rc == 5 and not h.value  # LOUVAIN_ERR_CUDA, no handle
+
+
+def test_null_handle_is_rejected(lib):
+    lib.louvain_run.restype = ctypes.c_int32
+    rc = lib.louvain_run(None, 0, 0, None, None, None, 0, None, None, None, None, None, 0, None)
+    assert rc == 1

@@ -1,0 +1,242 @@
+"""GPU parity: every step of the CUDA path through the C ABI against the CPU oracle.
+
+Integer weights: bit-exact (memberships, colours, super-graphs) and modularity equal to 1e-12.
+FP32 weights: the kernels sum per-vertex community weights in fp32 while the oracle works in
+fp64, so modularity must agree to 1e-4 (same-membership evaluation to 1e-10).
+Fast (asynchronous) mode is not reproducible: checked by validity and |Q - Q_oracle| <= 0.005.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import canonical, cliques, random_graph
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L(cuda_ok):
+    import paper_2312_04876_gb300 as lv
+    h = lv.Louvain(0)
+    yield h
+    h.close()
+
+
+def dev(g):
+    d = torch.device("cuda:0")
+    return (torch.from_numpy(g.offsets).to(d), torch.from_numpy(g.targets).to(d), torch.from_numpy(g.weights).to(d))
+
+
+GRAPHS = {
+    "sbm2k": lambda: gg.sbm(2000, 20, 0.1, 0.002, 7),
+    "sbm10k_cfg1": lambda: gg.sbm(10000, 100, 0.1, 0.0005, 1),
+    "rmat12": lambda: gg.rmat(12, weights=gg.W_INT8, seed=3),
+    "rmat14": lambda: gg.rmat(14, weights=gg.W_INT8, seed=22),
+    "grid": lambda: gg.grid(60, 70, 0.1, 0.01, 3),
+    "loops": lambda: random_graph(300, 0.03, np.random.default_rng(1), self_loops=True),
+    "ring": lambda: cliques(8, 6, ring=True),
+    "star": lambda: gg.from_edges(3000, [(0, i) for i in range(1, 3000)]),
+}
+
+
+# ---------------------------------------------------------------- primitives
+@pytest.mark.parametrize("n", [0, 1, 5, 4095, 4096, 4097, 100003, 3_000_001])
+def test_exclusive_scan(L, n):
+    rng = np.random.default_rng(n)
+    x = rng.integers(0, 1 << 20, size=n, dtype=np.int64)
+    out, tot = L.exclusive_scan(torch.from_numpy(x).cuda())
+    ref = np.concatenate([[0], np.cumsum(x)])
+    assert tot == int(ref[-1])
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("name", ["sbm2k", "rmat12", "loops", "star", "grid"])
+def test_modularity_matches_oracle(L, name):
+    g = GRAPHS[name]()
+    o, t, w = dev(g)
+    rng = np.random.default_rng(5)
+    for k in (1, 7, g.n):
+        mem = rng.integers(0, max(1, min(k, g.n)), size=g.n).astype(np.int32)
+        q = L.modularity(o, t, w, torch.from_numpy(mem).cuda())
+        assert abs(q - oracle.modularity(g.offsets, g.targets, g.weights, mem)) <= 1e-12
+
+
+def test_modularity_fp32(L):
+    g = gg.rmat(12, weights=gg.W_FP32, seed=4)
+    o, t, w = dev(g)
+    mem = np.random.default_rng(1).integers(0, 50, size=g.n).astype(np.int32)
+    q = L.modularity(o, t, w, torch.from_numpy(mem).cuda())
+    assert abs(q - oracle.modularity(g.offsets, g.targets, g.weights, mem)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["sbm2k", "rmat12", "rmat14", "loops", "star", "grid", "ring"])
+@pytest.mark.parametrize("seed,pass_index", [(0, 0), (99, 3)])
+def test_colouring_matches_oracle(L, name, seed, pass_index):
+    g = GRAPHS[name]()
+    o, t, _ = dev(g)
+    col, nc = L.colour(o, t, seed, pass_index)
+    ref, ref_nc = oracle.colour(g.offsets, g.targets, seed, pass_index)
+    assert nc == ref_nc
+    assert np.array_equal(col.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("name", ["sbm2k", "rmat12", "loops", "star", "grid"])
+@pytest.mark.parametrize("k", [1, 3, 40, 10**9])
+def test_aggregate_matches_oracle(L, name, k):
+    g = GRAPHS[name]()
+    o, t, w = dev(g)
+    mem = canonical(np.random.default_rng(k % 1000).integers(0, min(k, g.n), size=g.n))
+    nc = int(mem.max()) + 1
+    oo, ot, ow = L.aggregate(o, t, w, torch.from_numpy(mem).cuda(), nc)
+    ro, rt, rw = oracle.aggregate(g.offsets, g.targets, g.weights, mem, nc)
+    oo, ot, ow = oo.cpu().numpy(), ot.cpu().numpy(), ow.cpu().numpy()
+    assert np.array_equal(np.diff(oo), np.diff(ro))
+    for c in range(nc):
+        a = sorted(zip(ot[oo[c]:oo[c + 1]].tolist(), ow[oo[c]:oo[c + 1]].tolist()))
+        b = sorted(zip(rt[ro[c]:ro[c + 1]].tolist(), rw[ro[c]:ro[c + 1]].tolist()))
+        assert a == b
+
+
+def test_aggregate_fp32(L):
+    g = gg.rmat(11, weights=gg.W_FP32, seed=9)
+    o, t, w = dev(g)
+    mem = canonical(np.random.default_rng(2).integers(0, 30, size=g.n))
+    nc = int(mem.max()) + 1
+    oo, ot, ow = L.aggregate(o, t, w, torch.from_numpy(mem).cuda(), nc)
+    ro, rt, rw = oracle.aggregate(g.offsets, g.targets, g.weights, mem, nc)
+    oo, ot, ow = oo.cpu().numpy(), ot.cpu().numpy(), ow.cpu().numpy()
+    for c in range(nc):
+        a = dict(zip(ot[oo[c]:oo[c + 1]].tolist(), ow[oo[c]:oo[c + 1]].tolist()))
+        b = dict(zip(rt[ro[c]:ro[c + 1]].tolist(), rw[ro[c]:ro[c + 1]].tolist()))
+        assert a.keys() == b.keys()
+        for d in a:
+            assert abs(a[d] - b[d]) <= 1e-5 * max(1.0, abs(b[d]))
+
+
+# ---------------------------------------------------------------- local-moving phase
+@pytest.mark.parametrize("name", ["sbm2k", "sbm10k_cfg1", "rmat12", "rmat14", "loops", "grid", "ring", "star"])
+@pytest.mark.parametrize("pruning", [1, 0])
+def test_local_move_deterministic_bit_exact(L, name, pruning):
+    g = GRAPHS[name]()
+    o, t, w = dev(g)
+    cp, it, mv = L.local_move(o, t, w, mode="deterministic", pruning=pruning, seed=17, pass_index=0)
+    ref_cp, ref_it, ref_mv = oracle.local_move(g.offsets, g.targets, g.weights,
+                                               oracle.default_params(pruning=pruning, seed=17), 0)
+    assert (it, mv) == (ref_it, ref_mv)
+    assert np.array_equal(cp.cpu().numpy(), ref_cp)
+
+
+# ---------------------------------------------------------------- whole method
+@pytest.mark.parametrize("name", ["sbm2k", "sbm10k_cfg1", "rmat12", "rmat14", "loops", "grid", "ring", "star"])
+@pytest.mark.parametrize("compact", [1, 0])
+def test_run_deterministic_bit_exact(L, name, compact):
+    g = GRAPHS[name]()
+    o, t, w = dev(g)
+    mem, res = L.run(o, t, w, mode="deterministic", compact=compact, max_passes=100, seed=5)
+    ref_mem, ref_q, ref_passes, ref_stats = oracle.louvain(g.offsets, g.targets, g.weights,
+                                                           oracle.default_params(max_passes=100, seed=5))
+    assert np.array_equal(mem.cpu().numpy(), ref_mem)
+    assert abs(res.modularity - ref_q) <= 1e-12
+    assert res.passes == ref_passes
+    assert [s["iterations"] for s in res.stats] == [s["iterations"] for s in ref_stats]
+    assert [s["n_communities"] for s in res.stats] == [s["n_communities"] for s in ref_stats]
+
+
+def test_run_is_repeatable(L):
+    g = GRAPHS["rmat14"]()
+    o, t, w = dev(g)
+    a, _ = L.run(o, t, w, mode="deterministic")
+    b, _ = L.run(o, t, w, mode="deterministic")
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["sbm10k_cfg1", "rmat14", "grid", "ring"])
+def test_run_fast_mode_quality(L, name):
+    g = GRAPHS[name]()
+    o, t, w = dev(g)
+    mem, res = L.run(o, t, w, mode="fast", max_passes=100)
+    m = mem.cpu().numpy()
+    assert m.min() >= 0 and m.max() < g.n and res.n_communities == len(np.unique(m))
+    assert np.array_equal(np.unique(m), np.arange(res.n_communities))  # dense ids
+    q_check = oracle.modularity(g.offsets, g.targets, g.weights, m)
+    assert abs(res.modularity - q_check) <= 1e-12
+    _, ref_q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params(max_passes=100))
+    assert res.modularity >= ref_q - 0.005
+
+
+@pytest.mark.parametrize("mode", ["deterministic", "fast"])
+def test_run_fp32_weights(L, mode):
+    g = gg.rmat(13, weights=gg.W_FP32, seed=8)
+    o, t, w = dev(g)
+    mem, res = L.run(o, t, w, mode=mode, max_passes=100)
+    m = mem.cpu().numpy()
+    assert abs(res.modularity - oracle.modularity(g.offsets, g.targets, g.weights, m)) <= 1e-10
+    _, ref_q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params(max_passes=100))
+    tol = 1e-4 if mode == "deterministic" else 0.005
+    assert res.modularity >= ref_q - tol
+
+
+def test_run_host_equals_run(L):
+    g = GRAPHS["sbm2k"]()
+    o, t, w = dev(g)
+    a, ra = L.run(o, t, w)
+    b, rb = L.run_host(g.offsets, g.targets, g.weights)
+    assert np.array_equal(a.cpu().numpy(), b) and ra.modularity == rb.modularity
+
+
+# ---------------------------------------------------------------- edge cases and errors
+def test_empty_and_edgeless(L):
+    g0 = gg.from_edges(0, [])
+    o, t, w = dev(g0)
+    mem, res = L.run(o, t, w)
+    assert mem.numel() == 0 and res.modularity == 0.0
+    g = gg.from_edges(7, [])
+    o, t, w = dev(g)
+    mem, res = L.run(o, t, w)
+    assert mem.cpu().tolist() == list(range(7)) and res.modularity == 0.0
+
+
+def test_two_vertices(L):
+    g = gg.from_edges(2, [(0, 1)])
+    mem, res = L.run(*dev(g))
+    assert mem.cpu().tolist() == [0, 0] and res.modularity == 0.0 and res.passes == 2
+
+
+def _status(L, fn):
+    import paper_2312_04876_gb300 as lv
+    with pytest.raises(lv.LouvainError) as ei:
+        fn()
+    return ei.value.status
+
+
+def test_invalid_inputs_rejected(L):
+    g = gg.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    o, t, w = dev(g)
+    bad_t = t.clone(); bad_t[0] = 9
+    assert _status(L, lambda: L.run(o, bad_t, w)) == 1
+    bad_w = w.clone(); bad_w[2] = -1
+    assert _status(L, lambda: L.run(o, t, bad_w)) == 1
+    asym = w.clone(); asym[0] = 5
+    assert _status(L, lambda: L.run(o, t, asym)) == 1
+    bad_o = o.clone(); bad_o[2] = 99
+    assert _status(L, lambda: L.run(bad_o, t, w)) == 1
+    big = gg.from_edges(2, [(0, 1)], [2**30])
+    assert _status(L, lambda: L.run(*dev(big))) == 3
+    mem = torch.tensor([0, 0, 5, 1], dtype=torch.int32, device="cuda")
+    assert _status(L, lambda: L.modularity(o, t, w, mem)) == 1
+    # the handle stays usable after errors
+    m, r = L.run(o, t, w)
+    assert r.passes >= 1
+
+
+def test_hbm_budget_reports_oom(cuda_ok):
+    import paper_2312_04876_gb300 as lv
+    g = GRAPHS["sbm2k"]()
+    h = lv.Louvain(0, hbm_budget_bytes=1 << 16)
+    assert _status(h, lambda: h.run(*dev(g))) == 2
+    h.close()

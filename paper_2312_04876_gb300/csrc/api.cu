@@ -36,6 +36,7 @@ struct Workspace {
   int32_t *Cp = nullptr, *colour = nullptr, *csize = nullptr, *mv_from = nullptr, *mv_to = nullptr;
   int32_t *perm = nullptr, *cperm = nullptr, *occ = nullptr, *counts = nullptr, *cursor = nullptr;
   int32_t *cverts = nullptr, *jcnt = nullptr, *jl0 = nullptr, *jl1 = nullptr, *tmp_mem = nullptr;
+  unsigned long long* jrc = nullptr;
   uint8_t* flags = nullptr;
   int64_t *newid = nullptr, *coff = nullptr, *cdeg = nullptr, *len = nullptr, *tile_tmp = nullptr;
   RowSet rows[2];
@@ -142,7 +143,7 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
        dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.tmp_mem, n1);
   ok = ok && dalloc(h, d, &ws.flags, n1);
   ok = ok && dalloc(h, d, &ws.newid, n1 + 1) && dalloc(h, d, &ws.coff, n1 + 1) && dalloc(h, d, &ws.cdeg, n1 + 1) &&
-       dalloc(h, d, &ws.len, n1 + 1) &&
+       dalloc(h, d, &ws.len, n1 + 1) && dalloc(h, d, &ws.jrc, n1 + 16) &&
        dalloc(h, d, &ws.tile_tmp, scan_tmp_elems((int64_t)kNumBuckets * n1 + 8) + 8);  // class sort scans 5 n keys
   for (int r = 0; r < 2 && ok; r++)
     ok = dalloc(h, d, &ws.rows[r].hoff, n1 + 1) && dalloc(h, d, &ws.rows[r].hend, n1) &&
@@ -276,6 +277,16 @@ struct RunOut {
   int64_t n_communities = 0;
 };
 
+louvain_status colour_failure(louvain_handle h) {
+  const unsigned long long* q = h->pin;
+  char buf[256];
+  snprintf(buf, sizeof buf,
+           "internal: colouring did not finish (coloured %llu of %llu after %llu rounds, max colour %llu, "
+           "guard trips %llu)",
+           q[3], q[5], q[6], q[4], q[7]);
+  return set_err(h, LOUVAIN_ERR_CUDA, buf);
+}
+
 // Per-pass degree buckets of graph g into ws.perm with host offsets hb[kNumBuckets + 1].
 template <class W>
 louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, int64_t hb[kNumBuckets + 1],
@@ -310,12 +321,12 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   int32_t ncol = 1;
   if (det) {
     GraphView<int32_t> gs{g.n, g.rbeg, g.rend, g.tg, nullptr};
-    JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1};
+    JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1, ws.n_cap + 1, ws.jrc};
     if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
     cudaError_t ce;
     ncol = jp_colour(c, gs, ws.perm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce);
     if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
-    if (ncol < 0) return set_err(h, LOUVAIN_ERR_CUDA, "internal: colouring did not finish");
+    if (ncol < 0) return colour_failure(h);
     const int64_t nkeys = (int64_t)ncol * kNumBuckets;
     if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
     bucket_sort(c, 1, g.n, g.rbeg, g.rend, ws.colour, nullptr, nkeys, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
@@ -759,11 +770,11 @@ louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const
   GraphView<int32_t> g{n, d_offsets, d_offsets + 1, d_targets, nullptr};
   int64_t hb[kNumBuckets + 1], max_deg;
   if ((s = degree_buckets(h, c, g, hb, &max_deg)) != LOUVAIN_OK) return s;
-  JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1};
+  JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1, h->ws.n_cap + 1, h->ws.jrc};
   cudaError_t ce;
   int32_t nc = jp_colour(c, g, h->ws.perm, hb, seed, pass, d_colour, jb, ctrl, h->pin, &ce);
   if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
-  if (nc < 0) return set_err(h, LOUVAIN_ERR_CUDA, "internal: colouring did not finish");
+  if (nc < 0) return colour_failure(h);
   *n_colours = nc;
   return sync(h, c, "colour end");
 }

@@ -18,7 +18,9 @@ struct JpArgs {
   int32_t* colour;
   int32_t* cnt;
   int32_t* lists[2];
-  Ctrl* ctrl;  // cnt[0..2] rotating ready counts, cnt[3] coloured total, cnt[4] max colour + 1
+  int64_t list_cap;             // capacity of each ready list
+  unsigned long long* rcount;   // rcount[r] = size of the ready list of round r (zeroed up front)
+  Ctrl* ctrl;                   // cnt[3] coloured total, cnt[4] max colour + 1, cnt[7] guard trips
 };
 
 template <int G>
@@ -40,8 +42,9 @@ __global__ void __launch_bounds__(kBlock) jp_count(JpArgs a, const int32_t* list
       a.cnt[v] = k;
       a.colour[v] = -1;
       if (k == 0) {
-        unsigned long long pos = atomicAdd(&a.ctrl->cnt[0], 1ULL);
-        a.lists[0][pos] = v;
+        const unsigned long long pos = atomicAdd(&a.rcount[0], 1ULL);
+        if ((int64_t)pos < a.list_cap) a.lists[0][pos] = v;
+        else atomicAdd(&a.ctrl->cnt[7], 1ULL);
       }
     }
   }
@@ -52,18 +55,25 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
   __shared__ unsigned bm[kBlock / 32][32];
   __shared__ unsigned long long done_blk;
   __shared__ int32_t max_blk;
-  const int cur = r % 3, nxt = (r + 1) % 3, clr = (r + 2) % 3;
   const int32_t* in = a.lists[r & 1];
   int32_t* out = a.lists[(r + 1) & 1];
-  const unsigned long long count = *(volatile unsigned long long*)&a.ctrl->cnt[cur];
+  unsigned long long count = *(volatile unsigned long long*)&a.rcount[r];
   if (count == 0) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctrl->cnt[clr] = 0;  // untouched by this round
+  if ((int64_t)count > a.list_cap) count = (unsigned long long)a.list_cap;
   if (threadIdx.x == 0) { done_blk = 0; max_blk = 0; }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
   for (int64_t k = (int64_t)blockIdx.x * (kBlock / 32) + warp; k < (int64_t)count; k += nw) {
     const int32_t v = in[k];
+    // guard: a ready vertex is uncoloured; anything else is recorded and skipped
+    int32_t prev = 0;
+    if (lane == 0) prev = a.colour[v];
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != -1) {
+      if (lane == 0) atomicAdd(&a.ctrl->cnt[7], 1ULL);
+      continue;
+    }
     const uint64_t pv = hash3(a.seed, (uint64_t)a.pass, (uint64_t)v);
     const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
     int32_t mex = -1;
@@ -80,13 +90,13 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
       __syncwarp();
       const unsigned freeb = ~bm[warp][lane];
       const unsigned ball = __ballot_sync(0xffffffffu, freeb != 0u);
+      __syncwarp();
       if (ball) {
         const int L = __ffs(ball) - 1;
         const unsigned fw = __shfl_sync(0xffffffffu, freeb, L);
         mex = base + 32 * L + (__ffs(fw) - 1);
         break;
       }
-      __syncwarp();
     }
     if (mex < 0) {  // unreachable: some colour <= degree is always free
       if (lane == 0) atomicOr(&a.ctrl->error, kErrRange);
@@ -102,8 +112,9 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
       const int32_t u = a.g.tg[e];
       if (u == v || !higher(pv, v, hash3(a.seed, (uint64_t)a.pass, (uint64_t)u), u)) continue;
       if (atomicSub(&a.cnt[u], 1) == 1) {
-        unsigned long long pos = atomicAdd(&a.ctrl->cnt[nxt], 1ULL);
-        out[pos] = u;
+        const unsigned long long pos = atomicAdd(&a.rcount[r + 1], 1ULL);
+        if ((int64_t)pos < a.list_cap) out[pos] = u;
+        else atomicAdd(&a.ctrl->cnt[7], 1ULL);
       }
     }
   }
@@ -115,20 +126,27 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
 }
 
 __global__ void k_jp_reset(Ctrl* c) {
-  for (int k = 0; k < 5; k++) c->cnt[k] = 0;
+  c->cnt[3] = 0;
+  c->cnt[4] = 0;
+  c->cnt[7] = 0;
 }
 
 int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, const int64_t* hb, uint64_t seed,
                   int32_t pass, int32_t* colour, const JpBuffers& jb, Ctrl* ctrl, unsigned long long* h_pinned,
                   cudaError_t* err) {
   *err = cudaSuccess;
+  const int64_t listed = hb[kNumBuckets] - hb[0];
+  // Each round colours at least one vertex while any is left, so `listed` rounds always suffice.
+  const int batch = 8;
+  const int64_t max_rounds = listed + batch;
   // isolated vertices (left out of the bucket lists) get colour 0
   fill_i32(c, colour, 0, g.n);
+  cudaMemsetAsync(jb.rcount, 0, (size_t)(max_rounds + 2) * sizeof(unsigned long long), c.s);
   k_jp_reset<<<1, 1, 0, c.s>>>(ctrl);
   c.launches++;
   JpArgs a;
   a.g = g; a.seed = seed; a.pass = pass; a.colour = colour; a.cnt = jb.cnt;
-  a.lists[0] = jb.list0; a.lists[1] = jb.list1; a.ctrl = ctrl;
+  a.lists[0] = jb.list0; a.lists[1] = jb.list1; a.list_cap = jb.list_cap; a.rcount = jb.rcount; a.ctrl = ctrl;
   const int cap = c.num_sms * 16;
   for (int b = 0; b < kNumBuckets; b++) {
     int64_t cnt = hb[b + 1] - hb[b];
@@ -142,21 +160,25 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
     }
     c.launches++;
   }
-  const int64_t listed = hb[kNumBuckets] - hb[0];
-  // Each round colours at least one vertex while any is left, so `listed` rounds always suffice.
-  const int batch = 8;
+  if ((*err = cudaGetLastError()) != cudaSuccess) return -1;
   int64_t r = 0;
-  while (r < listed + batch) {
-    for (int k = 0; k < batch; k++, r++) {
+  h_pinned[3] = 0;
+  while (r < max_rounds) {
+    for (int k = 0; k < batch && r < max_rounds; k++, r++) {
       jp_round<<<c.num_sms * 8, kBlock, 0, c.s>>>(a, (int)r);
       c.launches++;
     }
-    cudaMemcpyAsync(h_pinned, &ctrl->cnt[0], 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.s);
+    if ((*err = cudaGetLastError()) != cudaSuccess) return -1;
+    cudaMemcpyAsync(h_pinned, &ctrl->cnt[0], 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.s);
     *err = cudaStreamSynchronize(c.s);
     if (*err != cudaSuccess) return -1;
-    if ((int64_t)h_pinned[3] >= listed) break;
+    if ((int64_t)h_pinned[3] >= listed || h_pinned[7]) break;
   }
-  if ((int64_t)h_pinned[3] != listed) return -1;
+  if ((int64_t)h_pinned[3] != listed || h_pinned[7]) {
+    h_pinned[5] = (unsigned long long)listed;
+    h_pinned[6] = (unsigned long long)r;
+    return -1;
+  }
   int32_t ncol = (int32_t)h_pinned[4];
   return ncol > 0 ? ncol : 1;
 }

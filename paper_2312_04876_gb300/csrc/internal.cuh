@@ -107,12 +107,14 @@ void move_finish(Ctx& c, Ctrl* ctrl);
 
 // ---------------------------------------------------------------- colour.cu
 struct JpBuffers {
-  int32_t* cnt;     // [n] uncoloured higher-priority neighbours
-  int32_t* list0;   // [n] ready lists
+  int32_t* cnt;                 // [n] uncoloured higher-priority neighbour arcs
+  int32_t* list0;               // [list_cap] ready lists
   int32_t* list1;
+  int64_t list_cap;
+  unsigned long long* rcount;   // [n + 16] per-round ready-list sizes
 };
 // Jones-Plassmann colouring of g (self-loops ignored).  Returns the number of colours.
-// Uses ctrl->cnt[0..4]; synchronises the stream a few times.
+// Uses ctrl->cnt[3, 4, 7]; synchronises the stream once per batch of rounds.
 int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g_struct, const int32_t* perm, const int64_t* h_bucket_offs,
                   uint64_t seed, int32_t pass, int32_t* colour, const JpBuffers& jb, Ctrl* ctrl,
                   unsigned long long* h_pinned, cudaError_t* err);

@@ -73,6 +73,11 @@ typedef struct {
   int32_t compact;               /* 1: compact each super-vertex graph to dense CSR (default);
                                     0: run later passes on the holey CSR with degrees */
   int32_t pass_modularity;       /* 1: fill louvain_pass_stats.modularity (extra arc sweep) */
+  int32_t profile;               /* 1: time every kernel launch with CUDA events on `stream` and
+                                    keep per-kernel totals for louvain_kernel_profile() */
+  int32_t fast_classes;          /* fast mode: vertices are split into this many random classes
+                                    (hash3(seed, pass, v) mod K) processed one after another; moves
+                                    inside a class stay asynchronous.  Default 16; 1 = all at once */
   int32_t reserved;
 } louvain_params;
 
@@ -106,7 +111,7 @@ void louvain_destroy(louvain_handle h);
 
 /* Defaults from Section 4.1: max_iterations 20, tolerance 0.01, tolerance_drop 10,
  * aggregation_tolerance 0.8, pruning on; max_passes 10; deterministic mode; seed 0;
- * validate 1; compact 1; pass_modularity 0. */
+ * validate 1; compact 1; pass_modularity 0; profile 0; fast_classes 16. */
 louvain_status louvain_default_params(louvain_params* p);
 
 /* Message of the last failure on this handle ("" if none).  Valid until the next call. */
@@ -167,6 +172,21 @@ louvain_status louvain_aggregate(louvain_handle h, int64_t n, int64_t n_arcs, co
                                  const int32_t* d_membership, int64_t n_comm, void* stream,
                                  int64_t* d_out_offsets, int32_t* d_out_targets, void* d_out_weights,
                                  int64_t* out_arcs);
+
+/* Per-kernel totals of the last louvain_run made with params.profile = 1: for each kernel class
+ * (local-move buckets, Sigma apply, merge buckets, compaction, colouring, modularity) the number of
+ * timed launches, their summed device time (CUDA events recorded on the run's stream around each
+ * launch) and the algorithmic bytes those launches had to move (from device-side counters of
+ * vertices, arcs, candidates and moves; formulas in the design notes).  Writes up to cap entries
+ * to out (host), the count to *n. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double algorithmic_bytes;
+} louvain_kernel_stat;
+
+louvain_status louvain_kernel_profile(louvain_handle h, louvain_kernel_stat* out, int32_t cap, int32_t* n);
 
 /* Exclusive prefix sum (Algorithm 3's exclusiveScan) of d_in[count] int64 into d_out[count + 1]
  * (d_out[count] = total); d_in == d_out is allowed.  *total (host, optional). */

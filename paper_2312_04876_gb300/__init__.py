@@ -196,6 +196,20 @@ class Louvain:
         a = int(na.value)
         return oo, ot[:a], ow[:a]
 
+    def kernel_profile(self) -> list:
+        """Per-kernel-class totals of the last run made with profile=1: name, launches, ms,
+        algorithmic bytes and the achieved GB/s those imply."""
+        cap = 32
+        arr = (_native.KernelStat * cap)()
+        n = ctypes.c_int32()
+        self._check(self._lib.louvain_kernel_profile(self._h, arr, cap, ctypes.byref(n)))
+        out = []
+        for k in arr[:n.value]:
+            gbs = k.algorithmic_bytes / (k.ms * 1e6) if k.ms > 0 else 0.0
+            out.append(dict(name=k.name.decode(), launches=k.launches, ms=k.ms, bytes=k.algorithmic_bytes,
+                            gbs=gbs))
+        return out
+
     def exclusive_scan(self, values, stream=None):
         import torch
         out = torch.empty(values.numel() + 1, dtype=torch.int64, device=values.device)

@@ -17,7 +17,8 @@ class Params(ctypes.Structure):
                 ("tolerance", ctypes.c_double), ("tolerance_drop", ctypes.c_double),
                 ("aggregation_tolerance", ctypes.c_double), ("pruning", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("validate", ctypes.c_int32),
-                ("compact", ctypes.c_int32), ("pass_modularity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("compact", ctypes.c_int32), ("pass_modularity", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("fast_classes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PassStats(ctypes.Structure):
@@ -31,6 +32,11 @@ class Result(ctypes.Structure):
     _fields_ = [("modularity", ctypes.c_double), ("passes", ctypes.c_int32), ("total_iterations", ctypes.c_int32),
                 ("n_communities", ctypes.c_int64), ("ms_total", ctypes.c_float),
                 ("kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("algorithmic_bytes", ctypes.c_double)]
 
 
 _V = ctypes.c_void_p
@@ -53,6 +59,7 @@ SIGNATURES = {
                                   _V, _V, ctypes.POINTER(_I32), ctypes.POINTER(_I64)]),
     "louvain_aggregate": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, _V, _I64, _V, _V, _V, _V, ctypes.POINTER(_I64)]),
     "louvain_exclusive_scan": (_I32, [_V, _V, _V, _I64, _V, ctypes.POINTER(_I64)]),
+    "louvain_kernel_profile": (_I32, [_V, ctypes.POINTER(KernelStat), _I32, ctypes.POINTER(_I32)]),
 }
 
 _lib = None

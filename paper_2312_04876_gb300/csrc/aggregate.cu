@@ -72,7 +72,7 @@ __device__ __forceinline__ int64_t lanes_incl_scan(int64_t x, unsigned mask) {
 template <class M, int W>
 __device__ __forceinline__ bool merge_members(const MergeArgs<M>& a, int64_t k0, int64_t k1, int64_t kstride,
                                               int32_t* tk, typename M::h_t* tv, unsigned size, int shift,
-                                              unsigned mask) {
+                                              unsigned mask, unsigned long long& arcs) {
   typedef typename M::h_t H;
   const int l = threadIdx.x & (W - 1);
   bool ok = true;
@@ -87,6 +87,7 @@ __device__ __forceinline__ bool merge_members(const MergeArgs<M>& a, int64_t k0,
     const int64_t incl = lanes_incl_scan<W>(len, mask);
     const int64_t total = __shfl_sync(mask, incl, W - 1, W);
     const int64_t excl = incl - len;
+    arcs += (unsigned long long)len;
     for (int64_t f0 = 0; f0 < total; f0 += W) {
       const int64_t f = f0 + l;
       const int o = flat_owner<W>(incl, f, mask);
@@ -124,19 +125,22 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
     tk = skeys + gib * SL;
     tv = svals + gib * SL;
   }
+  unsigned long long ctr[4] = {0, 0, 0, 0};  // communities, members, arcs scanned, arcs written
   for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
     const int32_t c = list[idx];
     const int64_t m0 = a.coff[c], m1 = a.coff[c + 1];
+    if (lane == 0) { ctr[0]++; ctr[1] += (unsigned long long)(m1 - m0); }
     const int64_t D = a.cdeg[c];
     const int lg = GLOBAL ? tbl_log2(D < a.nc ? D : a.nc, 6, glog) : tbl_log2(D, 1, LOG);
     const unsigned size = 1u << lg;
     const int shift = 32 - lg;
     bool ok;
     if (G <= 32) {
-      ok = merge_members<M, (G <= 32 ? G : 32)>(a, m0, m1, G, tk, tv, size, shift, Grp<G>::mask());
+      // each lane adds the row lengths of the members it loaded
+      ok = merge_members<M, (G <= 32 ? G : 32)>(a, m0, m1, G, tk, tv, size, shift, Grp<G>::mask(), ctr[2]);
     } else {
       const int warp = threadIdx.x >> 5;
-      ok = merge_members<M, 32>(a, m0 + 32 * warp, m1, 32 * (G / 32), tk, tv, size, shift, 0xffffffffu);
+      ok = merge_members<M, 32>(a, m0 + 32 * warp, m1, 32 * (G / 32), tk, tv, size, shift, 0xffffffffu, ctr[2]);
     }
     if (!ok) atomicOr(&a.ctrl->error, kErrTableFull);
     Grp<G>::sync();
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
         }
         cnt += __popc(ball);
       }
-      if (lane == 0) a.hend[c] = base + cnt;
+      if (lane == 0) { a.hend[c] = base + cnt; ctr[3] += cnt; }
     } else {
       if (threadIdx.x == 0) s_cnt = 0;
       __syncthreads();
@@ -184,10 +188,11 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
         }
       }
       __syncthreads();
-      if (threadIdx.x == 0) a.hend[c] = base + (int64_t)s_cnt;
+      if (threadIdx.x == 0) { a.hend[c] = base + (int64_t)s_cnt; ctr[3] += s_cnt; }
       __syncthreads();
     }
   }
+  block_add_counters<4>(a.ctrl->mg_stat[a.bucket], ctr);
 }
 
 template <class M, int G, int LOG, bool GLOBAL>
@@ -202,8 +207,11 @@ static void launch_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* list, int
 }
 
 template <class M>
-void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt) {
+void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& args, const int32_t* list, int64_t count,
+                  const GlobalTable& gt) {
   if (count <= 0) return;
+  MergeArgs<M> a = args;
+  a.bucket = bucket < kNumBuckets ? bucket : kNumBuckets - 1;
   const int cap = c.num_sms * 16;
   switch (bucket) {
     case 0: launch_merge<M, 4, 3, false>(c, a, list, count, gt, cap); break;

@@ -62,6 +62,33 @@ struct Workspace {
 
 }  // namespace
 
+// Kernel classes of the per-launch profile.
+enum KClass {
+  kLm0 = 0,            // local-move buckets 0..4
+  kApply = kNumBuckets,
+  kMg0,                // merge buckets 0..4
+  kCompact = kMg0 + kNumBuckets,
+  kColour,
+  kModularity,
+  kNumClasses
+};
+static const char* const kClassNames[kNumClasses] = {
+    "local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "local_move_b3_block", "local_move_b4_global",
+    "sigma_apply", "merge_b0_g4", "merge_b1_g8", "merge_b2_warp", "merge_b3_block", "merge_b4_global",
+    "compact", "colour_jp", "modularity"};
+
+struct Profile {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  struct Rec { int cls; size_t e0, e1; };
+  std::vector<Rec> recs;
+  int64_t launches[kNumClasses] = {};
+  double ms[kNumClasses] = {};
+  double bytes[kNumClasses] = {};
+  bool valid = false;
+};
+
 struct louvain_handle_s {
   int device = 0;
   int num_sms = 152;
@@ -71,6 +98,7 @@ struct louvain_handle_s {
   unsigned long long* pin = nullptr;  // pinned host staging
   size_t pin_bytes = 0;
   std::vector<cudaEvent_t> events;
+  Profile prof;
 };
 
 namespace {
@@ -203,6 +231,52 @@ louvain_status ensure_gtable(louvain_handle h, Ctx& c, int64_t max_distinct, int
   return LOUVAIN_OK;
 }
 
+// ---- per-launch profile: an event before and after each timed launch on the run's stream
+int prof_begin(louvain_handle h, Ctx& c) {
+  Profile& P = h->prof;
+  if (!P.on) return -1;
+  while (P.ev.size() < P.used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); P.on = false; return -1; }
+    P.ev.push_back(e);
+  }
+  cudaEventRecord(P.ev[P.used], c.s);
+  P.used += 2;
+  return (int)(P.used - 2);
+}
+void prof_end(louvain_handle h, Ctx& c, int cls, int mark) {
+  Profile& P = h->prof;
+  if (mark < 0 || !P.on) return;
+  cudaEventRecord(P.ev[mark + 1], c.s);
+  P.recs.push_back({cls, (size_t)mark, (size_t)mark + 1});
+}
+// After the final synchronisation: device times per class and algorithmic bytes from counters.
+void prof_finish(louvain_handle h, const Ctrl& ctrl) {
+  Profile& P = h->prof;
+  if (!P.on) return;
+  for (int k = 0; k < kNumClasses; k++) { P.launches[k] = 0; P.ms[k] = 0.0; P.bytes[k] = 0.0; }
+  for (const Profile::Rec& r : P.recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P.ev[r.e0], P.ev[r.e1]) == cudaSuccess) {
+      P.ms[r.cls] += ms;
+      P.launches[r.cls]++;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  for (int b = 0; b < kNumBuckets; b++) {
+    const unsigned long long* l = ctrl.lm_stat[b];
+    // list entry + flag; per processed vertex row bounds, C'[i], K_i, Sigma_d, flag clear; per arc
+    // target, weight, C'[j]; per candidate Sigma_c; per move C' write and two Sigma updates; marks
+    P.bytes[kLm0 + b] = 5.0 * l[0] + 37.0 * l[1] + 12.0 * l[2] + 8.0 * l[3] + 20.0 * l[4] + 1.0 * l[5];
+    const unsigned long long* m = ctrl.mg_stat[b];
+    // per community offsets, total degree, holey offset and end; per member id and row bounds; per
+    // arc target, weight, C'[j]; per written super-arc (target, weight)
+    P.bytes[kMg0 + b] = 32.0 * m[0] + 20.0 * m[1] + 12.0 * m[2] + 8.0 * m[3];
+  }
+  P.valid = true;
+}
+
 louvain_status sync(louvain_handle h, Ctx& c, const char* where) {
   cudaError_t e = cudaStreamSynchronize(c.s);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -213,9 +287,9 @@ louvain_status sync(louvain_handle h, Ctx& c, const char* where) {
 // Reads `count` int64 from device into the pinned buffer (synchronising) and returns it.
 const int64_t* read_i64(louvain_handle h, Ctx& c, const int64_t* d, int64_t count, louvain_status* st,
                         const char* where) {
-  *st = ensure_pinned(h, (size_t)count * sizeof(int64_t) + 4096);
+  *st = ensure_pinned(h, (size_t)count * sizeof(int64_t) + 8192);
   if (*st != LOUVAIN_OK) return nullptr;
-  int64_t* p = reinterpret_cast<int64_t*>(h->pin) + 64;  // first 512 bytes reserved for Ctrl copies
+  int64_t* p = reinterpret_cast<int64_t*>(h->pin) + 128;  // first 1 KiB reserved for Ctrl copies
   cudaMemcpyAsync(p, d, (size_t)count * sizeof(int64_t), cudaMemcpyDeviceToHost, c.s);
   *st = sync(h, c, where);
   return *st == LOUVAIN_OK ? p : nullptr;
@@ -246,7 +320,8 @@ float elapsed(louvain_handle h, size_t a, size_t b) {
 
 bool valid_params(const louvain_params* p) {
   return p && p->max_passes >= 0 && p->max_iterations >= 0 && p->tolerance >= 0.0 && p->tolerance_drop > 0.0 &&
-         p->aggregation_tolerance >= 0.0 && (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
+         p->aggregation_tolerance >= 0.0 && p->fast_classes >= 0 && p->fast_classes <= 4096 &&
+         (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
 }
 
 // Full CSR validation on the device.  Returns OK / INVALID / OVERFLOW.
@@ -295,7 +370,7 @@ louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, i
   louvain_status st = ensure_keys(h, kNumBuckets);
   if (st != LOUVAIN_OK) return st;
   cudaMemsetAsync(&ws.ctrl->cnt[6], 0, sizeof(unsigned long long), c.s);
-  bucket_sort(c, 0, g.n, g.rbeg, g.rend, nullptr, nullptr, kNumBuckets, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
+  bucket_sort(c, KeyDesc{0, 1, 0, 0}, g.n, g.rbeg, g.rend, nullptr, nullptr, kNumBuckets, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
               &ws.ctrl->cnt[6]);
   const int64_t* p = read_i64(h, c, ws.keyoffs, kNumBuckets + 1, &st, "degree buckets");
   if (!p) return st;
@@ -324,18 +399,28 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1, ws.n_cap + 1, ws.jrc};
     if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
     cudaError_t ce;
+    const int pm = prof_begin(h, c);
     ncol = jp_colour(c, gs, ws.perm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce);
+    prof_end(h, c, kColour, pm);
     if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
     if (ncol < 0) return colour_failure(h);
     const int64_t nkeys = (int64_t)ncol * kNumBuckets;
     if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
-    bucket_sort(c, 1, g.n, g.rbeg, g.rend, ws.colour, nullptr, nkeys, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
+    bucket_sort(c, KeyDesc{1, 1, 0, 0}, g.n, g.rbeg, g.rend, ws.colour, nullptr, nkeys, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
                 nullptr);
     const int64_t* q = read_i64(h, c, ws.keyoffs, nkeys + 1, &s, "class buckets");
     if (!q) return s;
     ho.assign(q, q + nkeys + 1);
   } else {
-    ho.assign(hb, hb + kNumBuckets + 1);
+    // fast schedule: random vertex classes processed one after another, asynchronous inside a class
+    ncol = p.fast_classes > 0 ? p.fast_classes : 1;
+    const int64_t nkeys = (int64_t)ncol * kNumBuckets;
+    if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
+    bucket_sort(c, KeyDesc{3, ncol, pass, p.seed ^ 0x46A57C1A55E5ULL}, g.n, g.rbeg, g.rend, nullptr, nullptr, nkeys,
+                ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp, nullptr);
+    const int64_t* q = read_i64(h, c, ws.keyoffs, nkeys + 1, &s, "fast classes");
+    if (!q) return s;
+    ho.assign(q, q + nkeys + 1);
   }
   if (event_at(h, ev_colour_done)) cudaEventRecord(h->events[ev_colour_done], c.s);
   // global tables for hubs
@@ -354,9 +439,16 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
         const size_t base = (size_t)cl * kNumBuckets;
         for (int b = 0; b < kNumBuckets; b++) {
           const int64_t cnt = ho[base + b + 1] - ho[base + b];
-          if (cnt > 0) move_bucket<M>(c, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
+          if (cnt <= 0) continue;
+          const int pm = prof_begin(h, c);
+          move_bucket<M>(c, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
+          prof_end(h, c, kLm0 + b, pm);
         }
-        if (det) move_apply<M>(c, st, ws.perm + ho[base], ho[base + kNumBuckets] - ho[base]);
+        if (det) {
+          const int pm = prof_begin(h, c);
+          move_apply<M>(c, st, ws.perm + ho[base], ho[base + kNumBuckets] - ho[base]);
+          prof_end(h, c, kApply, pm);
+        }
       }
       move_finish<M>(c, ws.ctrl);
     }
@@ -389,7 +481,7 @@ louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typenam
   // communities by total-degree bucket
   if ((s = ensure_keys(h, kNumBuckets)) != LOUVAIN_OK) return s;
   cudaMemsetAsync(&ws.ctrl->cnt[6], 0, sizeof(unsigned long long), c.s);
-  bucket_sort(c, 2, nc, nullptr, nullptr, nullptr, ws.cdeg, kNumBuckets, ws.cperm, ws.keyoffs, ws.keycur, ws.tile_tmp,
+  bucket_sort(c, KeyDesc{2, 1, 0, 0}, nc, nullptr, nullptr, nullptr, ws.cdeg, kNumBuckets, ws.cperm, ws.keyoffs, ws.keycur, ws.tile_tmp,
               &ws.ctrl->cnt[6]);
   const int64_t* q = read_i64(h, c, ws.keyoffs, kNumBuckets + 1, &s, "community buckets");
   if (!q) return s;
@@ -403,7 +495,12 @@ louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typenam
   MergeArgs<M> a;
   a.g = g; a.Cp = ws.Cp; a.coff = ws.coff; a.cverts = ws.cverts; a.cdeg = ws.cdeg; a.hoff = rs.hoff; a.hend = rs.hend;
   a.otg = otg_holey; a.ow = ow_holey; a.nc = nc; a.ctrl = ws.ctrl;
-  for (int b = 0; b < kNumBuckets; b++) merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.gt);
+  for (int b = 0; b < kNumBuckets; b++) {
+    if (cb[b + 1] - cb[b] <= 0) continue;
+    const int pm = prof_begin(h, c);
+    merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.gt);
+    prof_end(h, c, kMg0 + b, pm);
+  }
   return LOUVAIN_OK;
 }
 
@@ -489,7 +586,9 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
       if (p.compact) {
         row_lengths(c, nc, rs.hoff, rs.hend, ws.len);
         scan_exclusive_i64(c, ws.len, rs.doff, nc, ws.tile_tmp);
+        const int pm = prof_begin(h, c);
         compact_rows<W>(c, nc, rs.hoff, rs.hend, rs.doff, htg, hw, ws.tgB, reinterpret_cast<W*>(ws.wB));
+        prof_end(h, c, kCompact, pm);
         g = GraphView<W>{nc, rs.doff, rs.doff + 1, ws.tgB, reinterpret_cast<W*>(ws.wB)};
         const int64_t* t = read_i64(h, c, rs.doff + nc, 1, &s, "compaction");
         if (!t) return s;
@@ -516,10 +615,13 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
   scan_exclusive_i32(c, ws.occ, ws.newid, g.n, ws.tile_tmp);
   relabel(c, C, n, ws.newid);
   // (a10) Eq. 1 on the input graph
+  const int pm = prof_begin(h, c);
   modularity<M>(c, g0, C, reinterpret_cast<A*>(ws.tot), ws.ctrl);
+  prof_end(h, c, kModularity, pm);
   const Ctrl* hc = read_ctrl(h, c, &s, "final modularity");
   if (!hc) return s;
   if (hc->error) return set_err(h, LOUVAIN_ERR_CUDA, "internal: hash table overflow");
+  prof_finish(h, *hc);
   out->q = hc->q;
   const int64_t* q = read_i64(h, c, ws.newid + g.n, 1, &s, "final communities");
   if (!q) return s;
@@ -586,6 +688,8 @@ louvain_status louvain_default_params(louvain_params* p) {
   p->validate = 1;
   p->compact = 1;
   p->pass_modularity = 0;
+  p->profile = 0;
+  p->fast_classes = 16;
   return LOUVAIN_OK;
 }
 
@@ -620,6 +724,7 @@ void louvain_destroy(louvain_handle h) {
   free_all(h->ws.gt_alloc);
   free_all(h->ws.in_alloc);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
   if (h->pin) cudaFreeHost(h->pin);
   delete h;
 }
@@ -641,6 +746,10 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
   c.num_sms = h->num_sms;
   if (res) std::memset(res, 0, sizeof(*res));
   if (n_stats) *n_stats = 0;
+  h->prof.on = p->profile != 0;
+  h->prof.used = 0;
+  h->prof.recs.clear();
+  h->prof.valid = false;
   if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
   if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
   if (!event_at(h, 0)) return set_err(h, LOUVAIN_ERR_CUDA, "event creation failed");
@@ -784,6 +893,7 @@ louvain_status louvain_local_move(louvain_handle h, int64_t n, int64_t n_arcs, c
                                   const louvain_params* p, int32_t pass, double tau, void* stream, int32_t* d_cprime,
                                   int32_t* iterations, int64_t* moves) {
   louvain_status s = begin_call(h);
+  h->prof.on = false;
   if (s != LOUVAIN_OK) return s;
   if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
   if (!valid_params(p) || !iterations || !moves || (n > 0 && !d_cprime) || tau < 0.0)
@@ -827,6 +937,7 @@ louvain_status louvain_aggregate(louvain_handle h, int64_t n, int64_t n_arcs, co
                                  const int32_t* d_membership, int64_t n_comm, void* stream, int64_t* d_out_offsets,
                                  int32_t* d_out_targets, void* d_out_weights, int64_t* out_arcs) {
   louvain_status s = begin_call(h);
+  h->prof.on = false;
   if (s != LOUVAIN_OK) return s;
   if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
   if (n_comm < 0 || n_comm > n || !d_out_offsets || !out_arcs || (n > 0 && !d_membership) ||
@@ -870,6 +981,24 @@ louvain_status louvain_aggregate(louvain_handle h, int64_t n, int64_t n_arcs, co
     return LOUVAIN_OK;
   };
   return fp ? body(FpMode()) : body(IntMode());
+}
+
+louvain_status louvain_kernel_profile(louvain_handle h, louvain_kernel_stat* out, int32_t cap, int32_t* n) {
+  if (!h || !n || (cap > 0 && !out)) return LOUVAIN_ERR_INVALID;
+  *n = 0;
+  if (!h->prof.valid) return set_err(h, LOUVAIN_ERR_INVALID, "no profiled run (set params.profile = 1)");
+  int32_t k = 0;
+  for (int cls = 0; cls < kNumClasses && k < cap; cls++) {
+    if (h->prof.launches[cls] == 0) continue;
+    std::memset(&out[k], 0, sizeof(out[k]));
+    std::strncpy(out[k].name, kClassNames[cls], sizeof(out[k].name) - 1);
+    out[k].launches = h->prof.launches[cls];
+    out[k].ms = h->prof.ms[cls];
+    out[k].algorithmic_bytes = h->prof.bytes[cls];
+    k++;
+  }
+  *n = k;
+  return LOUVAIN_OK;
 }
 
 louvain_status louvain_exclusive_scan(louvain_handle h, const int64_t* d_in, int64_t* d_out, int64_t count,

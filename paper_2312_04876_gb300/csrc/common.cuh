@@ -44,7 +44,32 @@ struct Ctrl {
   long long acc_i[4];                 // general integer accumulators
   double acc_f[4];                    // general fp accumulators
   double q;                           // last modularity
+  // algorithmic-traffic counters, summed over a run (reset by the host before each run)
+  unsigned long long lm_stat[kNumBuckets][6];  // local move: list entries, vertices processed, arcs
+                                                // scanned, candidates scored, moves, neighbour marks
+  unsigned long long mg_stat[kNumBuckets][4];  // merge: communities, members, arcs scanned, arcs written
 };
+
+// Adds K per-thread counters of a whole block to dst[0..K) (one atomic per counter per block).
+// Every thread of the block must call it.
+template <int K>
+__device__ __forceinline__ void block_add_counters(unsigned long long* dst, unsigned long long (&v)[K]) {
+  __shared__ unsigned long long part[K][32];
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < K; k++) part[k][threadIdx.x >> 5] = v[k];
+  __syncthreads();
+  if (threadIdx.x < K) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[threadIdx.x][w];
+    if (t) atomicAdd(&dst[threadIdx.x], t);
+  }
+}
 
 enum CtrlErr : int32_t { kErrTableFull = 1, kErrTimeout = 2, kErrRange = 4 };
 

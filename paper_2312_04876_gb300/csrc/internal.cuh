@@ -43,12 +43,21 @@ void scan_exclusive_i32(Ctx& c, const int32_t* in, int64_t* out, int64_t n, int6
 void fill_i32(Ctx& c, int32_t* p, int32_t v, int64_t n);
 void iota_i32(Ctx& c, int32_t* p, int64_t n);
 
+// Sort key of bucket_sort: kind 0 degree bucket; 1 colour[i] * kNumBuckets + bucket; 2 degree bucket
+// of deg64[i]; 3 (hash3(seed, pass, i) % classes) * kNumBuckets + bucket.
+struct KeyDesc {
+  int kind = 0;
+  int classes = 1;
+  int pass = 0;
+  uint64_t seed = 0;
+};
+
 // Counting sort of vertex ids by key.  key_kind 0: degree bucket of (rend - rbeg); 1: colour *
 // kNumBuckets + degree bucket; 2: degree bucket of deg64[i].  Vertices with a negative key are
 // left out.  hist must hold nkeys + 1 int64; cursor nkeys int32.  Writes perm and offsets[nkeys+1]
 // (device).
 // max_deg (device, optional) receives the largest row length / deg64 value seen (atomicMax).
-void bucket_sort(Ctx& c, int key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
+void bucket_sort(Ctx& c, KeyDesc key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
                  const int64_t* deg64, int64_t nkeys, int32_t* perm, int64_t* offsets, int32_t* cursor,
                  int64_t* tile_tmp, unsigned long long* max_deg);
 
@@ -139,6 +148,7 @@ struct MergeArgs {
   typename M::w_t* ow;
   int64_t nc;
   Ctrl* ctrl;
+  int bucket = 0;  // set by merge_bucket (selects the traffic counters)
 };
 template <class M>
 void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt);

@@ -28,6 +28,7 @@ struct LmArgs {
   int glog;
   int fast;
   int pruning;
+  int bucket;
 };
 
 // Block-wide reduction of the per-thread move accumulators into the control block.
@@ -103,10 +104,12 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
   const int64_t n_cur = a.g.n;
   unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
   double acc_f = 0.0;
+  unsigned long long ctr[6] = {0, 0, 0, 0, 0, 0};  // list, processed, arcs, candidates, moves, marks
 
   const int64_t ngroups = (int64_t)gridDim.x * GPB;
   for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < a.count; idx += ngroups) {
     const int32_t i = a.list[idx];
+    if (lane == 0) ctr[0]++;
     if (a.pruning) {
       int f = 0;
       if (lane == 0) {
@@ -119,6 +122,7 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
     const int64_t beg = a.g.rbeg[i], end = a.g.rend[i];
     const int64_t deg = end - beg;
     const int32_t d = a.st.Cp[i];
+    if (lane == 0) { ctr[1]++; ctr[2] += (unsigned long long)deg; }
     int lg;
     if (GLOBAL) lg = tbl_log2(deg < n_cur ? deg : n_cur, 6, a.glog);
     else lg = tbl_log2(deg, 1, LOG);
@@ -151,6 +155,7 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
         const H v = tv[s];
         tk[s] = kEmpty;
         tv[s] = H(0);
+        ctr[3]++;
         const S sc = M::score(v, kid, ki, a.st.Sig[c], sd, two_m);
         if (better(sc, c, best, bc)) { best = sc; bc = c; }
       }
@@ -186,15 +191,17 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
           if (acc_lo < b) acc_hi++;
         }
         acc_mv++;
+        ctr[4]++;
       }
       if (a.pruning)
         for (int64_t e = beg + lane; e < end; e += G) {
           const int32_t j = a.g.tg[e];
-          if (j != i) a.st.flags[j] = 1;  // mark neighbours as unprocessed
+          if (j != i) { a.st.flags[j] = 1; ctr[5]++; }  // mark neighbours as unprocessed
         }
     }
   }
   flush_move_acc<M::is_fp>(ctrl, acc_lo, acc_hi, acc_mv, acc_f, r_lo, r_hi, r_mv, r_f);
+  block_add_counters<6>(ctrl->lm_stat[a.bucket], ctr);
 }
 
 template <class M, int G, int LOG, bool GLOBAL>
@@ -216,6 +223,7 @@ void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const 
   while (((int64_t)1 << a.glog) < gt.slots_per_block) a.glog++;
   a.fast = fast ? 1 : 0;
   a.pruning = pruning ? 1 : 0;
+  a.bucket = bucket < kNumBuckets ? bucket : kNumBuckets - 1;
   const int cap = c.num_sms * 16;
   switch (bucket) {
     case 0: launch_lm<M, 4, 3, false>(c, a, cap); break;

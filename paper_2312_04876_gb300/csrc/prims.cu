@@ -126,18 +126,20 @@ void iota_i32(Ctx& c, int32_t* p, int64_t n) {
 }
 
 // ---------------------------------------------------------------- counting sort by key
-__device__ __forceinline__ int sort_key(int kind, int64_t i, const int64_t* rbeg, const int64_t* rend,
+__device__ __forceinline__ int sort_key(KeyDesc kd, int64_t i, const int64_t* rbeg, const int64_t* rend,
                                         const int32_t* colour, const int64_t* deg64) {
-  if (kind == 2) return degree_bucket(deg64[i]);
+  if (kd.kind == 2) return degree_bucket(deg64[i]);
   int b = degree_bucket(rend[i] - rbeg[i]);
-  if (kind == 0 || b < 0) return b;
+  if (kd.kind == 0 || b < 0) return b;
+  if (kd.kind == 3)  // hash class of the fast schedule
+    return (int)(hash3(kd.seed, (uint64_t)kd.pass, (uint64_t)i) % (uint64_t)kd.classes) * kNumBuckets + b;
   return colour[i] * kNumBuckets + b;
 }
 
 constexpr int kSmemKeys = 4096;
 
 // Histogram of keys; block-local shared histograms when the key space is small.
-__global__ void __launch_bounds__(kBlock) k_key_hist(int kind, int64_t n, const int64_t* rbeg, const int64_t* rend,
+__global__ void __launch_bounds__(kBlock) k_key_hist(KeyDesc kind, int64_t n, const int64_t* rbeg, const int64_t* rend,
                                                      const int32_t* colour, const int64_t* deg64, int64_t nkeys,
                                                      int64_t* hist, unsigned long long* max_deg) {
   __shared__ int32_t sh[kSmemKeys];
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(int kind, int64_t n, const 
   }
   long long mx = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const long long dg = kind == 2 ? deg64[i] : rend[i] - rbeg[i];
+    const long long dg = kind.kind == 2 ? deg64[i] : rend[i] - rbeg[i];
     mx = dg > mx ? dg : mx;
     int k = sort_key(kind, i, rbeg, rend, colour, deg64);
     if (k < 0) continue;
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(int kind, int64_t n, const 
 
 // Scatter: each block reserves a range per key (one global atomic per key per block), then
 // ranks its own elements inside it.  Small key spaces only; large ones use one atomic per element.
-__global__ void __launch_bounds__(kBlock) k_key_scatter(int kind, int64_t n, const int64_t* rbeg, const int64_t* rend,
+__global__ void __launch_bounds__(kBlock) k_key_scatter(KeyDesc kind, int64_t n, const int64_t* rbeg, const int64_t* rend,
                                                         const int32_t* colour, const int64_t* deg64, int64_t nkeys,
                                                         const int64_t* offsets, int32_t* cursor, int32_t* perm) {
   __shared__ int32_t cnt[kSmemKeys];
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(kBlock) k_key_scatter(int kind, int64_t n, con
   }
 }
 
-void bucket_sort(Ctx& c, int key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
+void bucket_sort(Ctx& c, KeyDesc key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
                  const int64_t* deg64, int64_t nkeys, int32_t* perm, int64_t* offsets, int32_t* cursor,
                  int64_t* tile_tmp, unsigned long long* max_deg) {
   cudaMemsetAsync(offsets, 0, (size_t)(nkeys + 1) * sizeof(int64_t), c.s);

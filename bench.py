@@ -159,6 +159,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--mode", default="fast", choices=["fast", "deterministic"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--fast-classes", type=int, default=None, help="random vertex classes of the fast schedule")
+    ap.add_argument("--compact", type=int, default=None, help="1: compact super-vertex graphs, 0: keep holey CSR")
+    ap.add_argument("--ncu-window", action="store_true",
+                    help="after warm-up run ONE step between cudaProfilerStart/Stop and exit (for ncu "
+                         "--profile-from-start off); prints no bench line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -181,13 +186,27 @@ def main():
     tg = torch.from_numpy(g.targets).to(dev)
     w = torch.from_numpy(g.weights).to(dev)
     L = lv.Louvain(local)
-    params = lv.default_params(mode=args.mode, validate=0)
+    knobs = {}
+    if args.fast_classes is not None:
+        knobs["fast_classes"] = args.fast_classes
+    if args.compact is not None:
+        knobs["compact"] = args.compact
+    params = lv.default_params(mode=args.mode, validate=0, **knobs)
     mem = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
         L.run(offs, tg, w, params, membership=mem)
     torch.cuda.synchronize()
+
+    if args.ncu_window:
+        torch.cuda.profiler.start()
+        _, r = L.run(offs, tg, w, params, membership=mem)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"ncu_window": True, "workload": args.workload, "mode": args.mode,
+                          "kernel_launches": r.kernel_launches, "modularity": r.modularity}))
+        return 0
 
     def barrier():
         if ws > 1:
@@ -240,12 +259,32 @@ def main():
                "h2d_bytes_per_step": int(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes),
                "d2h_bytes_per_step": int(4 * g.n), "steps": k2}
 
+    # per-kernel device time (CUDA events around every launch on the run's stream) and algorithmic
+    # bytes (device counters), from a profiled repeat of the timed steps
+    pparams = lv.default_params(mode=args.mode, validate=0, profile=1, **knobs)
+    agg = {}
+    for _ in range(args.steps):
+        L.run(offs, tg, w, pparams, membership=mem)
+        for k in L.kernel_profile():
+            a = agg.setdefault(k["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            a["launches"] += k["launches"]
+            a["ms"] += k["ms"]
+            a["bytes"] += k["bytes"]
     if rank != 0:
         return 0
     peak, peak_kind = peaks()
-    s0 = last.stats[0] if last.stats else {}
+    kernels = []
+    for name, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"]):
+        gbs = a["bytes"] / (a["ms"] * 1e6) if a["ms"] > 0 and a["bytes"] > 0 else None
+        kernels.append({"name": name, "launches_per_step": a["launches"] / args.steps,
+                        "ms_per_step": a["ms"] / args.steps, "gbs": gbs})
+    dom = next((k for k in kernels if k["gbs"] is not None), None)
     roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
             "peak_kind": peak_kind}
+    if dom:
+        roof.update({"kernel": dom["name"], "achieved": dom["gbs"], "frac": dom["gbs"] / peak,
+                     "algorithmic_bytes_per_launch": agg[dom["name"]]["bytes"] / max(1, agg[dom["name"]]["launches"]),
+                     "avg_launch_ms": agg[dom["name"]]["ms"] / max(1, agg[dom["name"]]["launches"])})
     line = {
         "metric": "louvain_edges_per_second", "value": value, "unit": "edges/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -256,7 +295,7 @@ def main():
         "modularity": last.modularity, "passes": last.passes, "iterations": last.total_iterations,
         "communities": last.n_communities, "gpu_launches": launches,
         "pass_ms": [{k: round(v, 3) if isinstance(v, float) else v for k, v in s.items()} for s in last.stats],
-        "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+        "roofline": roof, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
   typedef typename M::h_t H;
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
   constexpr int SL = GLOBAL ? 1 : (1 << LOG);
-  __shared__ int32_t skeys[GPB * SL];
-  __shared__ H svals[GPB * SL];
+  extern __shared__ __align__(16) unsigned char mg_dyn[];  // GPB tables of SL (key, value) slots
+  int32_t* skeys = reinterpret_cast<int32_t*>(mg_dyn);
+  H* svals = reinterpret_cast<H*>(mg_dyn + sizeof(int32_t) * GPB * SL);
   __shared__ unsigned long long s_cnt;
   const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
   const unsigned lane = Grp<G>::lane();
@@ -199,9 +200,12 @@ template <class M, int G, int LOG, bool GLOBAL>
 static void launch_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt,
                          int max_blocks) {
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  constexpr size_t smem = (size_t)GPB * (GLOBAL ? 1 : (1 << LOG)) * (sizeof(int32_t) + sizeof(typename M::h_t));
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(merge_kernel<M, G, LOG, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int glog = 0;
   while (((int64_t)1 << glog) < gt.slots_per_block) glog++;
-  merge_kernel<M, G, LOG, GLOBAL><<<grid_for(count, GPB, max_blocks), kBlock, 0, c.s>>>(
+  merge_kernel<M, G, LOG, GLOBAL><<<grid_for(count, GPB, max_blocks), kBlock, smem, c.s>>>(
       a, list, count, gt.keys, reinterpret_cast<typename M::h_t*>(gt.vals), gt.slots_per_block, glog);
   c.launches++;
 }
@@ -218,7 +222,8 @@ void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& args, const int32_t* l
     case 1: launch_merge<M, 8, 5, false>(c, a, list, count, gt, cap); break;
     case 2: launch_merge<M, 32, 8, false>(c, a, list, count, gt, cap); break;
     case 3: launch_merge<M, 256, 12, false>(c, a, list, count, gt, cap); break;
-    default: launch_merge<M, 256, 0, true>(c, a, list, count, gt, gt.blocks > 0 ? gt.blocks : 1); break;
+    case 4: launch_merge<M, 256, 13, false>(c, a, list, count, gt, cap); break;
+    default: break;  // giant communities go through giant_merge
   }
 }
 
@@ -278,6 +283,53 @@ void compact_rows(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, c
   k_compact<W><<<grid_for(n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(n, hbeg, hend, doff, itg, iw, otg, ow);
   c.launches++;
 }
+
+// Bucketed compaction: one group of G lanes copies one holey row (rows listed by the community
+// total-degree buckets of the merge, which bound the row lengths); giant rows go by chunks.
+template <class W, int G>
+__global__ void __launch_bounds__(kBlock) k_compact_group(const int32_t* list, int64_t count, const int64_t* hbeg,
+                                                          const int64_t* hend, const int64_t* doff,
+                                                          const int32_t* itg, const W* iw, int32_t* otg, W* ow) {
+  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
+  const unsigned lane = Grp<G>::lane();
+  for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
+    const int32_t r = list[idx];
+    const int64_t b = hbeg[r], len = hend[r] - b, d = doff[r];
+    for (int64_t k = lane; k < len; k += G) {
+      otg[d + k] = itg[b + k];
+      ow[d + k] = iw[b + k];
+    }
+  }
+}
+
+template <class W>
+void compact_bucketed(Ctx& c, const int32_t* cperm, const int64_t* cb, const int64_t* hbeg, const int64_t* hend,
+                      const int64_t* doff, const int32_t* itg, const W* iw, int32_t* otg, W* ow, const GiantPlan& gp,
+                      Ctrl* ctrl) {
+  const int cap = c.num_sms * 16;
+  for (int b = 0; b < kNumBuckets; b++) {
+    const int64_t cnt = cb[b + 1] - cb[b];
+    if (cnt <= 0) continue;
+    const int32_t* l = cperm + cb[b];
+    switch (b) {
+      case 0: k_compact_group<W, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
+      case 1: k_compact_group<W, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
+      case 2: k_compact_group<W, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
+      case 3:
+      case 4: k_compact_group<W, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
+      default: giant_compact<W>(c, l, cnt, hbeg, hend, doff, itg, iw, otg, ow, gp, ctrl); c.launches--; break;
+    }
+    c.launches++;
+  }
+}
+
+template void compact_bucketed<int32_t>(Ctx&, const int32_t*, const int64_t*, const int64_t*, const int64_t*,
+                                        const int64_t*, const int32_t*, const int32_t*, int32_t*, int32_t*,
+                                        const GiantPlan&, Ctrl*);
+template void compact_bucketed<float>(Ctx&, const int32_t*, const int64_t*, const int64_t*, const int64_t*,
+                                      const int64_t*, const int32_t*, const float*, int32_t*, float*,
+                                      const GiantPlan&, Ctrl*);
 
 template void merge_bucket<IntMode>(Ctx&, int, const MergeArgs<IntMode>&, const int32_t*, int64_t, const GlobalTable&);
 template void merge_bucket<FpMode>(Ctx&, int, const MergeArgs<FpMode>&, const int32_t*, int64_t, const GlobalTable&);

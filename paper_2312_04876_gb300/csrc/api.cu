@@ -52,6 +52,10 @@ struct Workspace {
   DevAlloc gt_alloc;
   int64_t gt_slots_total = 0;
   GlobalTable gt;
+  int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
+  int64_t* ctab = nullptr;    // [n] table offset of each giant community (-1 otherwise)
+  int32_t* csz = nullptr;     // [n] table size of each giant community
+  GiantPlan gp, gpv;          // plans of giant vertices / communities and of giant members
   DevAlloc in_alloc;
   int64_t in_n = -1, in_a = -1;
   int64_t* in_offs = nullptr;
@@ -73,9 +77,9 @@ enum KClass {
   kNumClasses
 };
 static const char* const kClassNames[kNumClasses] = {
-    "local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "local_move_b3_block", "local_move_b4_global",
-    "sigma_apply", "merge_b0_g4", "merge_b1_g8", "merge_b2_warp", "merge_b3_block", "merge_b4_global",
-    "compact", "colour_jp", "modularity"};
+    "local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "local_move_b3_block4k", "local_move_b4_block8k",
+    "local_move_b5_giant", "sigma_apply", "merge_b0_g4", "merge_b1_g8", "merge_b2_warp", "merge_b3_block4k",
+    "merge_b4_block8k", "merge_b5_giant", "compact", "colour_jp", "modularity"};
 
 struct Profile {
   bool on = false;
@@ -169,7 +173,21 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
        dalloc(h, d, &ws.cperm, n1) && dalloc(h, d, &ws.occ, n1) && dalloc(h, d, &ws.counts, n1) &&
        dalloc(h, d, &ws.cursor, n1) && dalloc(h, d, &ws.cverts, n1) && dalloc(h, d, &ws.jcnt, n1) &&
        dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.tmp_mem, n1);
-  ok = ok && dalloc(h, d, &ws.flags, n1);
+  ok = ok && dalloc(h, d, &ws.flags, n1) && dalloc(h, d, &ws.dperm, n1) && dalloc(h, d, &ws.ctab, n1) &&
+       dalloc(h, d, &ws.csz, n1);
+  // giant plans: at most A / 2049 rows exceed 2048 arcs; tables of <= 4 x the arcs in 4096-slot slices
+  // giant rows have > 4096 arcs: at most A / 4097 of them; chunks of 2048 arcs over their rows:
+  // <= gcap + A / 2048; slices of 128 slots over tables of < 4 x the arcs: <= gcap + A / 32
+  const int64_t gcap = ac / 4096 + 16, scap = gcap + ac / 32 + 16, ccap = gcap + ac / 2048 + 16;
+  for (GiantPlan* gp : {&ws.gp, &ws.gpv})
+    ok = ok && dalloc(h, d, &gp->chunk_off, gcap + 1) && dalloc(h, d, &gp->tab_off, gcap + 1) &&
+         dalloc(h, d, &gp->slice_off, gcap + 1) && dalloc(h, d, (int32_t**)&gp->kid, gcap) &&
+         dalloc(h, d, &gp->moved, gcap) && dalloc(h, d, (long long**)&gp->part_s, scap) &&
+         dalloc(h, d, &gp->part_c, scap) && dalloc(h, d, &gp->cowner, ccap) && dalloc(h, d, &gp->sowner, scap);
+  for (GiantPlan* gp : {&ws.gp, &ws.gpv}) {
+    gp->chunk_cap = ccap;
+    gp->slice_cap = scap;
+  }
   ok = ok && dalloc(h, d, &ws.newid, n1 + 1) && dalloc(h, d, &ws.coff, n1 + 1) && dalloc(h, d, &ws.cdeg, n1 + 1) &&
        dalloc(h, d, &ws.len, n1 + 1) && dalloc(h, d, &ws.jrc, n1 + 16) &&
        dalloc(h, d, &ws.tile_tmp, scan_tmp_elems((int64_t)kNumBuckets * n1 + 8) + 8);  // class sort scans 5 n keys
@@ -201,24 +219,18 @@ louvain_status ensure_keys(louvain_handle h, int64_t nkeys) {
   return ensure_pinned(h, (size_t)(cap + 1) * sizeof(int64_t) + 4096);
 }
 
-// Global-memory hash tables for the largest bucket: `slots` per block for up to `want_blocks`.
-louvain_status ensure_gtable(louvain_handle h, Ctx& c, int64_t max_distinct, int64_t want_blocks) {
+// Shared pool of global-memory hash tables for the giant rows (all-empty between uses).
+louvain_status ensure_pool(louvain_handle h, Ctx& c, int64_t slots) {
   Workspace& ws = h->ws;
-  int64_t slots = 64;
-  while (slots < 2 * max_distinct) slots <<= 1;
-  int64_t blocks = want_blocks < (int64_t)c.num_sms * 4 ? want_blocks : (int64_t)c.num_sms * 4;
-  const int64_t limit = ((int64_t)1 << 31) / 8;  // at most 2 GiB of table slots in total
-  if (blocks * slots > limit) blocks = limit / slots > 0 ? limit / slots : 1;
-  if (blocks < 1) blocks = 1;
-  if (slots * blocks > ws.gt_slots_total) {
+  if (slots > ws.gt_slots_total) {
     free_all(ws.gt_alloc);
     ws.gt_slots_total = 0;
-    int64_t total = slots * blocks;
+    const int64_t total = slots + slots / 4 + 4096;
     int32_t* k = nullptr;
     int32_t* v = nullptr;
     if (!dalloc(h, ws.gt_alloc, &k, total) || !dalloc(h, ws.gt_alloc, &v, total)) {
       free_all(ws.gt_alloc);
-      return set_err(h, LOUVAIN_ERR_OOM, "global hash-table allocation failed");
+      return set_err(h, LOUVAIN_ERR_OOM, "giant hash-table pool allocation failed");
     }
     cudaMemsetAsync(k, 0xFF, (size_t)total * 4, c.s);
     cudaMemsetAsync(v, 0, (size_t)total * 4, c.s);
@@ -226,8 +238,11 @@ louvain_status ensure_gtable(louvain_handle h, Ctx& c, int64_t max_distinct, int
     ws.gt.vals = v;
     ws.gt_slots_total = total;
   }
-  ws.gt.slots_per_block = slots;
-  ws.gt.blocks = (int)blocks;
+  for (GiantPlan* gp : {&ws.gp, &ws.gpv}) {
+    gp->keys = ws.gt.keys;
+    gp->vals = ws.gt.vals;
+    gp->pool_slots = ws.gt_slots_total;
+  }
   return LOUVAIN_OK;
 }
 
@@ -362,22 +377,23 @@ louvain_status colour_failure(louvain_handle h) {
   return set_err(h, LOUVAIN_ERR_CUDA, buf);
 }
 
-// Per-pass degree buckets of graph g into ws.perm with host offsets hb[kNumBuckets + 1].
+// Per-pass degree buckets of graph g into ws.dperm with host offsets hb[kNumBuckets + 1];
+// *giant_slots = table slots its giant vertices need.
 template <class W>
 louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, int64_t hb[kNumBuckets + 1],
-                              int64_t* max_deg) {
+                              int64_t* giant_slots) {
   Workspace& ws = h->ws;
   louvain_status st = ensure_keys(h, kNumBuckets);
   if (st != LOUVAIN_OK) return st;
-  cudaMemsetAsync(&ws.ctrl->cnt[6], 0, sizeof(unsigned long long), c.s);
-  bucket_sort(c, KeyDesc{0, 1, 0, 0}, g.n, g.rbeg, g.rend, nullptr, nullptr, kNumBuckets, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
-              &ws.ctrl->cnt[6]);
+  cudaMemsetAsync(&ws.ctrl->gslots, 0, sizeof(unsigned long long), c.s);
+  bucket_sort(c, KeyDesc{0, 1, 0, 0}, g.n, g.rbeg, g.rend, nullptr, nullptr, kNumBuckets, ws.dperm, ws.keyoffs,
+              ws.keycur, ws.tile_tmp, nullptr, &ws.ctrl->gslots, g.n);
   const int64_t* p = read_i64(h, c, ws.keyoffs, kNumBuckets + 1, &st, "degree buckets");
   if (!p) return st;
   for (int b = 0; b <= kNumBuckets; b++) hb[b] = p[b];
   const Ctrl* hc = read_ctrl(h, c, &st, "degree buckets");
   if (!hc) return st;
-  *max_deg = (int64_t)hc->cnt[6];
+  *giant_slots = (int64_t)hc->gslots;
   return LOUVAIN_OK;
 }
 
@@ -385,7 +401,7 @@ louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, i
 // Fills *li and *moves.  Deterministic mode colours g first.
 template <class M>
 louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const int64_t hb[],
-                                int64_t max_deg, const louvain_params& p, int32_t pass, double tau, int32_t* li,
+                                int64_t giant_slots, const louvain_params& p, int32_t pass, double tau, int32_t* li,
                                 int64_t* moves, size_t ev_colour_done) {
   Workspace& ws = h->ws;
   PassState<M> st{reinterpret_cast<typename M::a_t*>(ws.K), reinterpret_cast<typename M::a_t*>(ws.Sig), ws.Cp,
@@ -400,7 +416,7 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
     cudaError_t ce;
     const int pm = prof_begin(h, c);
-    ncol = jp_colour(c, gs, ws.perm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce);
+    ncol = jp_colour(c, gs, ws.dperm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce);
     prof_end(h, c, kColour, pm);
     if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
     if (ncol < 0) return colour_failure(h);
@@ -423,12 +439,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     ho.assign(q, q + nkeys + 1);
   }
   if (event_at(h, ev_colour_done)) cudaEventRecord(h->events[ev_colour_done], c.s);
-  // global tables for hubs
-  int64_t n_hub = 0;
-  for (int k = 0; k < ncol; k++) n_hub += ho[(size_t)k * kNumBuckets + 5] - ho[(size_t)k * kNumBuckets + 4];
-  if (n_hub > 0) {
-    if ((s = ensure_gtable(h, c, max_deg < g.n ? max_deg : g.n, n_hub)) != LOUVAIN_OK) return s;
-  }
+  // table pool for the giant vertices (each class uses it from its start; tables are cleared)
+  if (giant_slots > 0 && (s = ensure_pool(h, c, giant_slots)) != LOUVAIN_OK) return s;
   move_setup(c, ws.ctrl, tau, p.max_iterations);
   const bool pruning = p.pruning != 0;
   int enq = 0;
@@ -441,7 +453,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
           const int64_t cnt = ho[base + b + 1] - ho[base + b];
           if (cnt <= 0) continue;
           const int pm = prof_begin(h, c);
-          move_bucket<M>(c, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
+          if (b < kNumBuckets - 1) move_bucket<M>(c, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
+          else giant_move<M>(c, g, st, ws.perm + ho[base + b], cnt, ws.gp, !det, pruning);
           prof_end(h, c, kLm0 + b, pm);
         }
         if (det) {
@@ -464,8 +477,9 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
 }
 
 template <class M>
-louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, int64_t nc,
-                               RowSet& rs, int32_t* otg_holey, typename M::w_t* ow_holey) {
+louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const int64_t* hb,
+                               int64_t nc, RowSet& rs, int32_t* otg_holey, typename M::w_t* ow_holey,
+                               int64_t* cb_out) {
   Workspace& ws = h->ws;
   louvain_status s;
   // community-vertex CSR (countCommunityVertices, exclusiveScan, atomic fill)
@@ -480,25 +494,25 @@ louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typenam
   cudaMemcpyAsync(rs.hend, rs.hoff, (size_t)nc * sizeof(int64_t), cudaMemcpyDeviceToDevice, c.s);
   // communities by total-degree bucket
   if ((s = ensure_keys(h, kNumBuckets)) != LOUVAIN_OK) return s;
-  cudaMemsetAsync(&ws.ctrl->cnt[6], 0, sizeof(unsigned long long), c.s);
-  bucket_sort(c, KeyDesc{2, 1, 0, 0}, nc, nullptr, nullptr, nullptr, ws.cdeg, kNumBuckets, ws.cperm, ws.keyoffs, ws.keycur, ws.tile_tmp,
-              &ws.ctrl->cnt[6]);
+  cudaMemsetAsync(&ws.ctrl->gslots, 0, sizeof(unsigned long long), c.s);
+  bucket_sort(c, KeyDesc{2, 1, 0, 0}, nc, nullptr, nullptr, nullptr, ws.cdeg, kNumBuckets, ws.cperm, ws.keyoffs,
+              ws.keycur, ws.tile_tmp, nullptr, &ws.ctrl->gslots, nc);
   const int64_t* q = read_i64(h, c, ws.keyoffs, kNumBuckets + 1, &s, "community buckets");
   if (!q) return s;
   int64_t cb[kNumBuckets + 1];
-  for (int b = 0; b <= kNumBuckets; b++) cb[b] = q[b];
+  for (int b = 0; b <= kNumBuckets; b++) cb[b] = cb_out[b] = q[b];
   const Ctrl* hc = read_ctrl(h, c, &s, "community buckets");
   if (!hc) return s;
-  const int64_t max_cdeg = (int64_t)hc->cnt[6];
-  if (cb[5] - cb[4] > 0)
-    if ((s = ensure_gtable(h, c, max_cdeg < nc ? max_cdeg : nc, cb[5] - cb[4])) != LOUVAIN_OK) return s;
+  const int64_t giant_slots = (int64_t)hc->gslots;
+  if (giant_slots > 0 && (s = ensure_pool(h, c, giant_slots)) != LOUVAIN_OK) return s;
   MergeArgs<M> a;
   a.g = g; a.Cp = ws.Cp; a.coff = ws.coff; a.cverts = ws.cverts; a.cdeg = ws.cdeg; a.hoff = rs.hoff; a.hend = rs.hend;
   a.otg = otg_holey; a.ow = ow_holey; a.nc = nc; a.ctrl = ws.ctrl;
   for (int b = 0; b < kNumBuckets; b++) {
     if (cb[b + 1] - cb[b] <= 0) continue;
     const int pm = prof_begin(h, c);
-    merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.gt);
+    if (b < kNumBuckets - 1) merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.gt);
+    else giant_merge<M>(c, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.dperm, hb, ws.csz, ws.gp, ws.gpv);
     prof_end(h, c, kMg0 + b, pm);
   }
   return LOUVAIN_OK;
@@ -528,11 +542,11 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
     cudaEventRecord(h->events[e0], c.s);
     const int64_t n_cur = g.n;
     // (a1) pass init: buckets, K' / Sigma' / C' / flags
-    int64_t hb[kNumBuckets + 1], max_deg = 0;
-    if ((s = degree_buckets(h, c, g, hb, &max_deg)) != LOUVAIN_OK) return s;
+    int64_t hb[kNumBuckets + 1], gslots = 0;
+    if ((s = degree_buckets(h, c, g, hb, &gslots)) != LOUVAIN_OK) return s;
     if (lp == 0) {
       vertex_init<M>(c, st, n_cur, false);
-      row_sums<M>(c, g, ws.perm, hb, st.K, st.Sig, reinterpret_cast<A*>(ws.K0));
+      row_sums<M>(c, g, ws.dperm, hb, st.K, st.Sig, reinterpret_cast<A*>(ws.K0));
       total_weight<M>(c, st.K, n_cur, ws.ctrl);
       const Ctrl* hc = read_ctrl(h, c, &s, "pass init");
       if (!hc) return s;
@@ -545,7 +559,7 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
     // (a2-a5) local-moving phase
     int32_t li = 0;
     int64_t moves = 0;
-    if ((s = local_move_phase<M>(h, c, g, hb, max_deg, p, lp, tau, &li, &moves, e0 + 2)) != LOUVAIN_OK) return s;
+    if ((s = local_move_phase<M>(h, c, g, hb, gslots, p, lp, tau, &li, &moves, e0 + 2)) != LOUVAIN_OK) return s;
     cudaEventRecord(h->events[e0 + 3], c.s);
     pending = true;
     out->passes = lp + 1;
@@ -582,12 +596,14 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
       int32_t* htg = ws.tgA;
       W* hw = reinterpret_cast<W*>(ws.wA);
       if (!p.compact && (lp & 1)) { htg = ws.tgB; hw = reinterpret_cast<W*>(ws.wB); }
-      if ((s = aggregate_phase<M>(h, c, g, nc, rs, htg, hw)) != LOUVAIN_OK) return s;
+      int64_t cb[kNumBuckets + 1];
+      if ((s = aggregate_phase<M>(h, c, g, hb, nc, rs, htg, hw, cb)) != LOUVAIN_OK) return s;
       if (p.compact) {
         row_lengths(c, nc, rs.hoff, rs.hend, ws.len);
         scan_exclusive_i64(c, ws.len, rs.doff, nc, ws.tile_tmp);
         const int pm = prof_begin(h, c);
-        compact_rows<W>(c, nc, rs.hoff, rs.hend, rs.doff, htg, hw, ws.tgB, reinterpret_cast<W*>(ws.wB));
+        compact_bucketed<W>(c, ws.cperm, cb, rs.hoff, rs.hend, rs.doff, htg, hw, ws.tgB, reinterpret_cast<W*>(ws.wB),
+                            ws.gpv, ws.ctrl);
         prof_end(h, c, kCompact, pm);
         g = GraphView<W>{nc, rs.doff, rs.doff + 1, ws.tgB, reinterpret_cast<W*>(ws.wB)};
         const int64_t* t = read_i64(h, c, rs.doff + nc, 1, &s, "compaction");
@@ -616,7 +632,9 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
   relabel(c, C, n, ws.newid);
   // (a10) Eq. 1 on the input graph
   const int pm = prof_begin(h, c);
-  modularity<M>(c, g0, C, reinterpret_cast<A*>(ws.tot), ws.ctrl);
+  int64_t hb0[kNumBuckets + 1], gs0 = 0;
+  if ((s = degree_buckets(h, c, g0, hb0, &gs0)) != LOUVAIN_OK) return s;
+  modularity_bucketed<M>(c, g0, C, reinterpret_cast<A*>(ws.tot), ws.ctrl, ws.dperm, hb0, ws.gpv);
   prof_end(h, c, kModularity, pm);
   const Ctrl* hc = read_ctrl(h, c, &s, "final modularity");
   if (!hc) return s;
@@ -832,19 +850,24 @@ louvain_status louvain_modularity(louvain_handle h, int64_t n, int64_t n_arcs, c
   Ctx c;
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
-  if ((s = ensure_workspace(h, n, 0)) != LOUVAIN_OK) return s;
+  if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
   const bool fp = wtype == LOUVAIN_W_FP32;
   if ((s = validate_graph(h, c, n, n_arcs, d_offsets, d_targets, d_weights, fp)) != LOUVAIN_OK) return s;
   validate_range(c, d_membership, n, n, h->ws.ctrl);
   const Ctrl* hc = read_ctrl(h, c, &s, "membership range");
   if (!hc) return s;
   if (hc->cnt[5]) return set_err(h, LOUVAIN_ERR_INVALID, "membership id outside [0, n)");
+  int64_t hb[kNumBuckets + 1], gs = 0;
   if (fp) {
     GraphView<float> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const float*>(d_weights)};
-    modularity<FpMode>(c, g, d_membership, reinterpret_cast<double*>(h->ws.tot), h->ws.ctrl);
+    if ((s = degree_buckets(h, c, g, hb, &gs)) != LOUVAIN_OK) return s;
+    modularity_bucketed<FpMode>(c, g, d_membership, reinterpret_cast<double*>(h->ws.tot), h->ws.ctrl, h->ws.dperm, hb,
+                                h->ws.gpv);
   } else {
     GraphView<int32_t> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const int32_t*>(d_weights)};
-    modularity<IntMode>(c, g, d_membership, reinterpret_cast<long long*>(h->ws.tot), h->ws.ctrl);
+    if ((s = degree_buckets(h, c, g, hb, &gs)) != LOUVAIN_OK) return s;
+    modularity_bucketed<IntMode>(c, g, d_membership, reinterpret_cast<long long*>(h->ws.tot), h->ws.ctrl, h->ws.dperm,
+                                 hb, h->ws.gpv);
   }
   hc = read_ctrl(h, c, &s, "modularity");
   if (!hc) return s;
@@ -877,11 +900,11 @@ louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const
   if (!hc) return s;
   if (hc->cnt[5]) return set_err(h, LOUVAIN_ERR_INVALID, "arc target outside [0, n)");
   GraphView<int32_t> g{n, d_offsets, d_offsets + 1, d_targets, nullptr};
-  int64_t hb[kNumBuckets + 1], max_deg;
-  if ((s = degree_buckets(h, c, g, hb, &max_deg)) != LOUVAIN_OK) return s;
+  int64_t hb[kNumBuckets + 1], gslots;
+  if ((s = degree_buckets(h, c, g, hb, &gslots)) != LOUVAIN_OK) return s;
   JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1, h->ws.n_cap + 1, h->ws.jrc};
   cudaError_t ce;
-  int32_t nc = jp_colour(c, g, h->ws.perm, hb, seed, pass, d_colour, jb, ctrl, h->pin, &ce);
+  int32_t nc = jp_colour(c, g, h->ws.dperm, hb, seed, pass, d_colour, jb, ctrl, h->pin, &ce);
   if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
   if (nc < 0) return colour_failure(h);
   *n_colours = nc;
@@ -917,14 +940,14 @@ louvain_status louvain_local_move(louvain_handle h, int64_t n, int64_t n_arcs, c
     GraphView<W> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const W*>(d_weights)};
     PassState<M> st{reinterpret_cast<A*>(ws.K), reinterpret_cast<A*>(ws.Sig), ws.Cp, ws.flags, ws.csize, ws.mv_from,
                     ws.mv_to, ws.ctrl};
-    int64_t hb[kNumBuckets + 1], max_deg;
-    louvain_status r = degree_buckets(h, c, g, hb, &max_deg);
+    int64_t hb[kNumBuckets + 1], gslots;
+    louvain_status r = degree_buckets(h, c, g, hb, &gslots);
     if (r != LOUVAIN_OK) return r;
     vertex_init<M>(c, st, n, false);
-    row_sums<M>(c, g, ws.perm, hb, st.K, st.Sig, reinterpret_cast<A*>(ws.K0));
+    row_sums<M>(c, g, ws.dperm, hb, st.K, st.Sig, reinterpret_cast<A*>(ws.K0));
     total_weight<M>(c, st.K, n, ws.ctrl);
     if (!event_at(h, 3)) return set_err(h, LOUVAIN_ERR_CUDA, "event creation failed");
-    r = local_move_phase<M>(h, c, g, hb, max_deg, *p, pass, tau, iterations, moves, 3);
+    r = local_move_phase<M>(h, c, g, hb, gslots, *p, pass, tau, iterations, moves, 3);
     if (r != LOUVAIN_OK) return r;
     cudaMemcpyAsync(d_cprime, ws.Cp, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.s);
     return sync(h, c, "local move end");
@@ -966,12 +989,16 @@ louvain_status louvain_aggregate(louvain_handle h, int64_t n, int64_t n_arcs, co
     typedef typename M::w_t W;
     GraphView<W> g{n, d_offsets, d_offsets + 1, d_targets, reinterpret_cast<const W*>(d_weights)};
     RowSet& rs = ws.rows[0];
-    louvain_status r = aggregate_phase<M>(h, c, g, n_comm, rs, ws.tgA, reinterpret_cast<W*>(ws.wA));
+    int64_t hb[kNumBuckets + 1], gslots;
+    louvain_status r = degree_buckets(h, c, g, hb, &gslots);
+    if (r != LOUVAIN_OK) return r;
+    int64_t cb[kNumBuckets + 1];
+    r = aggregate_phase<M>(h, c, g, hb, n_comm, rs, ws.tgA, reinterpret_cast<W*>(ws.wA), cb);
     if (r != LOUVAIN_OK) return r;
     row_lengths(c, n_comm, rs.hoff, rs.hend, ws.len);
     scan_exclusive_i64(c, ws.len, d_out_offsets, n_comm, ws.tile_tmp);
-    compact_rows<W>(c, n_comm, rs.hoff, rs.hend, d_out_offsets, ws.tgA, reinterpret_cast<W*>(ws.wA), d_out_targets,
-                    reinterpret_cast<W*>(d_out_weights));
+    compact_bucketed<W>(c, ws.cperm, cb, rs.hoff, rs.hend, d_out_offsets, ws.tgA, reinterpret_cast<W*>(ws.wA),
+                        d_out_targets, reinterpret_cast<W*>(d_out_weights), ws.gpv, ws.ctrl);
     const int64_t* t = read_i64(h, c, d_out_offsets + n_comm, 1, &r, "aggregate total");
     if (!t) return r;
     *out_arcs = t[0];

@@ -56,10 +56,13 @@ struct KeyDesc {
 // kNumBuckets + degree bucket; 2: degree bucket of deg64[i].  Vertices with a negative key are
 // left out.  hist must hold nkeys + 1 int64; cursor nkeys int32.  Writes perm and offsets[nkeys+1]
 // (device).
-// max_deg (device, optional) receives the largest row length / deg64 value seen (atomicMax).
+// max_deg (device, optional) receives the largest row length / deg64 value seen (atomicMax);
+// giant_slots (device, optional) the summed table size of the bucket-4 items, each
+// 2^tbl_log2(min(deg, n_bound), 6, 40).
 void bucket_sort(Ctx& c, KeyDesc key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
                  const int64_t* deg64, int64_t nkeys, int32_t* perm, int64_t* offsets, int32_t* cursor,
-                 int64_t* tile_tmp, unsigned long long* max_deg);
+                 int64_t* tile_tmp, unsigned long long* max_deg, unsigned long long* giant_slots = nullptr,
+                 int64_t n_bound = 0);
 
 // Renumbering (rank among occupied ids): occ[0, n) zeroed then marked from ids[0, m).
 void mark_occupied(Ctx& c, const int32_t* ids, int64_t m, int32_t* occ, int64_t n);
@@ -160,7 +163,56 @@ void compact_rows(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, c
 // len[r] = hend[r] - hbeg[r]
 void row_lengths(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, int64_t* len);
 
+// ---------------------------------------------------------------- giant.cu
+// Plan of the multi-block path for bucket-4 rows: per giant k, ranges [off[k], off[k+1]) of arc
+// chunks, table slots (in the shared pool keys/vals) and table slices.
+struct GiantPlan {
+  int64_t* chunk_off = nullptr;  // [cap + 1]
+  int64_t* tab_off = nullptr;    // [cap + 1]
+  int64_t* slice_off = nullptr;  // [cap + 1]
+  void* kid = nullptr;           // [cap] K_i->d accumulators (h_t)
+  uint8_t* moved = nullptr;      // [cap]
+  void* part_s = nullptr;        // [slice_cap] best score per slice (s_t)
+  int32_t* part_c = nullptr;     // [slice_cap] its community
+  int32_t* cowner = nullptr;     // [chunk_cap] giant of each chunk
+  int32_t* sowner = nullptr;     // [slice_cap] giant of each slice
+  int64_t chunk_cap = 0, slice_cap = 0;
+  int32_t* keys = nullptr;       // shared table pool, all kEmpty between uses
+  void* vals = nullptr;          // (h_t), all zero between uses
+  int64_t pool_slots = 0;
+};
+// Local moving of the giant vertices list[0, m) (one colour / random class).
+template <class M>
+void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t m,
+                const GiantPlan& p, bool fast, bool pruning);
+// Super-vertex rows of the giant communities clist[0, m): members inserted by their degree bucket
+// (dperm / hb of the current graph), giant members by chunks (plan pv).  gix [nc] receives each
+// community's giant index (-1 if not giant).
+template <class M>
+void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m, const int32_t* dperm,
+                 const int64_t* hb, int32_t* gix, const GiantPlan& p, const GiantPlan& pv);
+
+// Chunk-only plan over the rows [rbeg, rend) of list[0, m).
+void giant_chunk_plan(Ctx& c, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
+                      const GiantPlan& p, Ctrl* ctrl);
+template <class M>
+void giant_modularity(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* list, int64_t m, const int32_t* C,
+                      typename M::a_t* tot, const GiantPlan& p, Ctrl* ctrl);
+template <class W>
+void giant_compact(Ctx& c, const int32_t* list, int64_t m, const int64_t* hbeg, const int64_t* hend,
+                   const int64_t* doff, const int32_t* itg, const W* iw, int32_t* otg, W* ow, const GiantPlan& p,
+                   Ctrl* ctrl);
+// Compaction of holey rows listed by community-degree buckets (cperm, host offsets cb).
+template <class W>
+void compact_bucketed(Ctx& c, const int32_t* cperm, const int64_t* cb, const int64_t* hbeg, const int64_t* hend,
+                      const int64_t* doff, const int32_t* itg, const W* iw, int32_t* otg, W* ow, const GiantPlan& gp,
+                      Ctrl* ctrl);
+
 // ---------------------------------------------------------------- modularity.cu
+// Same value by degree-bucketed groups (dperm / hb: a degree-bucket sort of g), giant rows chunked.
+template <class M>
+void modularity_bucketed(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* C, typename M::a_t* tot,
+                         Ctrl* ctrl, const int32_t* dperm, const int64_t* hb, const GiantPlan& gp);
 // Q of membership C on dense CSR g; tot[n] scratch (zeroed inside); result in ctrl->q (and
 // acc slots).  Integer mode exact.
 template <class M>

@@ -101,6 +101,73 @@ void modularity(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* C, t
   c.launches++;
 }
 
+// Degree-bucketed form: one group of G threads per vertex (the lists of a degree-bucket sort),
+// giant rows by arc chunks, so no block is stuck with a hub's row.
+template <class M, int G>
+__global__ void __launch_bounds__(kBlock) k_mod_group(GraphView<typename M::w_t> g, const int32_t* list, int64_t count,
+                                                      const int32_t* C, typename M::a_t* tot, Ctrl* ctrl) {
+  typedef typename M::a_t A;
+  __shared__ A red[32];
+  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
+  const unsigned lane = Grp<G>::lane();
+  A sig = A(0), tm = A(0);
+  for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
+    const int32_t i = list[idx];
+    const int32_t ci = C[i];
+    A k = A(0);
+    for (int64_t e = g.rbeg[i] + lane; e < g.rend[i]; e += G) {
+      const A w = (A)g.w[e];
+      k += w;
+      if (C[g.tg[e]] == ci) sig += w;
+    }
+    k = group_sum<G>(k, red);
+    if (lane == 0) {
+      atomic_add_a(&tot[ci], k);
+      tm += k;
+    }
+  }
+  sig = group_sum<kBlock>(sig, red);
+  tm = group_sum<kBlock>(tm, red);
+  if (threadIdx.x == 0) {
+    if (M::is_fp) { atomicAdd(&ctrl->acc_f[0], (double)sig); atomicAdd(&ctrl->acc_f[1], (double)tm); }
+    else { atomic_add_a(&ctrl->acc_i[0], (long long)sig); atomic_add_a(&ctrl->acc_i[1], (long long)tm); }
+  }
+}
+
+template <class M>
+void modularity_bucketed(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* C, typename M::a_t* tot,
+                         Ctrl* ctrl, const int32_t* dperm, const int64_t* hb, const GiantPlan& gp) {
+  k_mod_reset<<<1, 1, 0, c.s>>>(ctrl);
+  c.launches++;
+  if (g.n > 0) {
+    cudaMemsetAsync(tot, 0, (size_t)g.n * sizeof(typename M::a_t), c.s);
+    const int cap = c.num_sms * 16;
+    for (int b = 0; b < kNumBuckets; b++) {
+      const int64_t cnt = hb[b + 1] - hb[b];
+      if (cnt <= 0) continue;
+      const int32_t* l = dperm + hb[b];
+      switch (b) {
+        case 0: k_mod_group<M, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
+        case 1: k_mod_group<M, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
+        case 2: k_mod_group<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
+        case 3:
+        case 4: k_mod_group<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
+        default: giant_modularity<M>(c, g, l, cnt, C, tot, gp, ctrl); c.launches--; break;
+      }
+      c.launches++;
+    }
+    k_mod_squares<M><<<grid_for(g.n, kBlock * 8, c.num_sms * 4), kBlock, 0, c.s>>>(tot, g.n, ctrl);
+    c.launches++;
+  }
+  k_mod_final<M::is_fp><<<1, 1, 0, c.s>>>(ctrl);
+  c.launches++;
+}
+
+template void modularity_bucketed<IntMode>(Ctx&, const GraphView<int32_t>&, const int32_t*, long long*, Ctrl*,
+                                           const int32_t*, const int64_t*, const GiantPlan&);
+template void modularity_bucketed<FpMode>(Ctx&, const GraphView<float>&, const int32_t*, double*, Ctrl*,
+                                          const int32_t*, const int64_t*, const GiantPlan&);
 template void modularity<IntMode>(Ctx&, const GraphView<int32_t>&, const int32_t*, long long*, Ctrl*);
 template void modularity<FpMode>(Ctx&, const GraphView<float>&, const int32_t*, double*, Ctrl*);
 

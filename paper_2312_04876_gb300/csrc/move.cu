@@ -78,8 +78,9 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
   if (*(volatile int32_t*)&ctrl->done) return;
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
   constexpr int SL = GLOBAL ? 1 : (1 << LOG);
-  __shared__ int32_t skeys[GPB * SL];
-  __shared__ H svals[GPB * SL];
+  extern __shared__ __align__(16) unsigned char lm_dyn[];  // GPB tables of SL (key, value) slots
+  int32_t* skeys = reinterpret_cast<int32_t*>(lm_dyn);
+  H* svals = reinterpret_cast<H*>(lm_dyn + sizeof(int32_t) * GPB * SL);
   __shared__ S red_s[32];
   __shared__ int32_t red_c[32];
   __shared__ H red_h[32];
@@ -207,8 +208,11 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
 template <class M, int G, int LOG, bool GLOBAL>
 static void launch_lm(Ctx& c, const LmArgs<M>& a, int max_blocks) {
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  constexpr size_t smem = (size_t)GPB * (GLOBAL ? 1 : (1 << LOG)) * (sizeof(int32_t) + sizeof(typename M::h_t));
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(lm_kernel<M, G, LOG, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = grid_for(a.count, GPB, max_blocks);
-  lm_kernel<M, G, LOG, GLOBAL><<<grid, kBlock, 0, c.s>>>(a);
+  lm_kernel<M, G, LOG, GLOBAL><<<grid, kBlock, smem, c.s>>>(a);
   c.launches++;
 }
 
@@ -230,7 +234,8 @@ void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const 
     case 1: launch_lm<M, 8, 5, false>(c, a, cap); break;
     case 2: launch_lm<M, 32, 8, false>(c, a, cap); break;
     case 3: launch_lm<M, 256, 12, false>(c, a, cap); break;
-    default: launch_lm<M, 256, 0, true>(c, a, gt.blocks > 0 ? gt.blocks : 1); break;
+    case 4: launch_lm<M, 256, 13, false>(c, a, cap); break;
+    default: break;  // giants go through giant_move
   }
 }
 

@@ -141,7 +141,9 @@ constexpr int kSmemKeys = 4096;
 // Histogram of keys; block-local shared histograms when the key space is small.
 __global__ void __launch_bounds__(kBlock) k_key_hist(KeyDesc kind, int64_t n, const int64_t* rbeg, const int64_t* rend,
                                                      const int32_t* colour, const int64_t* deg64, int64_t nkeys,
-                                                     int64_t* hist, unsigned long long* max_deg) {
+                                                     int64_t* hist, unsigned long long* max_deg,
+                                                     unsigned long long* giant_slots, int64_t n_bound) {
+  unsigned long long gs = 0;
   __shared__ int32_t sh[kSmemKeys];
   const bool local = nkeys <= kSmemKeys;
   if (local) {
@@ -152,10 +154,17 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(KeyDesc kind, int64_t n, co
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const long long dg = kind.kind == 2 ? deg64[i] : rend[i] - rbeg[i];
     mx = dg > mx ? dg : mx;
+    if (giant_slots && degree_bucket(dg) == kNumBuckets - 1)
+      gs += 1ULL << tbl_log2(dg < n_bound ? dg : n_bound, 6, 31);
     int k = sort_key(kind, i, rbeg, rend, colour, deg64);
     if (k < 0) continue;
     if (local) atomicAdd(&sh[k], 1);
     else atomicAdd(reinterpret_cast<unsigned long long*>(&hist[k]), 1ULL);
+  }
+  if (giant_slots) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) gs += __shfl_xor_sync(0xffffffffu, gs, o);
+    if ((threadIdx.x & 31) == 0 && gs) atomicAdd(giant_slots, gs);
   }
   if (max_deg) {
 #pragma unroll
@@ -217,12 +226,14 @@ __global__ void __launch_bounds__(kBlock) k_key_scatter(KeyDesc kind, int64_t n,
 
 void bucket_sort(Ctx& c, KeyDesc key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
                  const int64_t* deg64, int64_t nkeys, int32_t* perm, int64_t* offsets, int32_t* cursor,
-                 int64_t* tile_tmp, unsigned long long* max_deg) {
+                 int64_t* tile_tmp, unsigned long long* max_deg, unsigned long long* giant_slots,
+                 int64_t n_bound) {
   cudaMemsetAsync(offsets, 0, (size_t)(nkeys + 1) * sizeof(int64_t), c.s);
   cudaMemsetAsync(cursor, 0, (size_t)nkeys * sizeof(int32_t), c.s);
   if (n <= 0) return;
   int grid = grid_for(n, kBlock * 16, c.num_sms * 4);
-  k_key_hist<<<grid, kBlock, 0, c.s>>>(key_kind, n, rbeg, rend, colour, deg64, nkeys, offsets, max_deg);
+  k_key_hist<<<grid, kBlock, 0, c.s>>>(key_kind, n, rbeg, rend, colour, deg64, nkeys, offsets, max_deg, giant_slots,
+                                       n_bound);
   scan_exclusive_i64(c, offsets, offsets, nkeys, tile_tmp);
   k_key_scatter<<<grid, kBlock, 0, c.s>>>(key_kind, n, rbeg, rend, colour, deg64, nkeys, offsets, cursor, perm);
   c.launches += 2;

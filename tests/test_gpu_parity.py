@@ -41,6 +41,10 @@ GRAPHS = {
     "loops": lambda: random_graph(300, 0.03, np.random.default_rng(1), self_loops=True),
     "ring": lambda: cliques(8, 6, ring=True),
     "star": lambda: gg.from_edges(3000, [(0, i) for i in range(1, 3000)]),
+    # a hub of degree 20k (5 arc chunks, 16 table slices) plus a ring, so it also has a community
+    "star20k": lambda: gg.from_edges(20001, [(0, i) for i in range(1, 20001)] +
+                                     [(i, i + 1) for i in range(1, 20000)]),
+    "rmat16": lambda: gg.rmat(16, weights=gg.W_INT8, seed=22),
 }
 
 
@@ -85,7 +89,7 @@ def test_colouring_matches_oracle(L, name, seed, pass_index):
     assert np.array_equal(col.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("name", ["sbm2k", "rmat12", "loops", "star", "grid"])
+@pytest.mark.parametrize("name", ["sbm2k", "rmat12", "rmat16", "loops", "star", "star20k", "grid"])
 @pytest.mark.parametrize("k", [1, 3, 40, 10**9])
 def test_aggregate_matches_oracle(L, name, k):
     g = GRAPHS[name]()
@@ -119,7 +123,8 @@ def test_aggregate_fp32(L):
 
 
 # ---------------------------------------------------------------- local-moving phase
-@pytest.mark.parametrize("name", ["sbm2k", "sbm10k_cfg1", "rmat12", "rmat14", "loops", "grid", "ring", "star"])
+@pytest.mark.parametrize("name", ["sbm2k", "sbm10k_cfg1", "rmat12", "rmat14", "rmat16", "loops", "grid", "ring", "star",
+                                  "star20k"])
 @pytest.mark.parametrize("pruning", [1, 0])
 def test_local_move_deterministic_bit_exact(L, name, pruning):
     g = GRAPHS[name]()
@@ -132,7 +137,8 @@ def test_local_move_deterministic_bit_exact(L, name, pruning):
 
 
 # ---------------------------------------------------------------- whole method
-@pytest.mark.parametrize("name", ["sbm2k", "sbm10k_cfg1", "rmat12", "rmat14", "loops", "grid", "ring", "star"])
+@pytest.mark.parametrize("name", ["sbm2k", "sbm10k_cfg1", "rmat12", "rmat14", "rmat16", "loops", "grid", "ring", "star",
+                                  "star20k"])
 @pytest.mark.parametrize("compact", [1, 0])
 def test_run_deterministic_bit_exact(L, name, compact):
     g = GRAPHS[name]()
@@ -155,7 +161,7 @@ def test_run_is_repeatable(L):
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("name", ["sbm10k_cfg1", "rmat14", "grid", "ring"])
+@pytest.mark.parametrize("name", ["sbm10k_cfg1", "rmat14", "rmat16", "grid", "ring", "star20k"])
 def test_run_fast_mode_quality(L, name):
     g = GRAPHS[name]()
     o, t, w = dev(g)

@@ -193,6 +193,22 @@ louvain_status louvain_kernel_profile(louvain_handle h, louvain_kernel_stat* out
 louvain_status louvain_exclusive_scan(louvain_handle h, const int64_t* d_in, int64_t* d_out, int64_t count,
                                       void* stream, int64_t* total);
 
+/* louvain_exclusive_scan without any allocation (the paper has no counterpart; it exists for
+ * callers that cannot call cudaMalloc -- a host application whose memory manager owns all device
+ * memory, e.g. a framework's caching allocator or a fixed HBM budget already handed out, or a
+ * latency-critical loop that cannot take cudaMalloc / cudaFree's implicit device-wide
+ * synchronisation).  Needs no handle.  Same result and layout as louvain_exclusive_scan:
+ * d_out[0, count) = exclusive prefix sums of d_in[0, count) (int64, device), d_out[count] = total,
+ * d_in == d_out allowed, *total (host, optional).  count must not exceed 2^26 (67,108,864) elements,
+ * else LOUVAIN_ERR_INVALID.  The scratch is a 128 KiB __device__ array in the library that every GPU
+ * loading the library keeps until the process exits; the call allocates and frees nothing.  Its
+ * address is looked up on the first call on each device, so make that first call before any stream
+ * capture.  All calls on a device share the one scratch array: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.  Synchronises `stream`
+ * before returning.  LOUVAIN_ERR_CUDA on a CUDA failure. */
+louvain_status louvain_exclusive_scan_static(const int64_t* d_in, int64_t* d_out, int64_t count, void* stream,
+                                             int64_t* total);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,26 @@ def default_params(**overrides) -> Params:
     return p
 
 
+STATIC_SCAN_MAX = 1 << 26
+
+
+def exclusive_scan_static(values, out=None, stream=None):
+    """Exclusive scan through louvain_exclusive_scan_static, the entry point that allocates
+    nothing (scratch in a fixed device array; at most 2^26 elements; no handle).  For callers that
+    cannot call cudaMalloc.  Returns (out int64 tensor of numel + 1, total)."""
+    import torch
+    lib = _native.load()
+    n = values.numel()
+    if out is None:
+        out = torch.empty(n + 1, dtype=torch.int64, device=values.device)
+    tot = ctypes.c_int64()
+    st = lib.louvain_exclusive_scan_static(values.data_ptr(), out.data_ptr(), n, _stream_ptr(stream),
+                                           ctypes.byref(tot))
+    if st != _native.OK:
+        raise LouvainError(st, f"louvain_exclusive_scan_static(count={n}) failed")
+    return out, int(tot.value)
+
+
 @dataclass
 class RunResult:
     modularity: float

@@ -60,6 +60,7 @@ SIGNATURES = {
     "louvain_aggregate": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, _V, _I64, _V, _V, _V, _V, ctypes.POINTER(_I64)]),
     "louvain_exclusive_scan": (_I32, [_V, _V, _V, _I64, _V, ctypes.POINTER(_I64)]),
     "louvain_kernel_profile": (_I32, [_V, ctypes.POINTER(KernelStat), _I32, ctypes.POINTER(_I32)]),
+    "louvain_exclusive_scan_static": (_I32, [_V, _V, _I64, _V, ctypes.POINTER(_I64)]),
 }
 
 _lib = None

@@ -30,8 +30,10 @@ WORKLOADS = {
     "rmat18": (dict(kind="rmat", scale=18), "R-MAT scale 18, edge factor 16, int32 weights 1..8, seed 22"),
     "sbm10k": (dict(kind="sbm"), "planted-partition SBM, 10k vertices, 100 blocks, p_in 0.1, p_out 0.0005"),
 }
-CPU_SAMPLE = "rmat19"
+CPU_SAMPLE = "rmat20"   # cpu_baseline of the bench line: one oracle run, ~10-30 s
+REF_SAMPLE = "rmat18"   # one step of --impl reference: a few seconds each
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def make_graph(name):
@@ -110,6 +112,42 @@ def peaks():
         return PEAKS_FALLBACK["hbm_gbs"], "fallback"
 
 
+def stored_traffic(workload: str, mode: str, kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this workload, or None
+    when there is none or the kernels changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{mode}.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    from paper_2312_04876_gb300.profiling import source_sha256
+    if t.get("source_sha256") != source_sha256():
+        return None
+    c = t.get("classes", {}).get(kernel)
+    return None if c is None else c.get("dram_bytes_per_launch")
+
+
+def oracle_match(workload: str, mode: str, q: float, membership_sha: str | None):
+    """Compares the run with the CPU oracle's stored result for the same workload (written by
+    tests/golden/make_golden.py): deterministic mode must reproduce the membership bit for bit,
+    fast mode must reach the oracle's modularity within 0.005 (or exceed it)."""
+    path = os.path.join(GOLDEN, f"{workload}_oracle.json")
+    try:
+        with open(path) as f:
+            gold = json.load(f)
+    except (OSError, ValueError):
+        return {"oracle": None}
+    out = {"oracle_modularity": gold["modularity"], "oracle_sequential_modularity": gold["sequential_modularity"],
+           "delta_q": q - gold["modularity"]}
+    if mode == "deterministic":
+        out["membership_identical"] = membership_sha == gold["membership_sha256"]
+        out["matched"] = bool(out["membership_identical"] and q == gold["modularity"])
+    else:
+        out["matched"] = bool(q >= gold["modularity"] - 0.005)
+    return out
+
+
 def cpu_baseline(sample: str = CPU_SAMPLE, repeats: int = 1):
     """The CPU oracle (single-threaded C++, as it stands) on a bounded sample of the workload."""
     import oracle
@@ -129,7 +167,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    g = make_graph(CPU_SAMPLE)
+    g = make_graph(REF_SAMPLE)
     oracle.build()
     p = oracle.default_params()
     for _ in range(args.warmup):
@@ -143,9 +181,10 @@ def run_reference(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {"workload": f"{CPU_SAMPLE} (bounded sample of {args.workload})", "mode": "deterministic"},
+            "config": {"workload": f"{REF_SAMPLE} (bounded sample of {args.workload})", "mode": "deterministic"},
             "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"R-MAT scale {CPU_SAMPLE[4:]} ({g.n_arcs} arcs), full Louvain per step"},
+                             "sample": f"R-MAT scale {REF_SAMPLE[4:]} ({g.n_arcs} arcs), full deterministic "
+                                       f"Louvain per step, 1 of {os.cpu_count()} host cores"},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -232,6 +271,10 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_step = ms / args.steps
+    msha = None
+    if args.mode == "deterministic":
+        import hashlib
+        msha = hashlib.sha256(mem.cpu().numpy().astype("<i4").tobytes()).hexdigest()
     value = ws * args.steps * g.n_arcs / (ms / 1e3)
     launches = sum(r.kernel_launches for r in results)
     last = results[-1]
@@ -282,6 +325,7 @@ def main():
     roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
             "peak_kind": peak_kind}
     if dom:
+        roof["traffic"] = stored_traffic(args.workload, args.mode, dom["name"])
         roof.update({"kernel": dom["name"], "achieved": dom["gbs"], "frac": dom["gbs"] / peak,
                      "algorithmic_bytes_per_launch": agg[dom["name"]]["bytes"] / max(1, agg[dom["name"]]["launches"]),
                      "avg_launch_ms": agg[dom["name"]]["ms"] / max(1, agg[dom["name"]]["launches"])})
@@ -292,7 +336,8 @@ def main():
         "config": {"workload": WORKLOADS[args.workload][1], "n": g.n, "arcs": g.n_arcs, "mode": args.mode,
                    "parallelism": "replicas" if ws > 1 else "single", "l2": "inputs larger than L2 "
                    f"(CSR {(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes) / 1e9:.2f} GB vs 0.13 GB L2)"},
-        "modularity": last.modularity, "passes": last.passes, "iterations": last.total_iterations,
+        "modularity": last.modularity, "oracle_match": oracle_match(args.workload, args.mode, last.modularity, msha),
+        "passes": last.passes, "iterations": last.total_iterations,
         "communities": last.n_communities, "gpu_launches": launches,
         "pass_ms": [{k: round(v, 3) if isinstance(v, float) else v for k, v in s.items()} for s in last.stats],
         "roofline": roof, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,

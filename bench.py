@@ -190,6 +190,87 @@ def run_reference(args):
     return 0
 
 
+def batch_graphs(count: int, n_hi: float, threads: int):
+    """Members 0..count-1 of the batched planted-partition family (n log-uniform in [1e3, n_hi],
+    2-64 blocks, average degree log-uniform in [4, 64], p_out = 0.02 p_in, seed hash3(4, g, 0)),
+    generated on `threads` host threads (the C generator releases the GIL)."""
+    import graphgen as gg
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(lambda k: gg.batch_sbm(4, k, n_hi=n_hi), range(count)))
+
+
+def run_batch_bench(args):
+    """Batched workload: G independent graphs in one louvain_run_batch call (graphs/s), beside the
+    one-graph-at-a-time path (louvain_run per graph on the same device-resident graphs)."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_2312_04876_gb300 as lv
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    graphs = batch_graphs(args.batch_graphs, args.batch_n_hi, min(32, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    vo, offs, tg, w = gg.concat(graphs)
+    n_arcs = int(offs[-1])
+    o_d, t_d, w_d = (torch.from_numpy(a).to(dev) for a in (offs, tg, w))
+    del offs, tg, w
+    L = lv.Louvain(local)
+    params = lv.default_params(mode=args.mode, validate=0)
+    mem = torch.empty(int(vo[-1]), dtype=torch.int32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        L.run_batch(vo, o_d, t_d, w_d, params, membership=mem)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, per, res = L.run_batch(vo, o_d, t_d, w_d, params, membership=mem)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    G = len(graphs)
+    batch_gps = G / (ms / 1e3)
+    # one graph at a time on the same GPU: every graph alone through louvain_run (device-resident)
+    single_q = []
+    idx = range(G) if args.single_sample <= 0 else range(min(G, args.single_sample))
+    singles = [(torch.from_numpy(graphs[k].offsets).to(dev), torch.from_numpy(graphs[k].targets).to(dev),
+                torch.from_numpy(graphs[k].weights).to(dev)) for k in idx]
+    m1 = torch.empty(max(g.n for g in graphs), dtype=torch.int32, device=dev)
+    for so, st_, sw in singles[:3]:
+        L.run(so, st_, sw, params, membership=m1[:so.numel() - 1])
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for so, st_, sw in singles:
+        _, r = L.run(so, st_, sw, params, membership=m1[:so.numel() - 1])
+        single_q.append(r.modularity)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = ev0.elapsed_time(ev1)
+    single_gps = len(singles) / (single_ms / 1e3)
+    dq = [per[k]["modularity"] - single_q[j] for j, k in enumerate(idx)]
+    line = {
+        "metric": "louvain_batched_graphs_per_second", "value": batch_gps, "unit": "graphs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{G} planted-partition SBM graphs, n log-uniform [1e3, {args.batch_n_hi:.0f}], "
+                               "2-64 blocks, degree log-uniform [4, 64], p_out/p_in 0.02, unit int32 weights",
+                   "graphs": G, "vertices": int(vo[-1]), "arcs": n_arcs, "mode": args.mode,
+                   "l2": f"inputs larger than L2 (CSR {(8 * (int(vo[-1]) + 1) + 8 * n_arcs) / 1e9:.2f} GB)"},
+        "edges_per_second": n_arcs / (ms / 1e3), "gpu_launches_per_step": res.kernel_launches,
+        "one_at_a_time": {"graphs_per_second": single_gps, "graphs_timed": len(singles), "ms": single_ms,
+                          "max_abs_dq_vs_batch": max(abs(x) for x in dq) if dq else None},
+        "speedup_vs_one_at_a_time": batch_gps / single_gps,
+        "passes_max": res.passes, "generate_s": gen_s, "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,7 +278,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--mode", default="fast", choices=["fast", "deterministic"])
-    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--batch-graphs", type=int, default=4096, help="batch workload: number of graphs")
+    ap.add_argument("--batch-n-hi", type=float, default=2e5, help="batch workload: largest vertex count")
+    ap.add_argument("--single-sample", type=int, default=0,
+                    help="batch workload: time the one-at-a-time path on the first K graphs only (0 = all)")
     ap.add_argument("--fast-classes", type=int, default=None, help="random vertex classes of the fast schedule")
     ap.add_argument("--compact", type=int, default=None, help="1: compact super-vertex graphs, 0: keep holey CSR")
     ap.add_argument("--ncu-window", action="store_true",
@@ -208,6 +293,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch_bench(args)
 
     import numpy as np
     import torch

@@ -185,3 +185,21 @@ def from_edges(n: int, edges, weights=None, fp: bool = False) -> Graph:
     tg = np.array([v for _, v, _ in arcs], dtype=np.int32)
     w = np.array([w for _, _, w in arcs], dtype=np.float32 if fp else np.int32)
     return Graph(n, offs, tg, w, "edges")
+
+
+def concat(graphs):
+    """Segmented CSR of a list of graphs: (vo [G + 1] vertex ranges, union row offsets [n + 1],
+    graph-LOCAL targets, weights), the input layout of a batched run."""
+    G = len(graphs)
+    vo = np.zeros(G + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        vo[k + 1] = vo[k] + g.n
+    n = int(vo[-1])
+    offs = np.zeros(n + 1, dtype=np.int64)
+    abase = 0
+    for k, g in enumerate(graphs):
+        offs[vo[k]:vo[k + 1] + 1] = g.offsets + abase
+        abase += g.n_arcs
+    tg = np.concatenate([g.targets for g in graphs]) if G else np.zeros(0, np.int32)
+    wt = np.concatenate([g.weights for g in graphs]) if G else np.zeros(0, np.int32)
+    return vo, offs, tg.astype(np.int32, copy=False), wt

@@ -131,6 +131,36 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
                            louvain_result* res, louvain_pass_stats* stats, int32_t stats_cap,
                            int32_t* n_stats);
 
+/* Outcome of one graph of a batch (louvain_run_batch). */
+typedef struct {
+  double modularity;             /* Eq. 1 of the graph's membership on the graph */
+  int32_t passes;
+  int32_t total_iterations;      /* sum of l_i over the graph's passes */
+  int64_t n_communities;
+} louvain_graph_result;
+
+/* Algorithm 1 on each of n_graphs independent graphs at once.  The paper runs one graph; this
+ * entry point is a throughput extension that does not change the arithmetic: every graph gets
+ * exactly the membership, modularity and pass/iteration counts louvain_run gives it alone (in
+ * deterministic mode bit for bit; the colouring priorities and random classes hash graph-local
+ * ids), while every kernel launch covers all graphs still running.
+ *
+ * Segmented CSR: graph k owns the vertex range [graph_vtx_offs[k], graph_vtx_offs[k+1]) of the
+ * union (graph_vtx_offs: HOST int64 [n_graphs + 1], non-decreasing, graph_vtx_offs[0] = 0,
+ * n = graph_vtx_offs[n_graphs] < 2^31).  d_offsets (DEVICE int64 [n + 1]) are the union's row
+ * offsets, so graph k's arcs are [d_offsets[vo[k]], d_offsets[vo[k+1]]); d_targets (DEVICE int32
+ * [n_arcs]) hold GRAPH-LOCAL vertex ids (0 .. n_k - 1); d_weights as in louvain_run.  Inputs are
+ * read only.  d_membership (DEVICE int32 [n], caller-owned) receives graph-local canonical
+ * community ids.  results (HOST [n_graphs], optional) one entry per graph; res (optional): passes
+ * = the largest pass count, total_iterations and n_communities summed, modularity NaN, device time.
+ * Errors: LOUVAIN_ERR_INVALID (bad ranges, a target outside its graph, validation failures),
+ * LOUVAIN_ERR_OVERFLOW (integer weights with 2m >= 2^31 in some graph), LOUVAIN_ERR_OOM,
+ * LOUVAIN_ERR_CUDA.  Scratch beyond louvain_run's: 4 bytes per arc and 12 per vertex. */
+louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64_t* graph_vtx_offs, int64_t n_arcs,
+                                 const int64_t* d_offsets, const int32_t* d_targets, const void* d_weights,
+                                 louvain_wtype wtype, const louvain_params* p, void* stream, int32_t* d_membership,
+                                 louvain_graph_result* results, louvain_result* res);
+
 /* louvain_run for HOST buffers: copies the CSR to the device (through the handle's workspace),
  * runs, and copies the membership back to h_membership[n].  Pinned host memory gives the
  * fastest copies; pageable memory works.  The copies are part of the call. */

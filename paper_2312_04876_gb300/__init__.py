@@ -167,6 +167,32 @@ class Louvain:
         return membership, RunResult(res.modularity, res.passes, res.total_iterations, res.n_communities,
                                      res.ms_total, res.kernel_launches, _stats_list(st, nst.value))
 
+    def run_batch(self, graph_vtx_offs, offsets, targets, weights, params: Params | None = None, membership=None,
+                  stream=None, **overrides):
+        """louvain_run_batch: many graphs in one union (segmented CSR).  graph_vtx_offs: host int64
+        sequence [G + 1]; offsets: device int64 union row offsets [n + 1]; targets: device int32
+        graph-LOCAL ids; weights: device int32/float32.  Returns (membership int32 tensor with
+        graph-local ids, list of per-graph dicts, RunResult of the whole call)."""
+        import numpy as np
+        import torch
+        p = params if params is not None else default_params(**overrides)
+        vo = np.ascontiguousarray(np.asarray(graph_vtx_offs, dtype=np.int64))
+        G = len(vo) - 1
+        n = int(vo[-1]) if G >= 0 and len(vo) else 0
+        if membership is None:
+            membership = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+        per = (_native.GraphResult * max(G, 1))()
+        res = Result()
+        rc = self._lib.louvain_run_batch(self._h, G, vo.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         targets.numel(), offsets.data_ptr(), targets.data_ptr(), weights.data_ptr(),
+                                         _wtype(weights), ctypes.byref(p), _stream_ptr(stream), membership.data_ptr(),
+                                         per, ctypes.byref(res))
+        self._check(rc)
+        graphs = [dict(modularity=r.modularity, passes=r.passes, total_iterations=r.total_iterations,
+                       n_communities=r.n_communities) for r in per[:G]]
+        return membership, graphs, RunResult(res.modularity, res.passes, res.total_iterations, res.n_communities,
+                                             res.ms_total, res.kernel_launches)
+
     # ---------------------------------------------------------------- steps
     def modularity(self, offsets, targets, weights, membership, stream=None) -> float:
         q = ctypes.c_double()

@@ -34,6 +34,11 @@ class Result(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class GraphResult(ctypes.Structure):
+    _fields_ = [("modularity", ctypes.c_double), ("passes", ctypes.c_int32), ("total_iterations", ctypes.c_int32),
+                ("n_communities", ctypes.c_int64)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("algorithmic_bytes", ctypes.c_double)]
@@ -61,6 +66,8 @@ SIGNATURES = {
     "louvain_exclusive_scan": (_I32, [_V, _V, _V, _I64, _V, ctypes.POINTER(_I64)]),
     "louvain_kernel_profile": (_I32, [_V, ctypes.POINTER(KernelStat), _I32, ctypes.POINTER(_I32)]),
     "louvain_exclusive_scan_static": (_I32, [_V, _V, _I64, _V, ctypes.POINTER(_I64)]),
+    "louvain_run_batch": (_I32, [_V, _I32, ctypes.POINTER(_I64), _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V,
+                                 _V, ctypes.POINTER(GraphResult), ctypes.POINTER(Result)]),
 }
 
 _lib = None

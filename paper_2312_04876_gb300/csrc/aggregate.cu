@@ -19,6 +19,7 @@ __global__ void k_comm_count(const int32_t* Cp, const int64_t* rbeg, const int64
                              int64_t* cdeg) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = Cp[i];
+    if (c < 0) continue;  // batched: the graph of i left the pass loop
     atomicAdd(&counts[c], 1);
     const int64_t d = rend[i] - rbeg[i];
     if (d) atomicAdd(reinterpret_cast<unsigned long long*>(&cdeg[c]), (unsigned long long)d);
@@ -34,6 +35,7 @@ void community_count(Ctx& c, const int32_t* Cp, const int64_t* rbeg, const int64
 __global__ void k_comm_fill(const int32_t* Cp, int64_t n, const int64_t* coff, int32_t* cursor, int32_t* cverts) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = Cp[i];
+    if (c < 0) continue;
     cverts[coff[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
   }
 }

@@ -62,6 +62,15 @@ struct Workspace {
   int32_t* in_tg = nullptr;
   void* in_w = nullptr;
   int32_t* in_mem = nullptr;
+  // batched runs (louvain_run_batch): per-graph control and the union's segmentation
+  DevAlloc batch_alloc;
+  int64_t b_graphs = -1, b_n = -1, b_a = -1;
+  GraphCtl* gc = nullptr;     // [G]
+  int64_t* vo = nullptr;      // [G + 1] input vertex ranges
+  int64_t* ao = nullptr;      // [G + 1] input arc ranges
+  int32_t* vg0 = nullptr;     // [n] graph of each input vertex
+  int32_t *vgA = nullptr, *vgB = nullptr;  // [n] graph of each vertex of the current / next level
+  int32_t* tgU = nullptr;     // [A] input targets as union ids
 };
 
 }  // namespace
@@ -108,7 +117,7 @@ struct louvain_handle_s {
 namespace {
 
 size_t total_bytes(const Workspace& ws) {
-  return ws.core.bytes + ws.keys_alloc.bytes + ws.gt_alloc.bytes + ws.in_alloc.bytes;
+  return ws.core.bytes + ws.keys_alloc.bytes + ws.gt_alloc.bytes + ws.in_alloc.bytes + ws.batch_alloc.bytes;
 }
 
 void free_all(DevAlloc& a) {
@@ -341,7 +350,7 @@ bool valid_params(const louvain_params* p) {
 
 // Full CSR validation on the device.  Returns OK / INVALID / OVERFLOW.
 louvain_status validate_graph(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, const int64_t* offs,
-                              const int32_t* tg, const void* w, bool fp) {
+                              const int32_t* tg, const void* w, bool fp, bool check_two_m = true) {
   Ctrl* ctrl = h->ws.ctrl;
   validate_reset(c, ctrl);
   validate_offsets(c, n, n_arcs, offs, ctrl);
@@ -355,7 +364,7 @@ louvain_status validate_graph(louvain_handle h, Ctx& c, int64_t n, int64_t n_arc
   if (hc->cnt[1]) return set_err(h, LOUVAIN_ERR_INVALID, "arc target outside [0, n)");
   if (hc->cnt[2]) return set_err(h, LOUVAIN_ERR_INVALID, "arc weight not positive (or not finite)");
   if (hc->cnt[3]) return set_err(h, LOUVAIN_ERR_INVALID, "graph is not symmetric (w_ij != w_ji)");
-  if (!fp && (unsigned long long)hc->acc_i[0] >= (1ULL << 31))
+  if (check_two_m && !fp && (unsigned long long)hc->acc_i[0] >= (1ULL << 31))
     return set_err(h, LOUVAIN_ERR_OVERFLOW, "integer mode needs 2m < 2^31");
   return LOUVAIN_OK;
 }
@@ -402,10 +411,16 @@ louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, i
 template <class M>
 louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const int64_t hb[],
                                 int64_t giant_slots, const louvain_params& p, int32_t pass, double tau, int32_t* li,
-                                int64_t* moves, size_t ev_colour_done) {
+                                int64_t* moves, size_t ev_colour_done, GraphCtl* gc = nullptr,
+                                const int32_t* vg = nullptr, int32_t n_graphs = 0) {
   Workspace& ws = h->ws;
   PassState<M> st{reinterpret_cast<typename M::a_t*>(ws.K), reinterpret_cast<typename M::a_t*>(ws.Sig), ws.Cp,
                   ws.flags, ws.csize, ws.mv_from, ws.mv_to, ws.ctrl};
+  st.gc = gc;
+  st.vg = vg;
+  Segs seg;
+  seg.vg = vg;
+  seg.gc = gc;
   const bool det = p.mode == LOUVAIN_MODE_DETERMINISTIC;
   louvain_status s;
   std::vector<int64_t> ho;  // class-bucket offsets (deterministic) or bucket offsets (fast)
@@ -416,7 +431,7 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
     cudaError_t ce;
     const int pm = prof_begin(h, c);
-    ncol = jp_colour(c, gs, ws.dperm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce);
+    ncol = jp_colour(c, gs, ws.dperm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce, seg);
     prof_end(h, c, kColour, pm);
     if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
     if (ncol < 0) return colour_failure(h);
@@ -432,8 +447,10 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     ncol = p.fast_classes > 0 ? p.fast_classes : 1;
     const int64_t nkeys = (int64_t)ncol * kNumBuckets;
     if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
-    bucket_sort(c, KeyDesc{3, ncol, pass, p.seed ^ 0x46A57C1A55E5ULL}, g.n, g.rbeg, g.rend, nullptr, nullptr, nkeys,
-                ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp, nullptr);
+    KeyDesc kd{3, ncol, pass, p.seed ^ 0x46A57C1A55E5ULL};
+    kd.seg = seg;
+    bucket_sort(c, kd, g.n, g.rbeg, g.rend, nullptr, nullptr, nkeys, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
+                nullptr);
     const int64_t* q = read_i64(h, c, ws.keyoffs, nkeys + 1, &s, "fast classes");
     if (!q) return s;
     ho.assign(q, q + nkeys + 1);
@@ -442,6 +459,7 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   // table pool for the giant vertices (each class uses it from its start; tables are cleared)
   if (giant_slots > 0 && (s = ensure_pool(h, c, giant_slots)) != LOUVAIN_OK) return s;
   move_setup(c, ws.ctrl, tau, p.max_iterations);
+  if (gc) batch_move_setup(c, gc, n_graphs, p.max_iterations);
   const bool pruning = p.pruning != 0;
   int enq = 0;
   const int batch = det ? 2 : 4;
@@ -463,7 +481,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
           prof_end(h, c, kApply, pm);
         }
       }
-      move_finish<M>(c, ws.ctrl);
+      if (gc) batch_finish<M>(c, ws.ctrl, gc, n_graphs);
+      else move_finish<M>(c, ws.ctrl);
     }
     const Ctrl* hc = read_ctrl(h, c, &s, "local move");
     if (!hc) return s;
@@ -656,6 +675,107 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
   return LOUVAIN_OK;
 }
 
+louvain_status ensure_batch(louvain_handle h, int64_t G, int64_t n, int64_t a) {
+  Workspace& ws = h->ws;
+  if (ws.b_graphs >= G && ws.b_n >= n && ws.b_a >= a && ws.gc) return LOUVAIN_OK;
+  const int64_t gc_ = G > ws.b_graphs ? G : ws.b_graphs, nc = n > ws.b_n ? n : ws.b_n, ac = a > ws.b_a ? a : ws.b_a;
+  free_all(ws.batch_alloc);
+  ws.b_graphs = ws.b_n = ws.b_a = -1;
+  DevAlloc& d = ws.batch_alloc;
+  bool ok = dalloc(h, d, &ws.gc, gc_) && dalloc(h, d, &ws.vo, gc_ + 1) && dalloc(h, d, &ws.ao, gc_ + 1) &&
+            dalloc(h, d, &ws.vg0, nc + 1) && dalloc(h, d, &ws.vgA, nc + 1) && dalloc(h, d, &ws.vgB, nc + 1) &&
+            dalloc(h, d, &ws.tgU, ac);
+  if (!ok) {
+    free_all(ws.batch_alloc);
+    return set_err(h, LOUVAIN_ERR_OOM, "batch workspace allocation failed or exceeds the HBM budget");
+  }
+  ws.b_graphs = gc_; ws.b_n = nc; ws.b_a = ac;
+  return LOUVAIN_OK;
+}
+
+// Algorithm 1 over a batch of graphs as one union graph (batch.cu holds the per-graph steps).
+// The pass loop runs until every graph has stopped; each launch covers all graphs still in it.
+template <class M>
+louvain_status run_batch_impl(louvain_handle h, Ctx& c, int32_t G, int64_t n, int64_t n_arcs, const int64_t* offs,
+                              const typename M::w_t* w, const louvain_params& p, int32_t* C, int32_t* passes_out) {
+  typedef typename M::a_t A;
+  typedef typename M::w_t W;
+  Workspace& ws = h->ws;
+  louvain_status s;
+  iota_i32(c, C, n);
+  GraphView<W> g0{n, offs, offs + 1, ws.tgU, w};
+  GraphView<W> g = g0;
+  PassState<M> st{reinterpret_cast<A*>(ws.K), reinterpret_cast<A*>(ws.Sig), ws.Cp, ws.flags, ws.csize, ws.mv_from,
+                  ws.mv_to, ws.ctrl};
+  cudaMemcpyAsync(ws.vgA, ws.vg0, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, c.s);
+  int32_t* vg = ws.vgA;
+  int32_t* vg_next = ws.vgB;
+  double tau = p.tolerance;
+  int32_t passes = 0;
+  for (int32_t lp = 0; lp < p.max_passes && g.n > 0; lp++) {
+    const int64_t n_cur = g.n;
+    int64_t hb[kNumBuckets + 1], gslots = 0;
+    if ((s = degree_buckets(h, c, g, hb, &gslots)) != LOUVAIN_OK) return s;
+    if (lp == 0) {
+      vertex_init<M>(c, st, n_cur, false);
+      row_sums<M>(c, g, ws.dperm, hb, st.K, st.Sig, reinterpret_cast<A*>(ws.K0));
+      batch_two_m<M>(c, ws.gc, G, st.K, ws.ctrl);
+      const Ctrl* hc = read_ctrl(h, c, &s, "pass init");
+      if (!hc) return s;
+      if (!M::is_fp && hc->cnt[6]) return set_err(h, LOUVAIN_ERR_OVERFLOW, "integer mode needs 2m < 2^31 per graph");
+    } else {
+      vertex_init<M>(c, st, n_cur, true);
+    }
+    int32_t li = 0;
+    int64_t moves = 0;
+    if ((s = local_move_phase<M>(h, c, g, hb, gslots, p, lp, tau, &li, &moves, 1, ws.gc, vg, G)) != LOUVAIN_OK)
+      return s;
+    passes = lp + 1;
+    // renumbering, pass tests per graph, dendrogram lookup, next level
+    mark_occupied(c, ws.Cp, n_cur, ws.occ, n_cur);
+    scan_exclusive_i32(c, ws.occ, ws.newid, n_cur, ws.tile_tmp);
+    batch_pass_end(c, ws.gc, G, ws.newid, p.aggregation_tolerance, lp + 1 == p.max_passes, ws.ctrl);
+    batch_next_level<A>(c, ws.Cp, n_cur, ws.newid, vg, ws.gc, G, C, n, ws.vg0, st.Sig, ws.occ, st.K, vg_next);
+    const Ctrl* hc = read_ctrl(h, c, &s, "batch pass end");
+    if (!hc) return s;
+    const int64_t nc = hc->acc_i[3];
+    if (nc == 0) break;
+    // aggregation of the continuing graphs (vertices of the others carry Cp < 0 and are skipped)
+    RowSet& rs = ws.rows[lp & 1];
+    int32_t* htg = ws.tgA;
+    W* hw = reinterpret_cast<W*>(ws.wA);
+    if (!p.compact && (lp & 1)) { htg = ws.tgB; hw = reinterpret_cast<W*>(ws.wB); }
+    int64_t cb[kNumBuckets + 1];
+    if ((s = aggregate_phase<M>(h, c, g, hb, nc, rs, htg, hw, cb)) != LOUVAIN_OK) return s;
+    if (p.compact) {
+      row_lengths(c, nc, rs.hoff, rs.hend, ws.len);
+      scan_exclusive_i64(c, ws.len, rs.doff, nc, ws.tile_tmp);
+      const int pm = prof_begin(h, c);
+      compact_bucketed<W>(c, ws.cperm, cb, rs.hoff, rs.hend, rs.doff, htg, hw, ws.tgB, reinterpret_cast<W*>(ws.wB),
+                          ws.gpv, ws.ctrl);
+      prof_end(h, c, kCompact, pm);
+      g = GraphView<W>{nc, rs.doff, rs.doff + 1, ws.tgB, reinterpret_cast<W*>(ws.wB)};
+    } else {
+      g = GraphView<W>{nc, rs.hoff, rs.hend, htg, hw};
+    }
+    int32_t* t = vg; vg = vg_next; vg_next = t;
+    tau /= p.tolerance_drop;
+  }
+  batch_close(c, C, n, ws.vg0, ws.gc, G);
+  // (a10) Eq. 1 per graph on the input graphs
+  const int pm = prof_begin(h, c);
+  int64_t hb0[kNumBuckets + 1], gs0 = 0;
+  if ((s = degree_buckets(h, c, g0, hb0, &gs0)) != LOUVAIN_OK) return s;
+  batch_modularity<M>(c, g0, C, ws.vg0, ws.gc, G, ws.vo, ws.dperm, hb0, st.Sig, reinterpret_cast<A*>(ws.tot), n);
+  prof_end(h, c, kModularity, pm);
+  const Ctrl* hc = read_ctrl(h, c, &s, "batch modularity");
+  if (!hc) return s;
+  if (hc->error) return set_err(h, LOUVAIN_ERR_CUDA, "internal: hash table overflow");
+  prof_finish(h, *hc);
+  *passes_out = passes;
+  return LOUVAIN_OK;
+}
+
 louvain_status begin_call(louvain_handle h) {
   if (!h) return LOUVAIN_ERR_INVALID;
   h->err.clear();
@@ -748,6 +868,100 @@ void louvain_destroy(louvain_handle h) {
 }
 
 const char* louvain_last_error(louvain_handle h) { return h ? h->err.c_str() : "invalid handle"; }
+
+louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64_t* graph_vtx_offs, int64_t n_arcs,
+                                 const int64_t* d_offsets, const int32_t* d_targets, const void* d_weights,
+                                 louvain_wtype wtype, const louvain_params* p, void* stream, int32_t* d_membership,
+                                 louvain_graph_result* results, louvain_result* res) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if (n_graphs < 0 || (n_graphs > 0 && !graph_vtx_offs))
+    return set_err(h, LOUVAIN_ERR_INVALID, "n_graphs < 0 or graph_vtx_offs is NULL");
+  if (!valid_params(p)) return set_err(h, LOUVAIN_ERR_INVALID, "invalid louvain_params");
+  if (res) std::memset(res, 0, sizeof(*res));
+  if (results && n_graphs > 0) std::memset(results, 0, sizeof(*results) * (size_t)n_graphs);
+  if (n_graphs == 0) return LOUVAIN_OK;
+  if (graph_vtx_offs[0] != 0) return set_err(h, LOUVAIN_ERR_INVALID, "graph_vtx_offs[0] must be 0");
+  for (int32_t k = 0; k < n_graphs; k++)
+    if (graph_vtx_offs[k + 1] < graph_vtx_offs[k])
+      return set_err(h, LOUVAIN_ERR_INVALID, "graph_vtx_offs must be non-decreasing");
+  const int64_t n = graph_vtx_offs[n_graphs];
+  if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
+  if (n > 0 && !d_membership) return set_err(h, LOUVAIN_ERR_INVALID, "membership pointer is NULL");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  h->prof.on = p->profile != 0;
+  h->prof.used = 0;
+  h->prof.recs.clear();
+  h->prof.valid = false;
+  if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
+  if ((s = ensure_batch(h, n_graphs, n, n_arcs)) != LOUVAIN_OK) return s;
+  const size_t gbytes = sizeof(GraphCtl) * (size_t)n_graphs;
+  if ((s = ensure_pinned(h, gbytes + 65536)) != LOUVAIN_OK) return s;
+  if (!event_at(h, 2)) return set_err(h, LOUVAIN_ERR_CUDA, "event creation failed");
+  cudaEventRecord(h->events[0], c.s);
+  Workspace& ws = h->ws;
+  // vertex ranges to the device through the pinned buffer (after the Ctrl area)
+  unsigned char* stage = reinterpret_cast<unsigned char*>(h->pin) + 1024;
+  std::memcpy(stage, graph_vtx_offs, sizeof(int64_t) * ((size_t)n_graphs + 1));
+  cudaMemcpyAsync(ws.vo, stage, sizeof(int64_t) * ((size_t)n_graphs + 1), cudaMemcpyHostToDevice, c.s);
+  cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), c.s);
+  batch_setup(c, ws.vo, n_graphs, n, d_offsets, n_arcs, d_targets, ws.tgU, ws.ao, ws.vg0, ws.gc, ws.ctrl);
+  {
+    const Ctrl* hc = read_ctrl(h, c, &s, "batch setup");
+    if (!hc) return s;
+    if (hc->cnt[1]) return set_err(h, LOUVAIN_ERR_INVALID, "arc target outside its graph's vertex range");
+  }
+  const bool fp = wtype == LOUVAIN_W_FP32;
+  if (p->validate) {
+    if ((s = validate_graph(h, c, n, n_arcs, d_offsets, ws.tgU, d_weights, fp, false)) != LOUVAIN_OK) return s;
+    cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), c.s);
+  }
+  int32_t passes = 0;
+  if (n > 0) {
+    if (fp)
+      s = run_batch_impl<FpMode>(h, c, n_graphs, n, n_arcs, d_offsets, reinterpret_cast<const float*>(d_weights), *p,
+                                 d_membership, &passes);
+    else
+      s = run_batch_impl<IntMode>(h, c, n_graphs, n, n_arcs, d_offsets, reinterpret_cast<const int32_t*>(d_weights),
+                                  *p, d_membership, &passes);
+    if (s != LOUVAIN_OK) {
+      cudaStreamSynchronize(c.s);
+      cudaGetLastError();
+      return s;
+    }
+  }
+  if ((s = ensure_pinned(h, gbytes + 65536)) != LOUVAIN_OK) return s;
+  stage = reinterpret_cast<unsigned char*>(h->pin) + 1024;  // the buffer may have grown during the run
+  cudaMemcpyAsync(stage, ws.gc, gbytes, cudaMemcpyDeviceToHost, c.s);
+  cudaEventRecord(h->events[2], c.s);
+  if ((s = sync(h, c, "batch end")) != LOUVAIN_OK) return s;
+  const GraphCtl* gcs = reinterpret_cast<const GraphCtl*>(stage);
+  int64_t ncomm = 0;
+  int32_t max_pass = 0, iters = 0;
+  for (int32_t k = 0; k < n_graphs; k++) {
+    if (results) {
+      results[k].modularity = gcs[k].q;
+      results[k].passes = gcs[k].passes;
+      results[k].total_iterations = gcs[k].total_iterations;
+      results[k].n_communities = gcs[k].n_comm;
+    }
+    ncomm += gcs[k].n_comm;
+    if (gcs[k].passes > max_pass) max_pass = gcs[k].passes;
+    iters += gcs[k].total_iterations;
+  }
+  if (res) {
+    res->modularity = __builtin_nan("");
+    res->passes = max_pass;
+    res->total_iterations = iters;
+    res->n_communities = ncomm;
+    res->ms_total = elapsed(h, 0, 2);
+    res->kernel_launches = (int32_t)c.launches;
+  }
+  (void)passes;
+  return LOUVAIN_OK;
+}
 
 louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
                            const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,

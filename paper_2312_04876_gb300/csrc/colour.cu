@@ -21,6 +21,7 @@ struct JpArgs {
   int64_t list_cap;             // capacity of each ready list
   unsigned long long* rcount;   // rcount[r] = size of the ready list of round r (zeroed up front)
   Ctrl* ctrl;                   // cnt[3] coloured total, cnt[4] max colour + 1, cnt[7] guard trips
+  Segs seg;                     // batched run: priorities hash graph-local ids
 };
 
 template <int G>
@@ -31,11 +32,11 @@ __global__ void __launch_bounds__(kBlock) jp_count(JpArgs a, const int32_t* list
   const unsigned lane = Grp<G>::lane();
   for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
     const int32_t v = list[idx];
-    const uint64_t pv = hash3(a.seed, (uint64_t)a.pass, (uint64_t)v);
+    const uint64_t pv = hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, v));
     int32_t k = 0;
     for (int64_t e = a.g.rbeg[v] + lane; e < a.g.rend[v]; e += G) {
       const int32_t u = a.g.tg[e];
-      if (u != v && higher(hash3(a.seed, (uint64_t)a.pass, (uint64_t)u), u, pv, v)) k++;
+      if (u != v && higher(hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, u)), u, pv, v)) k++;
     }
     k = group_sum<G>(k, red);
     if (lane == 0) {
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
       if (lane == 0) atomicAdd(&a.ctrl->cnt[7], 1ULL);
       continue;
     }
-    const uint64_t pv = hash3(a.seed, (uint64_t)a.pass, (uint64_t)v);
+    const uint64_t pv = hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, v));
     const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
     int32_t mex = -1;
     // colours of higher-priority neighbours are final; mex <= degree, so windows are bounded
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
       __syncwarp();
       for (int64_t e = beg + lane; e < end; e += 32) {
         const int32_t u = a.g.tg[e];
-        if (u == v || !higher(hash3(a.seed, (uint64_t)a.pass, (uint64_t)u), u, pv, v)) continue;
+        if (u == v || !higher(hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, u)), u, pv, v)) continue;
         const int32_t cu = a.colour[u] - base;
         if (cu >= 0 && cu < 1024) atomicOr(&bm[warp][cu >> 5], 1u << (cu & 31));
       }
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
     __syncwarp();
     for (int64_t e = beg + lane; e < end; e += 32) {
       const int32_t u = a.g.tg[e];
-      if (u == v || !higher(pv, v, hash3(a.seed, (uint64_t)a.pass, (uint64_t)u), u)) continue;
+      if (u == v || !higher(pv, v, hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, u)), u)) continue;
       if (atomicSub(&a.cnt[u], 1) == 1) {
         const unsigned long long pos = atomicAdd(&a.rcount[r + 1], 1ULL);
         if ((int64_t)pos < a.list_cap) out[pos] = u;
@@ -133,7 +134,7 @@ __global__ void k_jp_reset(Ctrl* c) {
 
 int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, const int64_t* hb, uint64_t seed,
                   int32_t pass, int32_t* colour, const JpBuffers& jb, Ctrl* ctrl, unsigned long long* h_pinned,
-                  cudaError_t* err) {
+                  cudaError_t* err, Segs seg) {
   *err = cudaSuccess;
   const int64_t listed = hb[kNumBuckets] - hb[0];
   // Each round colours at least one vertex while any is left, so `listed` rounds always suffice.
@@ -147,6 +148,7 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
   JpArgs a;
   a.g = g; a.seed = seed; a.pass = pass; a.colour = colour; a.cnt = jb.cnt;
   a.lists[0] = jb.list0; a.lists[1] = jb.list1; a.list_cap = jb.list_cap; a.rcount = jb.rcount; a.ctrl = ctrl;
+  a.seg = seg;
   const int cap = c.num_sms * 16;
   for (int b = 0; b < kNumBuckets; b++) {
     int64_t cnt = hb[b + 1] - hb[b];

@@ -76,6 +76,41 @@ __device__ __forceinline__ void block_add_counters(unsigned long long* dst, unsi
 
 enum CtrlErr : int32_t { kErrTableFull = 1, kErrTimeout = 2, kErrRange = 4 };
 
+// Per-graph control of a batched run (louvain_run_batch): the graphs of a batch are disjoint
+// vertex ranges of one union graph, and everything the method keeps per graph -- 2m, the
+// per-iteration sum of N, the tolerance test, l_i, the pass decisions -- lives here.
+struct GraphCtl {
+  unsigned long long sum_lo, sum_hi;  // integer mode: sum of performed-move scores N (128-bit)
+  double sum_f;                       // fp mode
+  long long two_m_i;                  // 2m of the graph
+  double two_m_f;
+  long long vbase;                    // first vertex of the graph at the current level
+  long long nlev;                     // vertices of the graph at the current level
+  long long nbase;                    // first vertex at the next level (continuing graphs)
+  long long comm_base;                // occupied community ids before the graph (renumbering)
+  long long n_comm;                   // communities after the current pass
+  long long sig_in_i, sq_i;           // final modularity sums, integer mode
+  double sig_in_f, sq_f;              // final modularity sums, fp mode
+  double q;                           // final modularity
+  int32_t active;                     // in the pass loop at the current level
+  int32_t done;                       // local-moving phase of the current pass finished
+  int32_t iterations;                 // l_i of the current pass
+  int32_t cont;                       // continues to the next pass
+  int32_t passes;                     // passes run
+  int32_t total_iterations;           // sum of l_i
+};
+
+// Vertex segmentation of a batched run: vg[v] = graph of vertex v at the current level (null for
+// a single graph).  The colouring priority and the random classes hash the id LOCAL to the graph,
+// so a graph is treated identically alone and inside a batch.
+struct Segs {
+  const int32_t* vg = nullptr;
+  const GraphCtl* gc = nullptr;
+};
+__device__ __forceinline__ uint64_t local_id(const Segs& s, int32_t v) {
+  return s.vg ? (uint64_t)((long long)v - s.gc[s.vg[v]].vbase) : (uint64_t)v;
+}
+
 // ------------------------------------------------------------------ mode traits
 struct IntMode {
   typedef int32_t w_t;             // stored arc weight

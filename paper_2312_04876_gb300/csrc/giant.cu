@@ -37,7 +37,8 @@ constexpr int kLocLog = 12;    // shared pre-aggregation table: 4096 slots >= 2 
 __global__ void __launch_bounds__(1024) k_giant_plan(int kind, const int32_t* list, int64_t m, const int64_t* rbeg,
                                                      const int64_t* rend, const int64_t* cdeg, int64_t n_bound,
                                                      uint8_t* flags, int pruning, const int32_t* Cp, int32_t* gix,
-                                                     GiantPlan p, Ctrl* ctrl) {
+                                                     GiantPlan p, Ctrl* ctrl, const GraphCtl* gc = nullptr,
+                                                     const int32_t* vg = nullptr) {
   __shared__ int64_t part[3][1024];
   if (kind == 0 && *(volatile int32_t*)&ctrl->done) return;
   const int t = threadIdx.x;
@@ -53,11 +54,12 @@ __global__ void __launch_bounds__(1024) k_giant_plan(int kind, const int32_t* li
     } else {
       const int64_t deg = rend[v] - rbeg[v];
       bool active = true;
-      if (kind == 0 && pruning) {
+      if (kind == 0 && gc && gc[vg[v]].done) active = false;  // batched: graph converged
+      if (kind == 0 && pruning && active) {
         active = flags[v] != 0;
         if (active) flags[v] = 0;
       }
-      if (kind == 2) active = gix[Cp[v]] >= 0;
+      if (kind == 2) active = Cp[v] >= 0 && gix[Cp[v]] >= 0;  // batched: Cp < 0 = graph left
       if (active) {
         nch = (deg + kChunk - 1) / kChunk;
         if (kind == 0) ts = (int64_t)1 << tbl_log2(deg < n_bound ? deg : n_bound, 6, 31);
@@ -169,13 +171,14 @@ __global__ void __launch_bounds__(kBlock) k_giant_lm_insert(GraphView<typename M
 template <class M>
 __global__ void __launch_bounds__(kBlock) k_giant_lm_scan(const int32_t* list, int64_t m, const int32_t* Cp,
                                                           const typename M::a_t* K, const typename M::a_t* Sig,
-                                                          GiantPlan p, Ctrl* ctrl) {
+                                                          GiantPlan p, Ctrl* ctrl, const GraphCtl* gc,
+                                                          const int32_t* vg) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
   if (*(volatile int32_t*)&ctrl->done) return;
   const int64_t nslices = p.slice_off[m];
-  const A two_m = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
+  const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
   unsigned long long cand = 0;
@@ -197,6 +200,8 @@ __global__ void __launch_bounds__(kBlock) k_giant_lm_scan(const int32_t* list, i
         const int32_t d = Cp[i];
         const H kid = reinterpret_cast<const H*>(p.kid)[k];
         const A ki = K[i], sd = Sig[d];
+        const GraphCtl* gcv = gc ? gc + vg[i] : nullptr;
+        const A two_m = gcv ? (M::is_fp ? (A)gcv->two_m_f : (A)gcv->two_m_i) : two_m_all;
 #pragma unroll
         for (int u = 0; u < 4; u++) {
           const int32_t c = ks[u];
@@ -261,7 +266,11 @@ __global__ void __launch_bounds__(kBlock) k_giant_lm_decide(const int32_t* list,
     }
     st.Cp[i] = bc;
     p.moved[k] = 1;
-    if (M::is_fp) {
+    if (st.gc) {
+      GraphCtl* gcv = st.gc + st.vg[i];
+      if (M::is_fp) atomicAdd(&gcv->sum_f, (double)best);
+      else atomic_add_u128(&gcv->sum_lo, &gcv->sum_hi, (unsigned long long)best, 0ULL);
+    } else if (M::is_fp) {
       acc_f += (double)best;
     } else {
       const unsigned long long b = (unsigned long long)best;
@@ -334,11 +343,11 @@ void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>&
   if (m <= 0) return;
   const int grid = c.num_sms * 8;
   k_giant_plan<<<1, 1024, 0, c.s>>>(0, list, m, g.rbeg, g.rend, nullptr, g.n, st.flags, pruning ? 1 : 0, nullptr,
-                                    nullptr, p, st.ctrl);
+                                    nullptr, p, st.ctrl, st.gc, st.vg);
   GraphView<int32_t> gs{g.n, g.rbeg, g.rend, g.tg, nullptr};
   k_giant_lm_count<<<grid_for(m, kBlock, c.num_sms), kBlock, 0, c.s>>>(gs, list, m, p, st.ctrl);
   k_giant_lm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, m, st.Cp, p, st.ctrl);
-  k_giant_lm_scan<M><<<grid, kBlock, 0, c.s>>>(list, m, st.Cp, st.K, st.Sig, p, st.ctrl);
+  k_giant_lm_scan<M><<<grid, kBlock, 0, c.s>>>(list, m, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg);
   k_giant_lm_decide<M><<<grid_for(m, kBlock / 32, c.num_sms * 2), kBlock, 0, c.s>>>(list, m, st, p, fast ? 1 : 0);
   c.launches += 5;
   if (pruning) {
@@ -362,7 +371,9 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_insert(GraphView<typename M
   bool ok = true;
   for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
     const int32_t i = list[idx];
-    const int32_t k = gix[Cp[i]];
+    const int32_t ci = Cp[i];
+    if (ci < 0) continue;  // batched: the graph of i left the pass loop
+    const int32_t k = gix[ci];
     if (k < 0) continue;
     const int64_t off = p.tab_off[k];
     const unsigned ts = (unsigned)(p.tab_off[k + 1] - off);

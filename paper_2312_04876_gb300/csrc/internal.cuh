@@ -50,6 +50,7 @@ struct KeyDesc {
   int classes = 1;
   int pass = 0;
   uint64_t seed = 0;
+  Segs seg;  // kind 3 hashes the graph-local id
 };
 
 // Counting sort of vertex ids by key.  key_kind 0: degree bucket of (rend - rbeg); 1: colour *
@@ -85,6 +86,8 @@ struct PassState {
   int32_t* mv_from;
   int32_t* mv_to;
   Ctrl* ctrl;
+  GraphCtl* gc = nullptr;      // batched run: per-graph 2m, sums, convergence (null: one graph)
+  const int32_t* vg = nullptr; // batched run: graph of each vertex
 };
 
 // Per-pass vertex state: Cp = id, flags = 1, csize = 1, mv_to = -1; Sig = K if from_k else 0 with K = 0.
@@ -127,9 +130,10 @@ struct JpBuffers {
 };
 // Jones-Plassmann colouring of g (self-loops ignored).  Returns the number of colours.
 // Uses ctrl->cnt[3, 4, 7]; synchronises the stream once per batch of rounds.
+// In a batched run `seg` makes the priority hash the graph-local id.
 int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g_struct, const int32_t* perm, const int64_t* h_bucket_offs,
                   uint64_t seed, int32_t pass, int32_t* colour, const JpBuffers& jb, Ctrl* ctrl,
-                  unsigned long long* h_pinned, cudaError_t* err);
+                  unsigned long long* h_pinned, cudaError_t* err, Segs seg = Segs());
 
 // ---------------------------------------------------------------- aggregate.cu
 // counts[c] = members, cdeg[c] = sum of member degrees (both zeroed by the caller).
@@ -217,6 +221,33 @@ void modularity_bucketed(Ctx& c, const GraphView<typename M::w_t>& g, const int3
 // acc slots).  Integer mode exact.
 template <class M>
 void modularity(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* C, typename M::a_t* tot, Ctrl* ctrl);
+
+// ---------------------------------------------------------------- batch.cu
+// Union setup of a batch: vg0 (graph of every vertex), ao (arc range of every graph), graph-local
+// targets -> union ids (bad targets counted in ctrl->cnt[1]), GraphCtl initialised from vo.
+void batch_setup(Ctx& c, const int64_t* vo, int32_t G, int64_t n, const int64_t* offs, int64_t n_arcs,
+                 const int32_t* tg_local, int32_t* tg_union, int64_t* ao, int32_t* vg0, GraphCtl* gc, Ctrl* ctrl);
+// 2m per graph from K (pass 0); ctrl->cnt[6] counts integer graphs with 2m >= 2^31.
+template <class M>
+void batch_two_m(Ctx& c, GraphCtl* gc, int32_t G, const typename M::a_t* K, Ctrl* ctrl);
+void batch_move_setup(Ctx& c, GraphCtl* gc, int32_t G, int max_iterations);
+// Per-graph tolerance test after an iteration; ctrl->done once every graph is done.
+template <class M>
+void batch_finish(Ctx& c, Ctrl* ctrl, GraphCtl* gc, int32_t G);
+// Pass tests per graph and next-level bases; ctrl->acc_i[3] = next level's vertex count.
+void batch_pass_end(Ctx& c, GraphCtl* gc, int32_t G, const int64_t* newid, double tau_agg, bool last, Ctrl* ctrl);
+// Renumbering, dendrogram lookup, next-level K and vg, graphs that stop leave the union.
+template <class A>
+void batch_next_level(Ctx& c, int32_t* Cp, int64_t n_cur, const int64_t* newid, const int32_t* vg, GraphCtl* gc,
+                      int32_t G, int32_t* C, int64_t n0, const int32_t* vg0, const A* sig, const int32_t* occ,
+                      A* k_next, int32_t* vg_next);
+// Graphs still in the pass loop (max_passes = 0): singleton communities with local ids.
+void batch_close(Ctx& c, int32_t* C, int64_t n0, const int32_t* vg0, GraphCtl* gc, int32_t G);
+// Eq. 1 per graph on the input graphs (C graph-local); results in gc[g].q.
+template <class M>
+void batch_modularity(Ctx& c, const GraphView<typename M::w_t>& g0, const int32_t* C, const int32_t* vg0, GraphCtl* gc,
+                      int32_t G, const int64_t* vo, const int32_t* dperm, const int64_t* hb, typename M::a_t* intra,
+                      typename M::a_t* tot, int64_t n_comm_total);
 
 // ---------------------------------------------------------------- validate.cu
 // ctrl->cnt[0..3] receive: bad offsets, bad targets, bad weights, asymmetry hash; ctrl->acc_f[0]

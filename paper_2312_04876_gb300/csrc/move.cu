@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
     tk = skeys + gib * SL;
     tv = svals + gib * SL;
   }
-  const A two_m = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
+  const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
+  GraphCtl* const gcs = a.st.gc;
   const int64_t n_cur = a.g.n;
   unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
   double acc_f = 0.0;
@@ -111,6 +112,13 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
   for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < a.count; idx += ngroups) {
     const int32_t i = a.list[idx];
     if (lane == 0) ctr[0]++;
+    // batched run: the graph of i, skipped once its local-moving phase has converged
+    GraphCtl* gcv = nullptr;
+    if (gcs) {
+      gcv = gcs + a.st.vg[i];
+      if (*(volatile int32_t*)&gcv->done) continue;
+    }
+    const A two_m = gcv ? (M::is_fp ? (A)gcv->two_m_f : (A)gcv->two_m_i) : two_m_all;
     if (a.pruning) {
       int f = 0;
       if (lane == 0) {
@@ -184,7 +192,10 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
           a.st.mv_to[i] = bc;
         }
         a.st.Cp[i] = bc;
-        if (M::is_fp) {
+        if (gcv) {
+          if (M::is_fp) atomicAdd(&gcv->sum_f, (double)best);
+          else atomic_add_u128(&gcv->sum_lo, &gcv->sum_hi, (unsigned long long)best, 0ULL);
+        } else if (M::is_fp) {
           acc_f += (double)best;
         } else {
           const unsigned long long b = (unsigned long long)best;

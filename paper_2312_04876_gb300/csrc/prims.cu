@@ -132,7 +132,7 @@ __device__ __forceinline__ int sort_key(KeyDesc kd, int64_t i, const int64_t* rb
   int b = degree_bucket(rend[i] - rbeg[i]);
   if (kd.kind == 0 || b < 0) return b;
   if (kd.kind == 3)  // hash class of the fast schedule
-    return (int)(hash3(kd.seed, (uint64_t)kd.pass, (uint64_t)i) % (uint64_t)kd.classes) * kNumBuckets + b;
+    return (int)(hash3(kd.seed, (uint64_t)kd.pass, local_id(kd.seg, (int32_t)i)) % (uint64_t)kd.classes) * kNumBuckets + b;
   return colour[i] * kNumBuckets + b;
 }
 

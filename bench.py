@@ -271,6 +271,82 @@ def run_batch_bench(args):
     return 0
 
 
+def run_serve_bench(args):
+    """Serving workload: a Poisson stream of mixed graphs (half SBM, half R-MAT, 1e4-2e7 edges)
+    against the continuous-batching server and against the one-at-a-time server (one lane, one
+    graph per batch), at arrival rates that are multiples of the one-at-a-time capacity."""
+    import numpy as np
+    import torch
+    import graphgen as gg
+    import paper_2312_04876_gb300 as lv
+    from concurrent.futures import ThreadPoolExecutor
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    R = args.serve_requests
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        reqs = list(ex.map(lambda r: gg.serving_request(5, r), range(R)))
+    gen_s = time.perf_counter() - t0
+    budget = int(args.serve_budget_gb * (1 << 30))
+    kw = dict(mode=args.mode, validate=0)
+
+    def run_stream(lanes, max_graphs, rate):
+        srv = lv.Server(local, hbm_budget_bytes=budget, lanes=lanes, max_batch_graphs=max_graphs, **kw)
+        # warm the lanes' workspaces with the largest requests
+        for t in [srv.submit(g.offsets, g.targets, g.weights) for g in sorted(reqs, key=lambda g: -g.n_arcs)[:lanes]]:
+            srv.result(t)
+        gaps = [-np.log(((gg.hash3(9, r, 0) >> 11) + 1) / 9007199254740992.0) / rate for r in range(R)]
+        tickets = []
+        start = time.perf_counter()
+        due = start
+        for g, gap in zip(reqs, gaps):
+            due += gap if rate > 0 else 0.0
+            now = time.perf_counter()
+            if due > now:
+                time.sleep(due - now)
+            tickets.append(srv.submit(g.offsets, g.targets, g.weights))
+        lat, qs, bs = [], [], []
+        for t in tickets:
+            _, info = srv.result(t)
+            lat.append(info["latency_ms"])
+            qs.append(info["modularity"])
+            bs.append(info["batch_graphs"])
+        span = time.perf_counter() - start
+        srv.close()
+        return {"rate": rate, "graphs_per_second": R / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(np.mean(bs)), "q": qs}
+
+    # one-at-a-time capacity: everything submitted at once to one lane with one graph per batch
+    cap1 = run_stream(1, 1, 0.0)
+    base = cap1["graphs_per_second"]
+    rows = []
+    for mult in args.serve_rates:
+        rate = mult * base
+        b = run_stream(args.serve_lanes, 256, rate)
+        o = run_stream(1, 1, rate)
+        dq = max(abs(x - y) for x, y in zip(b["q"], o["q"]))
+        rows.append({"rate_x_one_at_a_time": mult, "rate_graphs_per_s": rate,
+                     "batched": {k: v for k, v in b.items() if k != "q"},
+                     "one_at_a_time": {k: v for k, v in o.items() if k != "q"}, "max_abs_dq": dq})
+    satb = run_stream(args.serve_lanes, 256, 0.0)  # saturated: everything at once
+    arcs = [g.n_arcs for g in reqs]
+    line = {
+        "metric": "louvain_serving_graphs_per_second", "value": satb["graphs_per_second"], "unit": "graphs/s",
+        "n_gpus": 1, "steps": R, "warmup": args.serve_lanes, "ms_per_step": 1e3 / satb["graphs_per_second"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{R} requests, half planted-partition SBM, half R-MAT (0.57,0.19,0.19,0.05), "
+                               "edge counts log-uniform [1e4, 2e7], Poisson arrivals",
+                   "mode": args.mode, "budget_gb": args.serve_budget_gb, "lanes": args.serve_lanes,
+                   "arcs_total": int(sum(arcs)), "arcs_max": int(max(arcs))},
+        "saturated": {k: v for k, v in satb.items() if k != "q"},
+        "one_at_a_time_capacity": {k: v for k, v in cap1.items() if k != "q"},
+        "speedup_saturated": satb["graphs_per_second"] / base, "rates": rows, "generate_s": gen_s,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,9 +354,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--mode", default="fast", choices=["fast", "deterministic"])
-    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batch", "serve"])
     ap.add_argument("--batch-graphs", type=int, default=4096, help="batch workload: number of graphs")
     ap.add_argument("--batch-n-hi", type=float, default=2e5, help="batch workload: largest vertex count")
+    ap.add_argument("--serve-requests", type=int, default=64, help="serving workload: requests in the stream")
+    ap.add_argument("--serve-lanes", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0, 2.0, 4.0],
+                    help="serving workload: arrival rates as multiples of the one-at-a-time capacity")
     ap.add_argument("--single-sample", type=int, default=0,
                     help="batch workload: time the one-at-a-time path on the first K graphs only (0 = all)")
     ap.add_argument("--fast-classes", type=int, default=None, help="random vertex classes of the fast schedule")
@@ -295,6 +376,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch_bench(args)
+    if args.workload == "serve":
+        return run_serve_bench(args)
 
     import numpy as np
     import torch

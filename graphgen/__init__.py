@@ -203,3 +203,29 @@ def concat(graphs):
     tg = np.concatenate([g.targets for g in graphs]) if G else np.zeros(0, np.int32)
     wt = np.concatenate([g.weights for g in graphs]) if G else np.zeros(0, np.int32)
     return vo, offs, tg.astype(np.int32, copy=False), wt
+
+
+def serving_request(base_seed: int, r: int) -> Graph:
+    """Request r of the mixed serving stream: target edge count E log-uniform in [1e4, 2e7]; even
+    r: a planted-partition SBM (average degree log-uniform in [4, 64], 2-64 blocks, p_out/p_in =
+    0.02, unit weights); odd r: R-MAT (0.57, 0.19, 0.19, 0.05) at scale ceil(log2(E / 16)) with the
+    edge factor that makes the draws closest to E, int32 weights 1..8."""
+    import math
+    u = lambda k: ((hash3(base_seed, r, k) >> 11) + 1) / 9007199254740992.0  # (0, 1]
+    E = math.exp(math.log(1e4) + u(1) * (math.log(2e7) - math.log(1e4)))
+    seed = hash3(base_seed, r, 0) & 0x7FFFFFFFFFFFFFFF
+    if r % 2 == 0:
+        d = math.exp(math.log(4.0) + u(2) * (math.log(64.0) - math.log(4.0)))
+        n = max(16, int(2.0 * E / d))
+        k = 2 + int(hash3(base_seed, r, 3) % 63)
+        k = min(k, n)
+        s = n / k
+        p_in = min(1.0, d / ((s - 1.0) + 0.02 * (n - s)))
+        g = sbm(n, k, p_in, 0.02 * p_in, seed, W_UNIT)
+        g.name = f"serve_sbm[{r}](n={n},k={k})"
+        return g
+    scale = max(1, math.ceil(math.log2(E / 16.0)))
+    ef = max(1, round(E / (1 << scale)))
+    g = rmat(scale, ef, 0.57, 0.19, 0.19, seed, W_INT8)
+    g.name = f"serve_rmat[{r}](scale={scale},ef={ef})"
+    return g

@@ -161,6 +161,51 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
                                  louvain_wtype wtype, const louvain_params* p, void* stream, int32_t* d_membership,
                                  louvain_graph_result* results, louvain_result* res);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop (a throughput extension; the paper has no
+ * counterpart).  Requests are host CSRs (int64 offsets, graph-local int32 targets, weights).
+ * `lanes` worker threads, each with its own CUDA stream and workspace, take every queued request
+ * that fits (at most max_batch_graphs graphs and max_batch_arcs arcs per batch, 0 = no arc cap)
+ * whenever they are free and run them as one louvain_run_batch call, so requests arriving while
+ * others run are admitted as lanes and memory free up, and the lanes' work overlaps on the device.
+ * Device memory: every batch reserves an upper bound of what it needs (256 B per vertex + 72 B
+ * per arc + 64 MiB) and the reservations of all lanes never exceed hbm_budget_bytes; each result
+ * is the one louvain_run gives the graph alone (deterministic mode: identical).
+ * --------------------------------------------------------------------------------------------- */
+typedef struct louvain_server_s* louvain_server;
+
+typedef struct {
+  int32_t ready;                 /* 1 when the request has finished (then the fields below are set) */
+  int32_t status;                /* louvain_status of the request */
+  louvain_graph_result result;
+  double latency_ms;             /* submit -> membership in the caller's buffer (host steady clock) */
+  double queue_ms;               /* submit -> its batch started */
+  int32_t batch_graphs;          /* graphs in the batch it ran in */
+  int32_t reserved;
+} louvain_serve_result;
+
+/* Start a server on `device` with the given parameters (mode, tolerances, seed ...).
+ * LOUVAIN_ERR_INVALID for lanes outside [1, 64], max_batch_graphs < 1, a zero budget. */
+louvain_status louvain_serve_create(louvain_server* s, int device, size_t hbm_budget_bytes, int32_t lanes,
+                                    int32_t max_batch_graphs, int64_t max_batch_arcs, const louvain_params* p);
+
+/* Queue one graph.  The host arrays (offsets [n+1] with offsets[0] = 0 and offsets[n] = n_arcs,
+ * targets and weights [n_arcs]) are read, and h_membership [n] written, by the server until the
+ * request's result has been collected with louvain_serve_poll: the caller keeps them alive.
+ * *ticket identifies the request.  LOUVAIN_ERR_OOM if the graph alone exceeds the budget,
+ * LOUVAIN_ERR_BUSY after louvain_serve_destroy has begun. */
+louvain_status louvain_serve_submit(louvain_server s, int64_t n, int64_t n_arcs, const int64_t* h_offsets,
+                                    const int32_t* h_targets, const void* h_weights, louvain_wtype wtype,
+                                    int32_t* h_membership, uint64_t* ticket);
+
+/* Result of a request, waiting up to wait_ms milliseconds (0 = do not wait).  out->ready = 0 if it
+ * has not finished; once a finished result is returned the ticket is released.  Unknown ticket:
+ * LOUVAIN_ERR_INVALID. */
+louvain_status louvain_serve_poll(louvain_server s, uint64_t ticket, int32_t wait_ms, louvain_serve_result* out);
+
+/* Finish the queued and running requests, then stop the lanes and free everything. */
+void louvain_serve_destroy(louvain_server s);
+
 /* louvain_run for HOST buffers: copies the CSR to the device (through the handle's workspace),
  * runs, and copies the membership back to h_membership[n].  Pinned host memory gives the
  * fastest copies; pageable memory works.  The copies are part of the call. */

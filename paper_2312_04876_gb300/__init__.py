@@ -16,7 +16,7 @@ from dataclasses import dataclass, field
 from . import _native
 from ._native import MODE_DETERMINISTIC, MODE_FAST, W_FP32, W_INT32, Params, PassStats, Result
 
-__all__ = ["Louvain", "LouvainError", "default_params", "MODE_DETERMINISTIC", "MODE_FAST"]
+__all__ = ["Louvain", "LouvainError", "Server", "default_params", "MODE_DETERMINISTIC", "MODE_FAST"]
 
 
 class LouvainError(RuntimeError):
@@ -62,6 +62,80 @@ def exclusive_scan_static(values, out=None, stream=None):
     if st != _native.OK:
         raise LouvainError(st, f"louvain_exclusive_scan_static(count={n}) failed")
     return out, int(tot.value)
+
+
+class Server:
+    """Continuous-batching request loop (louvain_serve_*): host CSRs in, memberships out.
+
+        srv = Server(device=0, hbm_budget_bytes=40 << 30, lanes=4, mode="deterministic")
+        t = srv.submit(offsets, targets, weights)        # numpy arrays, kept alive by the server object
+        membership, info = srv.result(t)                 # waits; info: modularity, latency_ms, ...
+    """
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 40 << 30, lanes: int = 4,
+                 max_batch_graphs: int = 256, max_batch_arcs: int = 0, params: Params | None = None, **overrides):
+        self._lib = _native.load()
+        self._s = ctypes.c_void_p()
+        p = params if params is not None else default_params(**overrides)
+        st = self._lib.louvain_serve_create(ctypes.byref(self._s), device, hbm_budget_bytes, lanes, max_batch_graphs,
+                                            max_batch_arcs, ctypes.byref(p))
+        if st != _native.OK:
+            raise LouvainError(st, "louvain_serve_create failed")
+        self._keep = {}
+
+    def submit(self, offsets, targets, weights) -> int:
+        import numpy as np
+        o = np.ascontiguousarray(offsets, dtype=np.int64)
+        t = np.ascontiguousarray(targets, dtype=np.int32)
+        fp = np.asarray(weights).dtype == np.float32
+        w = np.ascontiguousarray(weights, dtype=np.float32 if fp else np.int32)
+        n = len(o) - 1
+        out = np.empty(max(n, 0), dtype=np.int32)
+        tk = ctypes.c_uint64()
+        st = self._lib.louvain_serve_submit(self._s, n, len(t), o.ctypes.data, t.ctypes.data, w.ctypes.data,
+                                            W_FP32 if fp else W_INT32, out.ctypes.data, ctypes.byref(tk))
+        if st != _native.OK:
+            raise LouvainError(st, "louvain_serve_submit failed")
+        self._keep[tk.value] = (o, t, w, out)
+        return tk.value
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        """(membership, info) once finished, else None."""
+        r = _native.ServeResult()
+        st = self._lib.louvain_serve_poll(self._s, ticket, wait_ms, ctypes.byref(r))
+        if st != _native.OK:
+            raise LouvainError(st, f"louvain_serve_poll({ticket}) failed")
+        if not r.ready:
+            return None
+        _, _, _, out = self._keep.pop(ticket)
+        if r.status != _native.OK:
+            raise LouvainError(r.status, f"request {ticket} failed")
+        info = dict(modularity=r.result.modularity, passes=r.result.passes,
+                    total_iterations=r.result.total_iterations, n_communities=r.result.n_communities,
+                    latency_ms=r.latency_ms, queue_ms=r.queue_ms, batch_graphs=r.batch_graphs)
+        return out, info
+
+    def result(self, ticket: int, timeout_s: float = 600.0):
+        import time
+        t_end = time.monotonic() + timeout_s
+        while True:
+            got = self.poll(ticket, 200)
+            if got is not None:
+                return got
+            if time.monotonic() > t_end:
+                raise TimeoutError(f"request {ticket} not finished after {timeout_s} s")
+
+    def close(self):
+        if self._s:
+            self._lib.louvain_serve_destroy(self._s)
+            self._s = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 @dataclass

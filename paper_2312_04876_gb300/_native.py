@@ -39,6 +39,12 @@ class GraphResult(ctypes.Structure):
                 ("n_communities", ctypes.c_int64)]
 
 
+class ServeResult(ctypes.Structure):
+    _fields_ = [("ready", ctypes.c_int32), ("status", ctypes.c_int32), ("result", GraphResult),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("batch_graphs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("algorithmic_bytes", ctypes.c_double)]
@@ -66,6 +72,11 @@ SIGNATURES = {
     "louvain_exclusive_scan": (_I32, [_V, _V, _V, _I64, _V, ctypes.POINTER(_I64)]),
     "louvain_kernel_profile": (_I32, [_V, ctypes.POINTER(KernelStat), _I32, ctypes.POINTER(_I32)]),
     "louvain_exclusive_scan_static": (_I32, [_V, _V, _I64, _V, ctypes.POINTER(_I64)]),
+    "louvain_serve_create": (_I32, [ctypes.POINTER(_V), ctypes.c_int, ctypes.c_size_t, _I32, _I32, _I64,
+                                    ctypes.POINTER(Params)]),
+    "louvain_serve_submit": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, _V, ctypes.POINTER(ctypes.c_uint64)]),
+    "louvain_serve_poll": (_I32, [_V, ctypes.c_uint64, _I32, ctypes.POINTER(ServeResult)]),
+    "louvain_serve_destroy": (None, [_V]),
     "louvain_run_batch": (_I32, [_V, _I32, ctypes.POINTER(_I64), _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V,
                                  _V, ctypes.POINTER(GraphResult), ctypes.POINTER(Result)]),
 }

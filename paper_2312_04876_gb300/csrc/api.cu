@@ -796,6 +796,32 @@ louvain_status check_graph_args(louvain_handle h, int64_t n, int64_t n_arcs, con
 
 }  // namespace
 
+// ------------------------------------------------------------------ hooks of the serving runtime
+namespace lv {
+size_t handle_device_bytes(louvain_handle h) { return h ? total_bytes(h->ws) : 0; }
+void handle_set_budget(louvain_handle h, size_t bytes) {
+  if (h) h->budget = bytes;
+}
+// Frees every device buffer the handle caches (they are re-allocated on the next call).
+void handle_trim(louvain_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  Workspace& ws = h->ws;
+  free_all(ws.core);
+  free_all(ws.keys_alloc);
+  free_all(ws.gt_alloc);
+  free_all(ws.in_alloc);
+  free_all(ws.batch_alloc);
+  ws.n_cap = ws.a_cap = -1;
+  ws.key_cap = 0;
+  ws.gt_slots_total = 0;
+  ws.in_n = ws.in_a = -1;
+  ws.b_graphs = ws.b_n = ws.b_a = -1;
+  ws.gc = nullptr;
+  ws.ctrl = nullptr;
+}
+}  // namespace lv
+
 // =====================================================================================
 extern "C" {
 
@@ -861,6 +887,7 @@ void louvain_destroy(louvain_handle h) {
   free_all(h->ws.keys_alloc);
   free_all(h->ws.gt_alloc);
   free_all(h->ws.in_alloc);
+  free_all(h->ws.batch_alloc);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
   if (h->pin) cudaFreeHost(h->pin);
@@ -946,6 +973,10 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
       results[k].passes = gcs[k].passes;
       results[k].total_iterations = gcs[k].total_iterations;
       results[k].n_communities = gcs[k].n_comm;
+      if (graph_vtx_offs[k + 1] == graph_vtx_offs[k] && p->max_passes > 0) {
+        results[k].passes = 1;  // as louvain_run: one empty pass
+        results[k].total_iterations = p->max_iterations > 0 ? 1 : 0;
+      }
     }
     ncomm += gcs[k].n_comm;
     if (gcs[k].passes > max_pass) max_pass = gcs[k].passes;
@@ -991,6 +1022,16 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
     if ((s = validate_graph(h, c, n, n_arcs, d_offsets, d_targets, d_weights, fp)) != LOUVAIN_OK) return s;
   }
   RunOut out;
+  if (n == 0 && p->max_passes > 0) {
+    // an empty graph still takes one (empty) pass whose single iteration converges at once
+    out.passes = 1;
+    out.total_iterations = p->max_iterations > 0 ? 1 : 0;
+    if (stats && stats_cap > 0) {
+      std::memset(&stats[0], 0, sizeof(stats[0]));
+      stats[0].iterations = out.total_iterations;
+      if (n_stats) *n_stats = 1;
+    }
+  }
   if (n > 0) {
     if (fp)
       s = run_impl<FpMode>(h, c, n, n_arcs, d_offsets, d_targets, reinterpret_cast<const float*>(d_weights), *p,

@@ -249,6 +249,11 @@ void batch_modularity(Ctx& c, const GraphView<typename M::w_t>& g0, const int32_
                       int32_t G, const int64_t* vo, const int32_t* dperm, const int64_t* hb, typename M::a_t* intra,
                       typename M::a_t* tot, int64_t n_comm_total);
 
+// ---------------------------------------------------------------- api.cu hooks (host)
+size_t handle_device_bytes(louvain_handle h);       // device bytes the handle holds
+void handle_set_budget(louvain_handle h, size_t bytes);  // cap of its further allocations (0 = none)
+void handle_trim(louvain_handle h);                 // free everything it caches
+
 // ---------------------------------------------------------------- validate.cu
 // ctrl->cnt[0..3] receive: bad offsets, bad targets, bad weights, asymmetry hash; ctrl->acc_f[0]
 // the weight total (double), ctrl->acc_i[0] the integer weight total (saturating).

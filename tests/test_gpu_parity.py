@@ -201,6 +201,9 @@ def test_empty_and_edgeless(L):
     o, t, w = dev(g0)
     mem, res = L.run(o, t, w)
     assert mem.numel() == 0 and res.modularity == 0.0
+    # the oracle takes one empty pass with one iteration; so does the library
+    _, _, ref_passes, ref_stats = oracle.louvain(g0.offsets, g0.targets, g0.weights, oracle.default_params())
+    assert res.passes == ref_passes and res.total_iterations == ref_stats[0]["iterations"]
     g = gg.from_edges(7, [])
     o, t, w = dev(g)
     mem, res = L.run(o, t, w)

@@ -1,0 +1,99 @@
+"""Serving (louvain_serve_*): continuous batching over the batched path.
+
+Each result must be the same alone (louvain_run on the graph by itself) and in the mix (served
+together with other requests, in whatever batches the lanes formed): identical memberships and
+modularity in deterministic mode, a valid partition within 0.005 of the oracle in fast mode.
+The admission budget is respected: a request larger than the budget is refused, and a budget that
+holds only one request at a time still completes every request with the same results.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def request_mix():
+    gs = []
+    for k in range(6):
+        gs.append(gg.batch_sbm(7, k, n_lo=500.0, n_hi=20000.0))
+    for s in (10, 11, 12, 13):
+        gs.append(gg.rmat(s, weights=gg.W_INT8, seed=s))
+    gs.append(gg.from_edges(1, []))
+    gs.append(gg.grid(40, 50, 0.1, 0.01, 3))
+    return gs
+
+
+def alone(g, **kw):
+    import paper_2312_04876_gb300 as lv
+    L = lv.Louvain(0)
+    d = torch.device("cuda:0")
+    m, r = L.run(*(torch.from_numpy(a).to(d) for a in (g.offsets, g.targets, g.weights)), **kw)
+    out = m.cpu().numpy().copy(), r.modularity
+    L.close()
+    return out
+
+
+@pytest.mark.parametrize("lanes,max_graphs", [(1, 64), (3, 4), (4, 1)])
+def test_same_alone_and_in_the_mix(cuda_ok, lanes, max_graphs):
+    import paper_2312_04876_gb300 as lv
+    graphs = request_mix()
+    srv = lv.Server(0, hbm_budget_bytes=8 << 30, lanes=lanes, max_batch_graphs=max_graphs, mode="deterministic")
+    tickets = [srv.submit(g.offsets, g.targets, g.weights) for g in graphs]
+    got = [srv.result(t) for t in tickets]
+    srv.close()
+    for g, (m, info) in zip(graphs, got):
+        m1, q1 = alone(g, mode="deterministic")
+        assert np.array_equal(m, m1)
+        assert info["modularity"] == q1
+        assert info["latency_ms"] >= info["queue_ms"] >= 0.0
+    if max_graphs > 1 and lanes == 1:
+        # requests that queued behind the first batch ran together
+        assert max(info["batch_graphs"] for _, info in got) > 1
+
+
+def test_tight_budget_serialises_but_completes(cuda_ok):
+    import paper_2312_04876_gb300 as lv
+    graphs = [gg.rmat(13, weights=gg.W_INT8, seed=s) for s in range(4)]
+    # room for one of these requests at a time (estimate 256 B/vertex + 72 B/arc + 64 MiB)
+    var = 256 * (graphs[0].n + 1) + 72 * max(g.n_arcs for g in graphs)
+    budget = var + (64 << 20) + var // 2  # one request fits, two do not
+    srv = lv.Server(0, hbm_budget_bytes=budget, lanes=3, max_batch_graphs=8, mode="deterministic")
+    tickets = [srv.submit(g.offsets, g.targets, g.weights) for g in graphs]
+    got = [srv.result(t) for t in tickets]
+    srv.close()
+    for g, (m, info) in zip(graphs, got):
+        m1, q1 = alone(g, mode="deterministic")
+        assert np.array_equal(m, m1) and info["modularity"] == q1
+        assert info["batch_graphs"] == 1
+
+
+def test_request_over_budget_is_refused(cuda_ok):
+    import paper_2312_04876_gb300 as lv
+    g = gg.rmat(12, weights=gg.W_INT8, seed=1)
+    srv = lv.Server(0, hbm_budget_bytes=1 << 20, lanes=1)
+    with pytest.raises(lv.LouvainError):
+        srv.submit(g.offsets, g.targets, g.weights)
+    srv.close()
+
+
+def test_fast_mode_serving_quality(cuda_ok):
+    import paper_2312_04876_gb300 as lv
+    graphs = request_mix()
+    srv = lv.Server(0, hbm_budget_bytes=8 << 30, lanes=2, max_batch_graphs=16, mode="fast")
+    tickets = [srv.submit(g.offsets, g.targets, g.weights) for g in graphs]
+    got = [srv.result(t) for t in tickets]
+    srv.close()
+    for g, (m, info) in zip(graphs, got):
+        nc = info["n_communities"]
+        assert m.min() == 0 and m.max() == nc - 1 and len(np.unique(m)) == nc
+        q = oracle.modularity(g.offsets, g.targets, g.weights, m)
+        assert abs(q - info["modularity"]) <= 1e-12
+        _, ref_q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params())
+        assert q >= ref_q - 0.005

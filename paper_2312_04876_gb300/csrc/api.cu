@@ -53,6 +53,7 @@ struct Workspace {
   int64_t gt_slots_total = 0;
   GlobalTable gt;
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
+  int32_t* glist = nullptr;   // [gcap] giant vertices of a pass, class by class
   int64_t* ctab = nullptr;    // [n] table offset of each giant community (-1 otherwise)
   int32_t* csz = nullptr;     // [n] table size of each giant community
   GiantPlan gp, gpv;          // plans of giant vertices / communities and of giant members
@@ -191,12 +192,14 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   for (GiantPlan* gp : {&ws.gp, &ws.gpv})
     ok = ok && dalloc(h, d, &gp->chunk_off, gcap + 1) && dalloc(h, d, &gp->tab_off, gcap + 1) &&
          dalloc(h, d, &gp->slice_off, gcap + 1) && dalloc(h, d, (int32_t**)&gp->kid, gcap) &&
-         dalloc(h, d, &gp->moved, gcap) && dalloc(h, d, (long long**)&gp->part_s, scap) &&
+         dalloc(h, d, &gp->moved, gcap) && dalloc(h, d, &gp->active, gcap) &&
+         dalloc(h, d, (long long**)&gp->part_s, scap) &&
          dalloc(h, d, &gp->part_c, scap) && dalloc(h, d, &gp->cowner, ccap) && dalloc(h, d, &gp->sowner, scap);
   for (GiantPlan* gp : {&ws.gp, &ws.gpv}) {
     gp->chunk_cap = ccap;
     gp->slice_cap = scap;
   }
+  ok = ok && dalloc(h, d, &ws.glist, gcap);
   ok = ok && dalloc(h, d, &ws.newid, n1 + 1) && dalloc(h, d, &ws.coff, n1 + 1) && dalloc(h, d, &ws.cdeg, n1 + 1) &&
        dalloc(h, d, &ws.len, n1 + 1) && dalloc(h, d, &ws.jrc, n1 + 16) &&
        dalloc(h, d, &ws.tile_tmp, scan_tmp_elems((int64_t)kNumBuckets * n1 + 8) + 8);  // class sort scans 5 n keys
@@ -456,8 +459,19 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     ho.assign(q, q + nkeys + 1);
   }
   if (event_at(h, ev_colour_done)) cudaEventRecord(h->events[ev_colour_done], c.s);
-  // table pool for the giant vertices (each class uses it from its start; tables are cleared)
+  // giant vertices of every class in one list and one plan for the whole pass (each giant owns a
+  // table of the pool; the scans leave every table empty)
+  std::vector<int64_t> gofs((size_t)ncol + 1, 0);
+  for (int cl = 0; cl < ncol; cl++) {
+    const size_t base = (size_t)cl * kNumBuckets;
+    const int64_t cnt = ho[base + kNumBuckets] - ho[base + kNumBuckets - 1];
+    if (cnt > 0)
+      cudaMemcpyAsync(ws.glist + gofs[cl], ws.perm + ho[base + kNumBuckets - 1], (size_t)cnt * sizeof(int32_t),
+                      cudaMemcpyDeviceToDevice, c.s);
+    gofs[cl + 1] = gofs[cl] + (cnt > 0 ? cnt : 0);
+  }
   if (giant_slots > 0 && (s = ensure_pool(h, c, giant_slots)) != LOUVAIN_OK) return s;
+  if (gofs[ncol] > 0) giant_move_plan<M>(c, g, ws.glist, gofs[ncol], ws.gp, ws.ctrl);
   move_setup(c, ws.ctrl, tau, p.max_iterations);
   if (gc) batch_move_setup(c, gc, n_graphs, p.max_iterations);
   const bool pruning = p.pruning != 0;
@@ -472,7 +486,7 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
           if (cnt <= 0) continue;
           const int pm = prof_begin(h, c);
           if (b < kNumBuckets - 1) move_bucket<M>(c, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
-          else giant_move<M>(c, g, st, ws.perm + ho[base + b], cnt, ws.gp, !det, pruning);
+          else giant_move<M>(c, g, st, ws.glist, gofs[cl], gofs[cl + 1], ws.gp, !det, pruning);
           prof_end(h, c, kLm0 + b, pm);
         }
         if (det) {

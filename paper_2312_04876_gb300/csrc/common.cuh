@@ -257,6 +257,13 @@ __device__ __forceinline__ void group_argmax(S& s, int32_t& c, S* ss, int32_t* s
   }
 }
 
+// OR of a predicate over the group (uniform result; for a block it is also a barrier).
+template <int G>
+__device__ __forceinline__ bool group_any(bool p) {
+  if constexpr (G <= 32) return __any_sync(Grp<G>::mask(), p);
+  else return __syncthreads_or(p ? 1 : 0) != 0;
+}
+
 // Broadcast lane 0's value to the group.
 template <int G, class T>
 __device__ __forceinline__ T group_bcast(T v, T* scratch) {

@@ -1,20 +1,21 @@
-// giant.cu -- the multi-block path for giant rows (degree bucket 4, > 2048 arcs).
+// giant.cu -- the multi-block path for giant rows (degree bucket 5, > 4096 arcs).
 //
 // A hub vertex (R-MAT hubs reach 10^5 arcs) or a giant community (10^6-10^7 member arcs after a
 // pass) handled by one block serialises a whole launch on one SM.  Here the work of a giant is cut
 // into arc chunks and table slices that every SM shares:
-//   plan    one block: per giant its chunk count, table size (a power of two >= 2 x its distinct-key
-//           bound) and slice count; exclusive scans give each giant its chunk / slot / slice range
-//           in a shared pool of global-memory tables, and owner arrays map every chunk and slice
-//           back to its giant in one load;
-//   insert  grid-stride over chunks of 2048 arcs: a block first sums its chunk per key in a
-//           shared-memory table (K_i->c, scanCommunities), then adds each distinct key once to the
-//           giant's global table with L2 atomics;
-//   scan    grid-stride over slices of 8192 slots (16-byte key loads): local move scores every
-//           candidate with the Eq. 2 numerator and keeps the slice's best; merge emits the slice's
-//           (community, weight) pairs into the holey row of the community.  Every occupied slot
-//           is cleared, so the pool is all-empty between uses;
-//   decide  (local move) per giant: best over its slices, then the move exactly as the per-vertex
+//   plan    per giant its chunk count, table size (a power of two >= 2 x its distinct-key bound)
+//           and slice count; a one-block scan gives each giant its chunk / slot / slice range in a
+//           shared pool of global-memory tables; owner arrays map every chunk and slice back to its
+//           giant (binary search, fully parallel).  The local-moving plan covers every giant of a
+//           pass at once (the giants listed class by class), so it is built once per pass; each
+//           iteration of a class only decides which of its giants are active (pruning flags);
+//   insert  grid-stride over chunks of 2048 arcs: K_i->c into the giant's global table with L2
+//           atomics, K_i->d in registers (scanCommunities);
+//   scan    local move: one warp per range of 1024 table slots (16-byte key loads) scores every
+//           candidate with the Eq. 2 numerator and keeps the range's best; merge: one warp per
+//           128-slot slice emits the slice's (community, weight) pairs into the holey row of the
+//           community.  Every occupied slot is cleared, so the pool is all-empty between uses;
+//   decide  (local move) per giant: best over its ranges, then the move exactly as the per-vertex
 //           kernels make it;
 //   mark    (local move, pruning) grid-stride over chunks of the giants that moved.
 // Merges insert member rows vertex by vertex (members of giant communities, by their own degree
@@ -23,57 +24,58 @@
 
 namespace lv {
 
-constexpr int kChunk = 2048;   // arcs per chunk
-constexpr int kSlice = 128;    // table slots per slice: one warp, one 16-byte key load per lane
-constexpr int kLocLog = 12;    // shared pre-aggregation table: 4096 slots >= 2 x kChunk keys
+constexpr int kChunk = 2048;    // arcs per chunk
+constexpr int kSliceLog = 7;    // merge: 128 table slots per slice, one 16-byte key load per lane
+constexpr int kSlice = 1 << kSliceLog;
+constexpr int kRangeLog = 10;   // local move: 1024 table slots per warp range (8 key loads per lane)
+constexpr int kLocLog = 12;     // shared pre-aggregation table: 4096 slots >= 2 x kChunk keys
 
-// ---------------------------------------------------------------- plan (one block)
-// kind 0: local move, item = vertex list[k], bound = min(deg, n_bound), chunks over its row; a
-//          pruned vertex gets nothing, an active one has its flag cleared (marked processed).
-// kind 1: merge, item = community list[k], bound = min(cdeg, n_bound), no chunks (rows are inserted
-//          member-wise); gix[c] = k.
-// kind 2: chunks only, item = vertex list[k] if its community Cp[i] is giant (gix >= 0).
+// ---------------------------------------------------------------- plan
+// kind 0: local move, item = vertex list[k]: table for min(deg, n_bound) keys, chunks over its row;
+// kind 1: merge, item = community list[k]: table for min(cdeg, n_bound) keys, no chunks (rows are
+//         inserted member-wise); gix[c] = k;
+// kind 2: chunks only, item = vertex list[k] whose community Cp[i] >= 0 is giant (gix >= 0);
 // kind 3: chunks only, every listed row.
-__global__ void __launch_bounds__(1024) k_giant_plan(int kind, const int32_t* list, int64_t m, const int64_t* rbeg,
-                                                     const int64_t* rend, const int64_t* cdeg, int64_t n_bound,
-                                                     uint8_t* flags, int pruning, const int32_t* Cp, int32_t* gix,
-                                                     GiantPlan p, Ctrl* ctrl, const GraphCtl* gc = nullptr,
-                                                     const int32_t* vg = nullptr) {
-  __shared__ int64_t part[3][1024];
-  if (kind == 0 && *(volatile int32_t*)&ctrl->done) return;
-  const int t = threadIdx.x;
-  const int64_t per = (m + 1023) / 1024;
-  const int64_t b = t * per, e = b + per < m ? b + per : m;
-  int64_t sc = 0, st = 0, ss = 0;
-  for (int64_t k = b; k < e; k++) {
+__global__ void k_gplan_counts(int kind, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
+                               const int64_t* cdeg, int64_t n_bound, const int32_t* Cp, int32_t* gix, int slice_log,
+                               GiantPlan p) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = list[k];
     int64_t nch = 0, ts = 0;
     if (kind == 1) {
       const int64_t bound = cdeg[v] < n_bound ? cdeg[v] : n_bound;
       ts = (int64_t)1 << tbl_log2(bound, 6, 31);
+      gix[v] = (int32_t)k;
     } else {
       const int64_t deg = rend[v] - rbeg[v];
-      bool active = true;
-      if (kind == 0 && gc && gc[vg[v]].done) active = false;  // batched: graph converged
-      if (kind == 0 && pruning && active) {
-        active = flags[v] != 0;
-        if (active) flags[v] = 0;
-      }
-      if (kind == 2) active = Cp[v] >= 0 && gix[Cp[v]] >= 0;  // batched: Cp < 0 = graph left
-      if (active) {
+      const bool used = kind != 2 || (Cp[v] >= 0 && gix[Cp[v]] >= 0);
+      if (used) {
         nch = (deg + kChunk - 1) / kChunk;
         if (kind == 0) ts = (int64_t)1 << tbl_log2(deg < n_bound ? deg : n_bound, 6, 31);
       }
     }
     p.chunk_off[k] = nch;
     p.tab_off[k] = ts;
-    p.slice_off[k] = ts ? (ts + kSlice - 1) / kSlice : 0;
-    sc += nch; st += ts; ss += p.slice_off[k];
+    p.slice_off[k] = (ts + ((int64_t)1 << slice_log) - 1) >> slice_log;
+    reinterpret_cast<uint32_t*>(p.kid)[k] = 0u;  // 0u is also 0.0f
+    p.moved[k] = 0;
+    p.active[k] = 0;
   }
+}
+
+// Exclusive scans of the three counts (one block); totals at [m].  A plan that does not fit the
+// capacities runs nothing (chunk and slice totals read 0) and reports the error.
+__global__ void __launch_bounds__(1024) k_gplan_scan(int64_t m, GiantPlan p, Ctrl* ctrl) {
+  __shared__ int64_t part[3][1024];
+  const int t = threadIdx.x;
+  const int64_t per = (m + 1023) / 1024;
+  const int64_t b = t * per, e = b + per < m ? b + per : m;
+  int64_t sc = 0, st = 0, ss = 0;
+  for (int64_t k = b; k < e; k++) { sc += p.chunk_off[k]; st += p.tab_off[k]; ss += p.slice_off[k]; }
   part[0][t] = sc; part[1][t] = st; part[2][t] = ss;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {
-    int64_t v0 = t >= o ? part[0][t - o] : 0, v1 = t >= o ? part[1][t - o] : 0, v2 = t >= o ? part[2][t - o] : 0;
+    const int64_t v0 = t >= o ? part[0][t - o] : 0, v1 = t >= o ? part[1][t - o] : 0, v2 = t >= o ? part[2][t - o] : 0;
     __syncthreads();
     part[0][t] += v0; part[1][t] += v1; part[2][t] += v2;
     __syncthreads();
@@ -83,23 +85,46 @@ __global__ void __launch_bounds__(1024) k_giant_plan(int kind, const int32_t* li
   int64_t rc = t ? part[0][t - 1] : 0, rt = t ? part[1][t - 1] : 0, rs = t ? part[2][t - 1] : 0;
   for (int64_t k = b; k < e; k++) {
     const int64_t nch = p.chunk_off[k], ts = p.tab_off[k], ns = p.slice_off[k];
-    p.chunk_off[k] = rc; p.tab_off[k] = rt; p.slice_off[k] = rs;
-    if (fits) {
-      for (int64_t q = 0; q < nch; q++) p.cowner[rc + q] = (int32_t)k;
-      for (int64_t q = 0; q < ns; q++) p.sowner[rs + q] = (int32_t)k;
-    }
-    if (kind == 1) gix[list[k]] = (int32_t)k;
-    reinterpret_cast<uint32_t*>(p.kid)[k] = 0u;  // 0u is also 0.0f
-    p.moved[k] = 0;
+    // an over-full plan gets empty ranges everywhere, so no kernel touches a chunk or slice
+    p.chunk_off[k] = fits ? rc : 0; p.tab_off[k] = rt; p.slice_off[k] = fits ? rs : 0;
     rc += nch; rt += ts; rs += ns;
   }
   if (t == 1023) {
-    // an over-full plan runs nothing (chunk and slice totals read 0) and reports the error
     p.chunk_off[m] = fits ? tot_c : 0;
     p.tab_off[m] = tot_t;
     p.slice_off[m] = fits ? tot_s : 0;
     if (!fits) atomicOr(&ctrl->error, kErrTableFull);
   }
+}
+
+// Largest k in [0, m) with off[k] <= q (the item whose range holds q).
+__device__ __forceinline__ int32_t owner_of(const int64_t* off, int64_t m, int64_t q) {
+  int64_t lo = 0, hi = m;  // off[lo] <= q < off[hi]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (off[mid] <= q) lo = mid; else hi = mid;
+  }
+  return (int32_t)lo;
+}
+
+__global__ void k_gplan_owners(int64_t m, GiantPlan p) {
+  const int64_t nc = p.chunk_off[m], ns = p.slice_off[m];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += stride)
+    p.cowner[q] = owner_of(p.chunk_off, m, q);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns; q += stride)
+    p.sowner[q] = owner_of(p.slice_off, m, q);
+}
+
+void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
+                const int64_t* cdeg, int64_t n_bound, const int32_t* Cp, int32_t* gix, int slice_log,
+                const GiantPlan& p, Ctrl* ctrl) {
+  const int cap = c.num_sms * 8;
+  k_gplan_counts<<<grid_for(m, kBlock, cap), kBlock, 0, c.s>>>(kind, list, m, rbeg, rend, cdeg, n_bound, Cp, gix,
+                                                              slice_log, p);
+  k_gplan_scan<<<1, 1024, 0, c.s>>>(m, p, ctrl);
+  k_gplan_owners<<<cap, kBlock, 0, c.s>>>(m, p);
+  c.launches += 3;
 }
 
 // ---------------------------------------------------------------- shared pre-aggregation
@@ -132,17 +157,54 @@ __device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* tk, H* tv,
   return ok;
 }
 
+// ---------------------------------------------------------------- local move: activation
+// Giants [k0, k1) of the class: active iff their graph has not converged and (pruning) their flag
+// is set, which is then cleared (processed).  Also resets K_i->d and the moved marks, and counts
+// list entries / processed vertices / arcs.
+template <class W>
+__global__ void k_glm_activate(GraphView<W> g, const int32_t* list, int64_t k0, int64_t k1, uint8_t* flags,
+                               int pruning, const GraphCtl* gc, const int32_t* vg, GiantPlan p, Ctrl* ctrl) {
+  if (*(volatile int32_t*)&ctrl->done) return;
+  unsigned long long act = 0, arcs = 0;
+  for (int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < k1; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = list[k];
+    bool a = !(gc && gc[vg[v]].done);
+    if (a && pruning) {
+      a = flags[v] != 0;
+      if (a) flags[v] = 0;
+    }
+    p.active[k] = a ? 1 : 0;
+    p.moved[k] = 0;
+    reinterpret_cast<uint32_t*>(p.kid)[k] = 0u;
+    if (a) { act++; arcs += (unsigned long long)(g.rend[v] - g.rbeg[v]); }
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    act += __shfl_xor_sync(0xffffffffu, act, o);
+    arcs += __shfl_xor_sync(0xffffffffu, arcs, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][0], (unsigned long long)(k1 - k0));
+    if (act) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][1], act);
+    if (arcs) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][2], arcs);
+  }
+}
+
 // ---------------------------------------------------------------- local move: insert
+// One block per chunk of an active giant; each thread loads its U arcs before their C'[j] gathers
+// and table updates (U memory requests in flight per thread).
 template <class M>
-__global__ void __launch_bounds__(kBlock) k_giant_lm_insert(GraphView<typename M::w_t> g, const int32_t* list, int64_t m,
-                                                            const int32_t* Cp, GiantPlan p, Ctrl* ctrl) {
+__global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t> g, const int32_t* list, int64_t k0,
+                                                       int64_t k1, const int32_t* Cp, GiantPlan p, Ctrl* ctrl) {
   typedef typename M::h_t H;
+  constexpr int U = kChunk / kBlock;  // 8
   __shared__ H red[32];
   if (*(volatile int32_t*)&ctrl->done) return;
-  const int64_t nchunks = p.chunk_off[m];
+  const int64_t q0 = p.chunk_off[k0], q1 = p.chunk_off[k1];
   bool ok = true;
-  for (int64_t q = blockIdx.x; q < nchunks; q += gridDim.x) {
+  for (int64_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
     const int64_t k = p.cowner[q];
+    if (!p.active[k]) continue;  // uniform over the block
     const int32_t i = list[k];
     const int32_t d = Cp[i];
     const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
@@ -152,14 +214,23 @@ __global__ void __launch_bounds__(kBlock) k_giant_lm_insert(GraphView<typename M
     H* tv = reinterpret_cast<H*>(p.vals) + off;
     const int64_t e0 = g.rbeg[i] + (q - p.chunk_off[k]) * kChunk;
     const int64_t e1 = e0 + kChunk < g.rend[i] ? e0 + kChunk : g.rend[i];
+    int32_t jj[U];
+    H ww[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t e = e0 + threadIdx.x + (int64_t)u * kBlock;
+      jj[u] = e < e1 ? g.tg[e] : i;
+      ww[u] = e < e1 ? (H)g.w[e] : H(0);
+    }
+    int32_t cc[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) cc[u] = jj[u] != i ? Cp[jj[u]] : kEmpty;
     H kid = H(0);
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += kBlock) {
-      const int32_t j = g.tg[e];
-      if (j == i) continue;
-      const H wv = (H)g.w[e];
-      const int32_t cj = Cp[j];
-      if (cj == d) kid += wv;
-      else ok &= tbl_add(tk, tv, (unsigned)ts, 32 - lg, cj, wv);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (jj[u] == i) continue;
+      if (cc[u] == d) kid += ww[u];
+      else ok &= tbl_add(tk, tv, (unsigned)ts, 32 - lg, cc[u], ww[u]);
     }
     kid = group_sum<kBlock>(kid, red);
     if (threadIdx.x == 0 && kid != H(0)) atomicAdd(reinterpret_cast<H*>(p.kid) + k, kid);
@@ -167,52 +238,61 @@ __global__ void __launch_bounds__(kBlock) k_giant_lm_insert(GraphView<typename M
   if (!ok) atomicOr(&ctrl->error, kErrTableFull);
 }
 
-// ---------------------------------------------------------------- local move: slice scan
+// ---------------------------------------------------------------- local move: range scan
+// One warp per range of 1024 slots of an active giant's table: 8 steps of one 16-byte key load per
+// lane (tables are >= 64 slots and 64-slot aligned, so loads are aligned and never straddle two
+// tables); the Sigma gathers of a step are issued together.  Writes the range's best to part_s/c.
 template <class M>
-__global__ void __launch_bounds__(kBlock) k_giant_lm_scan(const int32_t* list, int64_t m, const int32_t* Cp,
-                                                          const typename M::a_t* K, const typename M::a_t* Sig,
-                                                          GiantPlan p, Ctrl* ctrl, const GraphCtl* gc,
-                                                          const int32_t* vg) {
+__global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_t k0, int64_t k1, const int32_t* Cp,
+                                                     const typename M::a_t* K, const typename M::a_t* Sig,
+                                                     GiantPlan p, Ctrl* ctrl, const GraphCtl* gc, const int32_t* vg) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
   if (*(volatile int32_t*)&ctrl->done) return;
-  const int64_t nslices = p.slice_off[m];
+  const int64_t r0 = p.slice_off[k0], r1 = p.slice_off[k1];
   const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
   unsigned long long cand = 0;
-  // one warp per slice of 128 slots, one 16-byte key load per lane (tables are >= 64 slots and
-  // 64-slot aligned, so a slice never straddles two tables and every load is aligned)
-  for (int64_t q = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); q < nslices; q += nwarps) {
+  for (int64_t q = r0 + (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); q < r1; q += nwarps) {
     const int64_t k = p.sowner[q];
+    if (!p.active[k]) continue;  // uniform over the warp
+    const int32_t i = list[k];
+    const int32_t d = Cp[i];
     const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
-    const int64_t s = (q - p.slice_off[k]) * kSlice + 4 * lane;
+    const H kid = reinterpret_cast<const H*>(p.kid)[k];
+    const A ki = K[i], sd = Sig[d];
+    const A two_m = gc ? (M::is_fp ? (A)gc[vg[i]].two_m_f : (A)gc[vg[i]].two_m_i) : two_m_all;
+    int32_t* tk = p.keys + off;
+    H* tv = reinterpret_cast<H*>(p.vals) + off;
+    const int64_t sb = (q - p.slice_off[k]) << kRangeLog;
+    const int64_t se = sb + (1 << kRangeLog) < ts ? sb + (1 << kRangeLog) : ts;
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
-    if (s < ts) {
-      int32_t* tk = p.keys + off;
-      H* tv = reinterpret_cast<H*>(p.vals) + off;
+    for (int64_t s = sb + 4 * lane; s < se; s += 128) {
       const int4 kk = *reinterpret_cast<const int4*>(tk + s);
+      if ((kk.x & kk.y & kk.z & kk.w) == kEmpty) continue;  // all four empty
       const int32_t ks[4] = {kk.x, kk.y, kk.z, kk.w};
-      if ((kk.x & kk.y & kk.z & kk.w) != kEmpty) {  // some slot occupied
-        const int32_t i = list[k];
-        const int32_t d = Cp[i];
-        const H kid = reinterpret_cast<const H*>(p.kid)[k];
-        const A ki = K[i], sd = Sig[d];
-        const GraphCtl* gcv = gc ? gc + vg[i] : nullptr;
-        const A two_m = gcv ? (M::is_fp ? (A)gcv->two_m_f : (A)gcv->two_m_i) : two_m_all;
+      H vv[4];
+      A sg[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int32_t c = ks[u];
-          if (c == kEmpty) continue;
-          const H v = tv[s + u];
+      for (int u = 0; u < 4; u++) {
+        vv[u] = H(0);
+        sg[u] = A(0);
+        if (ks[u] != kEmpty) {
+          vv[u] = tv[s + u];
+          sg[u] = Sig[ks[u]];
           tk[s + u] = kEmpty;
           tv[s + u] = H(0);
-          cand++;
-          const S sc = M::score(v, kid, ki, Sig[c], sd, two_m);
-          if (better(sc, c, best, bc)) { best = sc; bc = c; }
         }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        if (ks[u] == kEmpty) continue;
+        cand++;
+        const S sc = M::score(vv[u], kid, ki, sg[u], sd, two_m);
+        if (better(sc, ks[u], best, bc)) { best = sc; bc = ks[u]; }
       }
     }
     group_argmax<32>(best, bc, (S*)nullptr, (int32_t*)nullptr);
@@ -228,19 +308,19 @@ __global__ void __launch_bounds__(kBlock) k_giant_lm_scan(const int32_t* list, i
 
 // ---------------------------------------------------------------- local move: decide (+ apply)
 template <class M>
-__global__ void __launch_bounds__(kBlock) k_giant_lm_decide(const int32_t* list, int64_t m, PassState<M> st,
-                                                            GiantPlan p, int fast) {
+__global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int64_t k0, int64_t k1, PassState<M> st,
+                                                       GiantPlan p, int fast) {
   typedef typename M::a_t A;
   typedef typename M::s_t S;
   Ctrl* ctrl = st.ctrl;
-  if (*(volatile int32_t*)&ctrl->done || p.slice_off[m] == 0) return;
+  if (*(volatile int32_t*)&ctrl->done) return;
   unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
   double acc_f = 0.0;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
-  for (int64_t k = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); k < m; k += nw) {
+  for (int64_t k = k0 + (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); k < k1; k += nw) {
+    if (!p.active[k]) continue;
     const int64_t q0 = p.slice_off[k], q1 = p.slice_off[k + 1];
-    if (q0 == q1) continue;  // pruned
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
     for (int64_t q = q0 + lane; q < q1; q += 32) {
@@ -298,60 +378,53 @@ __global__ void __launch_bounds__(kBlock) k_giant_lm_decide(const int32_t* list,
 
 // ---------------------------------------------------------------- local move: mark neighbours
 template <class W>
-__global__ void __launch_bounds__(kBlock) k_giant_lm_mark(GraphView<W> g, const int32_t* list, int64_t m,
-                                                          uint8_t* flags, GiantPlan p, Ctrl* ctrl) {
+__global__ void __launch_bounds__(kBlock) k_glm_mark(GraphView<W> g, const int32_t* list, int64_t k0, int64_t k1,
+                                                     uint8_t* flags, GiantPlan p, Ctrl* ctrl) {
+  constexpr int U = kChunk / kBlock;
   if (*(volatile int32_t*)&ctrl->done) return;
-  const int64_t nchunks = p.chunk_off[m];
+  const int64_t q0 = p.chunk_off[k0], q1 = p.chunk_off[k1];
   unsigned long long marks = 0;
-  for (int64_t q = blockIdx.x; q < nchunks; q += gridDim.x) {
+  for (int64_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
     const int64_t k = p.cowner[q];
     if (!p.moved[k]) continue;
     const int32_t i = list[k];
     const int64_t e0 = g.rbeg[i] + (q - p.chunk_off[k]) * kChunk;
     const int64_t e1 = e0 + kChunk < g.rend[i] ? e0 + kChunk : g.rend[i];
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += kBlock) {
-      const int32_t j = g.tg[e];
-      if (j != i) { flags[j] = 1; marks++; }
+    int32_t jj[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t e = e0 + threadIdx.x + (int64_t)u * kBlock;
+      jj[u] = e < e1 ? g.tg[e] : i;
     }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+      if (jj[u] != i) { flags[jj[u]] = 1; marks++; }
   }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) marks += __shfl_xor_sync(0xffffffffu, marks, o);
   if ((threadIdx.x & 31) == 0 && marks) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][5], marks);
 }
 
-// list / processed / arcs counters of the giant bucket (after the plan)
-__global__ void k_giant_lm_count(GraphView<int32_t> gs, const int32_t* list, int64_t m, GiantPlan p, Ctrl* ctrl) {
-  if (*(volatile int32_t*)&ctrl->done) return;
-  unsigned long long act = 0, arcs = 0;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
-    if (p.slice_off[k + 1] > p.slice_off[k]) { act++; arcs += (unsigned long long)(gs.rend[list[k]] - gs.rbeg[list[k]]); }
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    act += __shfl_xor_sync(0xffffffffu, act, o);
-    arcs += __shfl_xor_sync(0xffffffffu, arcs, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][0], (unsigned long long)m);
-    if (act) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][1], act);
-    if (arcs) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][2], arcs);
-  }
+template <class M>
+void giant_move_plan(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* list, int64_t m, const GiantPlan& p,
+                     Ctrl* ctrl) {
+  if (m <= 0) return;
+  giant_plan(c, 0, list, m, g.rbeg, g.rend, nullptr, g.n, nullptr, nullptr, kRangeLog, p, ctrl);
 }
 
 template <class M>
-void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t m,
-                const GiantPlan& p, bool fast, bool pruning) {
-  if (m <= 0) return;
+void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t k0,
+                int64_t k1, const GiantPlan& p, bool fast, bool pruning) {
+  if (k1 <= k0) return;
   const int grid = c.num_sms * 8;
-  k_giant_plan<<<1, 1024, 0, c.s>>>(0, list, m, g.rbeg, g.rend, nullptr, g.n, st.flags, pruning ? 1 : 0, nullptr,
-                                    nullptr, p, st.ctrl, st.gc, st.vg);
-  GraphView<int32_t> gs{g.n, g.rbeg, g.rend, g.tg, nullptr};
-  k_giant_lm_count<<<grid_for(m, kBlock, c.num_sms), kBlock, 0, c.s>>>(gs, list, m, p, st.ctrl);
-  k_giant_lm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, m, st.Cp, p, st.ctrl);
-  k_giant_lm_scan<M><<<grid, kBlock, 0, c.s>>>(list, m, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg);
-  k_giant_lm_decide<M><<<grid_for(m, kBlock / 32, c.num_sms * 2), kBlock, 0, c.s>>>(list, m, st, p, fast ? 1 : 0);
-  c.launches += 5;
+  k_glm_activate<typename M::w_t><<<grid_for(k1 - k0, kBlock, c.num_sms * 2), kBlock, 0, c.s>>>(
+      g, list, k0, k1, st.flags, pruning ? 1 : 0, st.gc, st.vg, p, st.ctrl);
+  k_glm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.Cp, p, st.ctrl);
+  k_glm_scan<M><<<grid, kBlock, 0, c.s>>>(list, k0, k1, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg);
+  k_glm_decide<M><<<grid_for(k1 - k0, kBlock / 32, c.num_sms * 2), kBlock, 0, c.s>>>(list, k0, k1, st, p, fast ? 1 : 0);
+  c.launches += 4;
   if (pruning) {
-    k_giant_lm_mark<typename M::w_t><<<grid, kBlock, 0, c.s>>>(g, list, m, st.flags, p, st.ctrl);
+    k_glm_mark<typename M::w_t><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, p, st.ctrl);
     c.launches++;
   }
 }
@@ -476,8 +549,7 @@ void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m,
   const int grid = c.num_sms * 8;
   // tables of the giant communities; gix = -1 for every other community
   cudaMemsetAsync(gix, 0xFF, (size_t)a.nc * sizeof(int32_t), c.s);
-  k_giant_plan<<<1, 1024, 0, c.s>>>(1, clist, m, nullptr, nullptr, a.cdeg, a.nc, nullptr, 0, nullptr, gix, p, a.ctrl);
-  c.launches++;
+  giant_plan(c, 1, clist, m, nullptr, nullptr, a.cdeg, a.nc, nullptr, gix, kSliceLog, p, a.ctrl);
   // member rows, by the member's degree bucket
   const int cap = c.num_sms * 16;
   for (int b = 0; b < kNumBuckets; b++) {
@@ -492,8 +564,7 @@ void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m,
       case 4: k_giant_mg_insert<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
       default:
         // giant members: chunk plan over their rows (members of giant communities only)
-        k_giant_plan<<<1, 1024, 0, c.s>>>(2, l, cnt, a.g.rbeg, a.g.rend, nullptr, a.g.n, nullptr, 0, a.Cp, gix, pv,
-                                          a.ctrl);
+        giant_plan(c, 2, l, cnt, a.g.rbeg, a.g.rend, nullptr, a.g.n, a.Cp, gix, kSliceLog, pv, a.ctrl);
         k_giant_mg_insert_chunks<M><<<grid, kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, pv, p, m, a.ctrl);
         c.launches++;
         break;
@@ -508,8 +579,7 @@ void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m,
 void giant_chunk_plan(Ctx& c, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
                       const GiantPlan& p, Ctrl* ctrl) {
   if (m <= 0) return;
-  k_giant_plan<<<1, 1024, 0, c.s>>>(3, list, m, rbeg, rend, nullptr, 0, nullptr, 0, nullptr, nullptr, p, ctrl);
-  c.launches++;
+  giant_plan(c, 3, list, m, rbeg, rend, nullptr, 0, nullptr, nullptr, kSliceLog, p, ctrl);
 }
 
 // Eq. 1 terms of giant rows: each chunk adds its part of K_i to Sigma_{C_i} and its intra-community
@@ -594,9 +664,12 @@ template void giant_compact<int32_t>(Ctx&, const int32_t*, int64_t, const int64_
 template void giant_compact<float>(Ctx&, const int32_t*, int64_t, const int64_t*, const int64_t*, const int64_t*,
                                    const int32_t*, const float*, int32_t*, float*, const GiantPlan&, Ctrl*);
 template void giant_move<IntMode>(Ctx&, const GraphView<int32_t>&, const PassState<IntMode>&, const int32_t*, int64_t,
-                                  const GiantPlan&, bool, bool);
+                                  int64_t, const GiantPlan&, bool, bool);
 template void giant_move<FpMode>(Ctx&, const GraphView<float>&, const PassState<FpMode>&, const int32_t*, int64_t,
-                                 const GiantPlan&, bool, bool);
+                                 int64_t, const GiantPlan&, bool, bool);
+template void giant_move_plan<IntMode>(Ctx&, const GraphView<int32_t>&, const int32_t*, int64_t, const GiantPlan&,
+                                       Ctrl*);
+template void giant_move_plan<FpMode>(Ctx&, const GraphView<float>&, const int32_t*, int64_t, const GiantPlan&, Ctrl*);
 template void giant_merge<IntMode>(Ctx&, const MergeArgs<IntMode>&, const int32_t*, int64_t, const int32_t*,
                                    const int64_t*, int32_t*, const GiantPlan&, const GiantPlan&);
 template void giant_merge<FpMode>(Ctx&, const MergeArgs<FpMode>&, const int32_t*, int64_t, const int32_t*,

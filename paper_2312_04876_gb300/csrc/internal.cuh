@@ -176,6 +176,7 @@ struct GiantPlan {
   int64_t* slice_off = nullptr;  // [cap + 1]
   void* kid = nullptr;           // [cap] K_i->d accumulators (h_t)
   uint8_t* moved = nullptr;      // [cap]
+  uint8_t* active = nullptr;     // [cap] local move: processed in the current class iteration
   void* part_s = nullptr;        // [slice_cap] best score per slice (s_t)
   int32_t* part_c = nullptr;     // [slice_cap] its community
   int32_t* cowner = nullptr;     // [chunk_cap] giant of each chunk
@@ -185,10 +186,19 @@ struct GiantPlan {
   void* vals = nullptr;          // (h_t), all zero between uses
   int64_t pool_slots = 0;
 };
-// Local moving of the giant vertices list[0, m) (one colour / random class).
+// Plan of the local-moving phase over every giant vertex of a pass, list[0, m) ordered class by
+// class (chunks, tables, 1024-slot ranges); built once per pass.
 template <class M>
-void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t m,
-                const GiantPlan& p, bool fast, bool pruning);
+void giant_move_plan(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* list, int64_t m, const GiantPlan& p,
+                     Ctrl* ctrl);
+// Local moving of the giants list[k0, k1) of one colour / random class under that plan.
+template <class M>
+void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t k0,
+                int64_t k1, const GiantPlan& p, bool fast, bool pruning);
+// Plan kernels (kind: see giant.cu); slices of 2^slice_log table slots.
+void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
+                const int64_t* cdeg, int64_t n_bound, const int32_t* Cp, int32_t* gix, int slice_log,
+                const GiantPlan& p, Ctrl* ctrl);
 // Super-vertex rows of the giant communities clist[0, m): members inserted by their degree bucket
 // (dperm / hb of the current graph), giant members by chunks (plan pv).  gix [nc] receives each
 // community's giant index (-1 if not giant).

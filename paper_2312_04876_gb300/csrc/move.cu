@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
   if (*(volatile int32_t*)&ctrl->done) return;
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
   constexpr int SL = GLOBAL ? 1 : (1 << LOG);
+  constexpr int U = G >= 32 ? 4 : 2;  // arcs (and table slots) per lane per step
   extern __shared__ __align__(16) unsigned char lm_dyn[];  // GPB tables of SL (key, value) slots
   int32_t* skeys = reinterpret_cast<int32_t*>(lm_dyn);
   H* svals = reinterpret_cast<H*>(lm_dyn + sizeof(int32_t) * GPB * SL);
@@ -119,18 +120,17 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
       if (*(volatile int32_t*)&gcv->done) continue;
     }
     const A two_m = gcv ? (M::is_fp ? (A)gcv->two_m_f : (A)gcv->two_m_i) : two_m_all;
-    if (a.pruning) {
-      int f = 0;
-      if (lane == 0) {
-        f = a.st.flags[i];
-        if (f) a.st.flags[i] = 0;  // mark i as processed
-      }
-      f = group_bcast<G>(f, red_i);
-      if (!f) continue;
-    }
+    // row bounds, C'[i] and the flag are loaded together (the loads overlap)
     const int64_t beg = a.g.rbeg[i], end = a.g.rend[i];
-    const int64_t deg = end - beg;
     const int32_t d = a.st.Cp[i];
+    if (a.pruning) {
+      // every lane reads the flag and the group takes the OR, so the decision is uniform even if a
+      // neighbour re-marks i meanwhile; then i is marked as processed
+      const int f = a.st.flags[i];
+      if (!group_any<G>(f != 0)) continue;
+      if (lane == 0) a.st.flags[i] = 0;
+    }
+    const int64_t deg = end - beg;
     if (lane == 0) { ctr[1]++; ctr[2] += (unsigned long long)deg; }
     int lg;
     if (GLOBAL) lg = tbl_log2(deg < n_cur ? deg : n_cur, 6, a.glog);
@@ -138,35 +138,63 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
     const unsigned size = 1u << lg;
     const int shift = 32 - lg;
 
-    // scanCommunities(i, self = false): K_i->c into the table, K_i->d in registers
+    // scanCommunities(i, self = false): K_i->c into the table, K_i->d in registers.  U arcs per
+    // lane are loaded before their C'[j] gathers and the table updates, so each lane keeps U
+    // independent memory requests in flight.
     H kid = H(0);
     bool ok = true;
-    for (int64_t e = beg + lane; e < end; e += G) {
-      const int32_t j = a.g.tg[e];
-      if (j == i) continue;
-      const H wv = (H)a.g.w[e];
-      const int32_t cj = a.st.Cp[j];
-      if (cj == d) kid += wv;
-      else ok &= tbl_add(tk, tv, size, shift, cj, wv);
+    for (int64_t e0 = beg + lane; e0 < end; e0 += (int64_t)G * U) {
+      int32_t jj[U];
+      H ww[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int64_t e = e0 + (int64_t)u * G;
+        jj[u] = e < end ? a.g.tg[e] : i;
+        ww[u] = e < end ? (H)a.g.w[e] : H(0);
+      }
+      int32_t cc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) cc[u] = jj[u] != i ? a.st.Cp[jj[u]] : kEmpty;
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (jj[u] == i) continue;  // padding or i's self-loop
+        if (cc[u] == d) kid += ww[u];
+        else ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
+      }
     }
     if (!ok) atomicOr(&ctrl->error, kErrTableFull);
     Grp<G>::sync();
     kid = group_sum<G>(kid, red_h);
 
-    // best community by the Eq. 2 numerator; the scan also clears the table
+    // best community by the Eq. 2 numerator; the scan also clears the table.  The Sigma gathers of
+    // U slots per lane are issued together.
     const A ki = a.st.K[i];
     const A sd = a.st.Sig[d];
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
-    for (unsigned s = lane; s < size; s += G) {
-      const int32_t c = tk[s];
-      if (c != kEmpty) {
-        const H v = tv[s];
-        tk[s] = kEmpty;
-        tv[s] = H(0);
+    for (unsigned s0 = lane; s0 < size; s0 += (unsigned)G * U) {
+      int32_t ck[U];
+      H vv[U];
+      A sg[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const unsigned s = s0 + (unsigned)u * G;
+        ck[u] = s < size ? tk[s] : kEmpty;
+        vv[u] = H(0);
+        if (ck[u] != kEmpty) {
+          vv[u] = tv[s];
+          tk[s] = kEmpty;
+          tv[s] = H(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) sg[u] = ck[u] != kEmpty ? a.st.Sig[ck[u]] : A(0);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (ck[u] == kEmpty) continue;
         ctr[3]++;
-        const S sc = M::score(v, kid, ki, a.st.Sig[c], sd, two_m);
-        if (better(sc, c, best, bc)) { best = sc; bc = c; }
+        const S sc = M::score(vv[u], kid, ki, sg[u], sd, two_m);
+        if (better(sc, ck[u], best, bc)) { best = sc; bc = ck[u]; }
       }
     }
     group_argmax<G>(best, bc, red_s, red_c);
@@ -206,9 +234,16 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
         ctr[4]++;
       }
       if (a.pruning)
-        for (int64_t e = beg + lane; e < end; e += G) {
-          const int32_t j = a.g.tg[e];
-          if (j != i) { a.st.flags[j] = 1; ctr[5]++; }  // mark neighbours as unprocessed
+        for (int64_t e0 = beg + lane; e0 < end; e0 += (int64_t)G * U) {
+          int32_t jj[U];
+#pragma unroll
+          for (int u = 0; u < U; u++) {
+            const int64_t e = e0 + (int64_t)u * G;
+            jj[u] = e < end ? a.g.tg[e] : i;
+          }
+#pragma unroll
+          for (int u = 0; u < U; u++)
+            if (jj[u] != i) { a.st.flags[jj[u]] = 1; ctr[5]++; }  // mark neighbours as unprocessed
         }
     }
   }

@@ -169,13 +169,13 @@ def markdown(s: dict, title: str, command: str) -> str:
     return "\n".join(out) + "\n"
 
 
-def traffic_json(s: dict, workload: str, mode: str, command: str) -> dict:
+def traffic_json(s: dict, workload: str, mode: str, command: str, source_root: str = ROOT) -> dict:
     classes = {}
     for name, c in s["classes"].items():
         if c["has_dram"] and c["launches"]:
             classes[name] = {"dram_bytes_per_launch": c["dram"] / c["launches"], "invocations": c["launches"],
                              "kernel_launches": c["kernel_launches"], "ncu_ms": c["ns"] / 1e6}
-    return {"workload": workload, "mode": mode, "source_sha256": source_sha256(), "command": command,
+    return {"workload": workload, "mode": mode, "source_sha256": source_sha256(source_root), "command": command,
             "note": "dram__bytes_read.sum + dram__bytes_write.sum per class invocation, one ncu pass "
                     "per launch; valid only while the CUDA sources hash to source_sha256",
             "classes": classes}
@@ -189,6 +189,8 @@ def main(argv=None):
     ap.add_argument("--command", required=True)
     ap.add_argument("--md")
     ap.add_argument("--traffic-json")
+    ap.add_argument("--source-root", default=ROOT,
+                    help="tree whose CUDA sources ran under ncu (e.g. a checkout of the profiled commit)")
     a = ap.parse_args(argv)
     s = summarise(read_launches(a.csv))
     if a.md:
@@ -196,7 +198,7 @@ def main(argv=None):
             f.write(markdown(s, f"Kernel launch list: {a.workload}, {a.mode} mode", a.command))
     if a.traffic_json:
         with open(a.traffic_json, "w") as f:
-            json.dump(traffic_json(s, a.workload, a.mode, a.command), f, indent=1)
+            json.dump(traffic_json(s, a.workload, a.mode, a.command, a.source_root), f, indent=1)
     if not a.md:
         print(markdown(s, f"{a.workload} {a.mode}", a.command))
 

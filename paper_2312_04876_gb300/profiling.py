@@ -32,7 +32,7 @@ _LM_NAMES = ["local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "loca
 _MG_NAMES = ["merge_b0_g4", "merge_b1_g8", "merge_b2_warp", "merge_b3_block4k", "merge_b4_block8k",
              "merge_b5_giant"]
 # kernel whose launch count is the number of invocations of each multi-kernel class
-PRIMARY = {"local_move_b5_giant": "k_giant_lm_scan", "merge_b5_giant": "k_giant_mg_emit"}
+PRIMARY = {"local_move_b5_giant": "k_glm_scan", "merge_b5_giant": "k_giant_mg_emit"}
 
 
 def source_sha256(root: str = ROOT) -> str:
@@ -71,11 +71,11 @@ def kernel_class(name: str) -> str | None:
         return _LM_NAMES[_BUCKET_OF.get((args[1], args[2]), 5)]
     if base == "merge_kernel" and len(args) >= 3:
         return _MG_NAMES[_BUCKET_OF.get((args[1], args[2]), 5)]
-    if base.startswith("k_giant_lm_"):
+    if base.startswith("k_glm_"):
         return "local_move_b5_giant"
     if base.startswith("k_giant_mg_"):
         return "merge_b5_giant"
-    if base in ("k_giant_plan",):
+    if base.startswith("k_gplan_"):
         return None
     if base in ("k_compact", "k_compact_group", "k_giant_copy_chunks", "k_row_len"):
         return "compact"

@@ -263,7 +263,12 @@ def run_batch_bench(args):
                    "l2": f"inputs larger than L2 (CSR {(8 * (int(vo[-1]) + 1) + 8 * n_arcs) / 1e9:.2f} GB)"},
         "edges_per_second": n_arcs / (ms / 1e3), "gpu_launches_per_step": res.kernel_launches,
         "one_at_a_time": {"graphs_per_second": single_gps, "graphs_timed": len(singles), "ms": single_ms,
-                          "max_abs_dq_vs_batch": max(abs(x) for x in dq) if dq else None},
+                          "max_abs_dq_vs_batch": max(abs(x) for x in dq) if dq else None,
+                          "mean_dq_batch_minus_single": float(np.mean(dq)) if dq else None,
+                          "graphs_abs_dq_over_0.005": int(sum(abs(x) > 0.005 for x in dq)),
+                          "worst_graph": (lambda j: {"index": j, "n": graphs[j].n, "arcs": graphs[j].n_arcs,
+                                                     "q_batch": per[j]["modularity"], "q_single": single_q[j]})(
+                              int(np.argmax(np.abs(dq)))) if dq else None},
         "speedup_vs_one_at_a_time": batch_gps / single_gps,
         "passes_max": res.passes, "generate_s": gen_s, "clocks": clk.summary(),
     }

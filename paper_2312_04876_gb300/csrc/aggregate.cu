@@ -90,15 +90,32 @@ __device__ __forceinline__ bool merge_members(const MergeArgs<M>& a, int64_t k0,
     const int64_t total = __shfl_sync(mask, incl, W - 1, W);
     const int64_t excl = incl - len;
     arcs += (unsigned long long)len;
-    for (int64_t f0 = 0; f0 < total; f0 += W) {
-      const int64_t f = f0 + l;
-      const int o = flat_owner<W>(incl, f, mask);
-      const int64_t ob = __shfl_sync(mask, b, o, W);
-      const int64_t oe = __shfl_sync(mask, excl, o, W);
-      if (f < total) {
-        const int64_t e = ob + (f - oe);
-        ok &= tbl_add(tk, tv, size, shift, a.Cp[a.g.tg[e]], (H)a.g.w[e]);
+    // U flat arcs per lane per step: their target / weight loads, then their C'[j] gathers, then
+    // the table updates, so each lane keeps U independent memory requests in flight
+    constexpr int U = 4;
+    for (int64_t f0 = 0; f0 < total; f0 += (int64_t)W * U) {
+      int64_t ee[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int64_t f = f0 + (int64_t)u * W + l;
+        const int o = flat_owner<W>(incl, f, mask);
+        const int64_t ob = __shfl_sync(mask, b, o, W);
+        const int64_t oe = __shfl_sync(mask, excl, o, W);
+        ee[u] = f < total ? ob + (f - oe) : -1;
       }
+      int32_t jj[U];
+      H ww[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        jj[u] = ee[u] >= 0 ? a.g.tg[ee[u]] : 0;
+        ww[u] = ee[u] >= 0 ? (H)a.g.w[ee[u]] : H(0);
+      }
+      int32_t cc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) cc[u] = ee[u] >= 0 ? a.Cp[jj[u]] : kEmpty;
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (ee[u] >= 0) ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
     }
   }
   return ok;
@@ -223,8 +240,9 @@ void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& args, const int32_t* l
     case 0: launch_merge<M, 4, 3, false>(c, a, list, count, gt, cap); break;
     case 1: launch_merge<M, 8, 5, false>(c, a, list, count, gt, cap); break;
     case 2: launch_merge<M, 32, 8, false>(c, a, list, count, gt, cap); break;
-    case 3: launch_merge<M, 256, 12, false>(c, a, list, count, gt, cap); break;
-    case 4: launch_merge<M, 256, 13, false>(c, a, list, count, gt, cap); break;
+    case 3: launch_merge<M, 32, 10, false>(c, a, list, count, gt, cap); break;
+    case 4: launch_merge<M, 256, 12, false>(c, a, list, count, gt, cap); break;
+    case 5: launch_merge<M, 256, 13, false>(c, a, list, count, gt, cap); break;
     default: break;  // giant communities go through giant_merge
   }
 }
@@ -317,9 +335,10 @@ void compact_bucketed(Ctx& c, const int32_t* cperm, const int64_t* cb, const int
     switch (b) {
       case 0: k_compact_group<W, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
       case 1: k_compact_group<W, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
-      case 2: k_compact_group<W, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
-      case 3:
-      case 4: k_compact_group<W, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
+      case 2:
+      case 3: k_compact_group<W, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
+      case 4:
+      case 5: k_compact_group<W, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(l, cnt, hbeg, hend, doff, itg, iw, otg, ow); break;
       default: giant_compact<W>(c, l, cnt, hbeg, hend, doff, itg, iw, otg, ow, gp, ctrl); c.launches--; break;
     }
     c.launches++;

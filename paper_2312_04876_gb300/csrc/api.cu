@@ -54,7 +54,6 @@ struct Workspace {
   GlobalTable gt;
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
   int32_t* glist = nullptr;   // [gcap] giant vertices of a pass, class by class
-  int64_t* ctab = nullptr;    // [n] table offset of each giant community (-1 otherwise)
   int32_t* csz = nullptr;     // [n] table size of each giant community
   GiantPlan gp, gpv;          // plans of giant vertices / communities and of giant members
   DevAlloc in_alloc;
@@ -78,18 +77,19 @@ struct Workspace {
 
 // Kernel classes of the per-launch profile.
 enum KClass {
-  kLm0 = 0,            // local-move buckets 0..4
+  kLm0 = 0,            // local-move buckets 0..6
   kApply = kNumBuckets,
-  kMg0,                // merge buckets 0..4
+  kMg0,                // merge buckets 0..6
   kCompact = kMg0 + kNumBuckets,
   kColour,
   kModularity,
   kNumClasses
 };
 static const char* const kClassNames[kNumClasses] = {
-    "local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "local_move_b3_block4k", "local_move_b4_block8k",
-    "local_move_b5_giant", "sigma_apply", "merge_b0_g4", "merge_b1_g8", "merge_b2_warp", "merge_b3_block4k",
-    "merge_b4_block8k", "merge_b5_giant", "compact", "colour_jp", "modularity"};
+    "local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "local_move_b3_warp1k", "local_move_b4_block4k",
+    "local_move_b5_block8k", "local_move_b6_giant", "sigma_apply", "merge_b0_g4", "merge_b1_g8", "merge_b2_warp",
+    "merge_b3_warp1k", "merge_b4_block4k", "merge_b5_block8k", "merge_b6_giant", "compact", "colour_jp",
+    "modularity"};
 
 struct Profile {
   bool on = false;
@@ -183,12 +183,11 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
        dalloc(h, d, &ws.cperm, n1) && dalloc(h, d, &ws.occ, n1) && dalloc(h, d, &ws.counts, n1) &&
        dalloc(h, d, &ws.cursor, n1) && dalloc(h, d, &ws.cverts, n1) && dalloc(h, d, &ws.jcnt, n1) &&
        dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.tmp_mem, n1);
-  ok = ok && dalloc(h, d, &ws.flags, n1) && dalloc(h, d, &ws.dperm, n1) && dalloc(h, d, &ws.ctab, n1) &&
-       dalloc(h, d, &ws.csz, n1);
-  // giant plans: at most A / 2049 rows exceed 2048 arcs; tables of <= 4 x the arcs in 4096-slot slices
-  // giant rows have > 4096 arcs: at most A / 4097 of them; chunks of 2048 arcs over their rows:
-  // <= gcap + A / 2048; slices of 128 slots over tables of < 4 x the arcs: <= gcap + A / 32
-  const int64_t gcap = ac / 4096 + 16, scap = gcap + ac / 32 + 16, ccap = gcap + ac / 2048 + 16;
+  ok = ok && dalloc(h, d, &ws.flags, n1) && dalloc(h, d, &ws.dperm, n1) && dalloc(h, d, &ws.csz, n1);
+  // giant plans: giant rows have > 4096 arcs, so there are at most A / 4097 of them; chunks of >= 512
+  // arcs over their rows: <= gcap + A / 512; slices of >= 128 slots over tables of < 4 x the arcs:
+  // <= gcap + A / 32
+  const int64_t gcap = ac / 4096 + 16, scap = gcap + ac / 32 + 16, ccap = gcap + ac / 512 + 16;
   for (GiantPlan* gp : {&ws.gp, &ws.gpv})
     ok = ok && dalloc(h, d, &gp->chunk_off, gcap + 1) && dalloc(h, d, &gp->tab_off, gcap + 1) &&
          dalloc(h, d, &gp->slice_off, gcap + 1) && dalloc(h, d, (int32_t**)&gp->kid, gcap) &&

@@ -385,7 +385,8 @@ void batch_modularity(Ctx& c, const GraphView<typename M::w_t>& g0, const int32_
     switch (b) {
       case 0: k_bmod_group<M, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(g0, l, cnt, C, vg0, gc, intra, tot); break;
       case 1: k_bmod_group<M, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(g0, l, cnt, C, vg0, gc, intra, tot); break;
-      case 2: k_bmod_group<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g0, l, cnt, C, vg0, gc, intra, tot); break;
+      case 2:
+      case 3: k_bmod_group<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g0, l, cnt, C, vg0, gc, intra, tot); break;
       default: k_bmod_group<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(g0, l, cnt, C, vg0, gc, intra, tot); break;
     }
     c.launches++;

@@ -157,7 +157,8 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
     switch (b) {
       case 0: jp_count<4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(a, l, cnt); break;
       case 1: jp_count<8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(a, l, cnt); break;
-      case 2: jp_count<32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(a, l, cnt); break;
+      case 2:
+      case 3: jp_count<32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(a, l, cnt); break;
       default: jp_count<256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(a, l, cnt); break;
     }
     c.launches++;

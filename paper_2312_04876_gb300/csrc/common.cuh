@@ -10,23 +10,25 @@ namespace lv {
 
 constexpr int32_t kEmpty = -1;     // empty hash-table key
 constexpr int kBlock = 256;        // threads per block of the vertex-parallel kernels
-constexpr int kNumBuckets = 6;     // degree buckets of the per-vertex kernels
+constexpr int kNumBuckets = 7;     // degree buckets of the per-vertex kernels
 
 // Degree buckets: upper bound of the row length (arcs, self-loop included) handled by each.
 //   0: 1..4       groups of 4 lanes, 8-slot shared-memory table
 //   1: 5..16      groups of 8 lanes, 32 slots
 //   2: 17..128    one warp, 256 slots
-//   3: 129..2048  one 256-thread block, 4096 slots (32 KB)
-//   4: 2049..4096 one 256-thread block, 8192 slots (64 KB, dynamic shared memory)
-//   5: > 4096     giant: arc chunks and table slices over the whole GPU (giant.cu)
+//   3: 129..512   one warp, 1024 slots (8 KB per warp, 64 KB of dynamic shared memory per block)
+//   4: 513..2048  one 256-thread block, 4096 slots (32 KB)
+//   5: 2049..4096 one 256-thread block, 8192 slots (64 KB, dynamic shared memory)
+//   6: > 4096     giant: arc chunks and table slices over the whole GPU (giant.cu)
 __host__ __device__ inline int degree_bucket(int64_t deg) {
   if (deg <= 0) return -1;
   if (deg <= 4) return 0;
   if (deg <= 16) return 1;
   if (deg <= 128) return 2;
-  if (deg <= 2048) return 3;
-  if (deg <= 4096) return 4;
-  return 5;
+  if (deg <= 512) return 3;
+  if (deg <= 2048) return 4;
+  if (deg <= 4096) return 5;
+  return 6;
 }
 
 // Device control block: per-iteration accumulators and convergence state.

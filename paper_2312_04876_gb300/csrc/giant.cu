@@ -9,9 +9,9 @@
 //           giant (binary search, fully parallel).  The local-moving plan covers every giant of a
 //           pass at once (the giants listed class by class), so it is built once per pass; each
 //           iteration of a class only decides which of its giants are active (pruning flags);
-//   insert  grid-stride over chunks of 2048 arcs: K_i->c into the giant's global table with L2
-//           atomics, K_i->d in registers (scanCommunities);
-//   scan    local move: one warp per range of 1024 table slots (16-byte key loads) scores every
+//   insert  grid-stride over chunks of 512 arcs (local move) or 2048 arcs (merge): K_i->c into the
+//           giant's global table with L2 atomics, K_i->d in registers (scanCommunities);
+//   scan    local move: one warp per range of 256 table slots (16-byte key loads) scores every
 //           candidate with the Eq. 2 numerator and keeps the range's best; merge: one warp per
 //           128-slot slice emits the slice's (community, weight) pairs into the holey row of the
 //           community.  Every occupied slot is cleared, so the pool is all-empty between uses;
@@ -24,10 +24,11 @@
 
 namespace lv {
 
-constexpr int kChunk = 2048;    // arcs per chunk
+constexpr int kChunk = 2048;    // arcs per chunk (merge, modularity, compaction)
+constexpr int kLmChunk = 512;   // arcs per chunk of the local-moving phase (2 per thread)
 constexpr int kSliceLog = 7;    // merge: 128 table slots per slice, one 16-byte key load per lane
 constexpr int kSlice = 1 << kSliceLog;
-constexpr int kRangeLog = 10;   // local move: 1024 table slots per warp range (8 key loads per lane)
+constexpr int kRangeLog = 8;    // local move: 256 table slots per warp range (2 key loads per lane)
 constexpr int kLocLog = 12;     // shared pre-aggregation table: 4096 slots >= 2 x kChunk keys
 
 // ---------------------------------------------------------------- plan
@@ -50,7 +51,8 @@ __global__ void k_gplan_counts(int kind, const int32_t* list, int64_t m, const i
       const int64_t deg = rend[v] - rbeg[v];
       const bool used = kind != 2 || (Cp[v] >= 0 && gix[Cp[v]] >= 0);
       if (used) {
-        nch = (deg + kChunk - 1) / kChunk;
+        const int64_t ch = kind == 0 ? kLmChunk : kChunk;
+        nch = (deg + ch - 1) / ch;
         if (kind == 0) ts = (int64_t)1 << tbl_log2(deg < n_bound ? deg : n_bound, 6, 31);
       }
     }
@@ -197,7 +199,7 @@ template <class M>
 __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t> g, const int32_t* list, int64_t k0,
                                                        int64_t k1, const int32_t* Cp, GiantPlan p, Ctrl* ctrl) {
   typedef typename M::h_t H;
-  constexpr int U = kChunk / kBlock;  // 8
+  constexpr int U = kLmChunk / kBlock;  // 2
   __shared__ H red[32];
   if (*(volatile int32_t*)&ctrl->done) return;
   const int64_t q0 = p.chunk_off[k0], q1 = p.chunk_off[k1];
@@ -212,8 +214,8 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
     while (((int64_t)1 << lg) < ts) lg++;
     int32_t* tk = p.keys + off;
     H* tv = reinterpret_cast<H*>(p.vals) + off;
-    const int64_t e0 = g.rbeg[i] + (q - p.chunk_off[k]) * kChunk;
-    const int64_t e1 = e0 + kChunk < g.rend[i] ? e0 + kChunk : g.rend[i];
+    const int64_t e0 = g.rbeg[i] + (q - p.chunk_off[k]) * kLmChunk;
+    const int64_t e1 = e0 + kLmChunk < g.rend[i] ? e0 + kLmChunk : g.rend[i];
     int32_t jj[U];
     H ww[U];
 #pragma unroll
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
 }
 
 // ---------------------------------------------------------------- local move: range scan
-// One warp per range of 1024 slots of an active giant's table: 8 steps of one 16-byte key load per
+// One warp per range of 256 slots of an active giant's table: 2 steps of one 16-byte key load per
 // lane (tables are >= 64 slots and 64-slot aligned, so loads are aligned and never straddle two
 // tables); the Sigma gathers of a step are issued together.  Writes the range's best to part_s/c.
 template <class M>
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int6
 template <class W>
 __global__ void __launch_bounds__(kBlock) k_glm_mark(GraphView<W> g, const int32_t* list, int64_t k0, int64_t k1,
                                                      uint8_t* flags, GiantPlan p, Ctrl* ctrl) {
-  constexpr int U = kChunk / kBlock;
+  constexpr int U = kLmChunk / kBlock;
   if (*(volatile int32_t*)&ctrl->done) return;
   const int64_t q0 = p.chunk_off[k0], q1 = p.chunk_off[k1];
   unsigned long long marks = 0;
@@ -388,8 +390,8 @@ __global__ void __launch_bounds__(kBlock) k_glm_mark(GraphView<W> g, const int32
     const int64_t k = p.cowner[q];
     if (!p.moved[k]) continue;
     const int32_t i = list[k];
-    const int64_t e0 = g.rbeg[i] + (q - p.chunk_off[k]) * kChunk;
-    const int64_t e1 = e0 + kChunk < g.rend[i] ? e0 + kChunk : g.rend[i];
+    const int64_t e0 = g.rbeg[i] + (q - p.chunk_off[k]) * kLmChunk;
+    const int64_t e1 = e0 + kLmChunk < g.rend[i] ? e0 + kLmChunk : g.rend[i];
     int32_t jj[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
@@ -559,9 +561,10 @@ void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m,
     switch (b) {
       case 0: k_giant_mg_insert<M, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
       case 1: k_giant_mg_insert<M, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
-      case 2: k_giant_mg_insert<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
-      case 3:
-      case 4: k_giant_mg_insert<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
+      case 2:
+      case 3: k_giant_mg_insert<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
+      case 4:
+      case 5: k_giant_mg_insert<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
       default:
         // giant members: chunk plan over their rows (members of giant communities only)
         giant_plan(c, 2, l, cnt, a.g.rbeg, a.g.rend, nullptr, a.g.n, a.Cp, gix, kSliceLog, pv, a.ctrl);

@@ -150,9 +150,10 @@ void modularity_bucketed(Ctx& c, const GraphView<typename M::w_t>& g, const int3
       switch (b) {
         case 0: k_mod_group<M, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
         case 1: k_mod_group<M, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
-        case 2: k_mod_group<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
-        case 3:
-        case 4: k_mod_group<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
+        case 2:
+        case 3: k_mod_group<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
+        case 4:
+        case 5: k_mod_group<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(g, l, cnt, C, tot, ctrl); break;
         default: giant_modularity<M>(c, g, l, cnt, C, tot, gp, ctrl); c.launches--; break;
       }
       c.launches++;

@@ -279,8 +279,9 @@ void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const 
     case 0: launch_lm<M, 4, 3, false>(c, a, cap); break;
     case 1: launch_lm<M, 8, 5, false>(c, a, cap); break;
     case 2: launch_lm<M, 32, 8, false>(c, a, cap); break;
-    case 3: launch_lm<M, 256, 12, false>(c, a, cap); break;
-    case 4: launch_lm<M, 256, 13, false>(c, a, cap); break;
+    case 3: launch_lm<M, 32, 10, false>(c, a, cap); break;
+    case 4: launch_lm<M, 256, 12, false>(c, a, cap); break;
+    case 5: launch_lm<M, 256, 13, false>(c, a, cap); break;
     default: break;  // giants go through giant_move
   }
 }
@@ -404,7 +405,8 @@ void row_sums(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* perm, 
     switch (b) {
       case 0: k_row_sums<M, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
       case 1: k_row_sums<M, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
-      case 2: k_row_sums<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
+      case 2:
+      case 3: k_row_sums<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
       default: k_row_sums<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(g, l, cnt, K, Sig, K0); break;
     }
     c.launches++;

@@ -26,13 +26,14 @@ import re
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # (group lanes, log2 table slots) of the per-bucket kernels -> bucket
-_BUCKET_OF = {("4", "3"): 0, ("8", "5"): 1, ("32", "8"): 2, ("256", "12"): 3, ("256", "13"): 4}
-_LM_NAMES = ["local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "local_move_b3_block4k",
-             "local_move_b4_block8k", "local_move_b5_giant"]
-_MG_NAMES = ["merge_b0_g4", "merge_b1_g8", "merge_b2_warp", "merge_b3_block4k", "merge_b4_block8k",
-             "merge_b5_giant"]
+_BUCKET_OF = {("4", "3"): 0, ("8", "5"): 1, ("32", "8"): 2, ("32", "10"): 3, ("256", "12"): 4, ("256", "13"): 5}
+_LM_NAMES = ["local_move_b0_g4", "local_move_b1_g8", "local_move_b2_warp", "local_move_b3_warp1k",
+             "local_move_b4_block4k", "local_move_b5_block8k", "local_move_b6_giant"]
+_MG_NAMES = ["merge_b0_g4", "merge_b1_g8", "merge_b2_warp", "merge_b3_warp1k", "merge_b4_block4k",
+             "merge_b5_block8k", "merge_b6_giant"]
+GIANT = 6
 # kernel whose launch count is the number of invocations of each multi-kernel class
-PRIMARY = {"local_move_b5_giant": "k_glm_scan", "merge_b5_giant": "k_giant_mg_emit"}
+PRIMARY = {"local_move_b6_giant": "k_glm_scan", "merge_b6_giant": "k_giant_mg_emit"}
 
 
 def source_sha256(root: str = ROOT) -> str:
@@ -68,13 +69,13 @@ def kernel_class(name: str) -> str | None:
     base = name.split("<")[0]
     args = [a.strip() for a in name[len(base) + 1:-1].split(",")] if "<" in name else []
     if base == "lm_kernel" and len(args) >= 3:
-        return _LM_NAMES[_BUCKET_OF.get((args[1], args[2]), 5)]
+        return _LM_NAMES[_BUCKET_OF.get((args[1], args[2]), GIANT)]
     if base == "merge_kernel" and len(args) >= 3:
-        return _MG_NAMES[_BUCKET_OF.get((args[1], args[2]), 5)]
+        return _MG_NAMES[_BUCKET_OF.get((args[1], args[2]), GIANT)]
     if base.startswith("k_glm_"):
-        return "local_move_b5_giant"
+        return _LM_NAMES[GIANT]
     if base.startswith("k_giant_mg_"):
-        return "merge_b5_giant"
+        return _MG_NAMES[GIANT]
     if base.startswith("k_gplan_"):
         return None
     if base in ("k_compact", "k_compact_group", "k_giant_copy_chunks", "k_row_len"):
@@ -118,7 +119,7 @@ def read_launches(path: str) -> list[dict]:
         c = kernel_class(L["name"])
         if c is None:
             c = nxt or "other"
-        elif c in ("local_move_b5_giant", "merge_b5_giant", "compact", "modularity"):
+        elif c in (_LM_NAMES[GIANT], _MG_NAMES[GIANT], "compact", "modularity"):
             nxt = c
         L["class"] = c
     return rows

@@ -25,6 +25,8 @@ WORKLOADS = {
     "rmat22": lambda: gg.rmat(22, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "rmat20": lambda: gg.rmat(20, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "sbm10k": lambda: gg.sbm(10000, 100, 0.1, 0.0005, 1),
+    # road-like: 4899 x 4899 lattice (~24.0M vertices), 10% of the edges deleted, 1% long links
+    "grid24m": lambda: gg.grid(4899, 4899, 0.10, 0.01, 3),
 }
 
 

@@ -1,4 +1,5 @@
-"""Full-size parity: R-MAT scale 20 and 22 and the 10k SBM against the CPU oracle's stored results.
+"""Full-size parity: the 10k SBM, R-MAT scale 20 and 22 and the 24M-vertex road-like grid against the
+CPU oracle's stored results, and R-MAT scale 27 with fp32 weights by invariants.
 
 tests/golden/<workload>_oracle.json is written by tests/golden/make_golden.py, which calls only
 the seeded generators and the CPU oracle.  The graph is regenerated here and checked against the
@@ -27,6 +28,7 @@ GEN = {
     "sbm10k": lambda: gg.sbm(10000, 100, 0.1, 0.0005, 1),
     "rmat20": lambda: gg.rmat(20, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "rmat22": lambda: gg.rmat(22, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
+    "grid24m": lambda: gg.grid(4899, 4899, 0.10, 0.01, 3),
 }
 
 
@@ -45,7 +47,7 @@ def L(cuda_ok):
     h.close()
 
 
-@pytest.fixture(scope="module", params=["sbm10k", "rmat20", "rmat22"])
+@pytest.fixture(scope="module", params=["sbm10k", "rmat20", "rmat22", "grid24m"])
 def workload(request):
     with open(os.path.join(GOLDEN, f"{request.param}_oracle.json")) as f:
         gold = json.load(f)
@@ -77,3 +79,26 @@ def test_fast_within_tolerance(L, workload):
     # its modularity, re-evaluated by the library's Eq. 1 kernel, is the one reported
     assert abs(L.modularity(o, t, w, mem) - r.modularity) <= 1e-12
     assert r.modularity >= gold["modularity"] - 0.005
+
+
+def test_rmat27_fp32_fast_full_size(cuda_ok):
+    """R-MAT scale 27 (134M vertices, ~4.3B arcs) with fp32 weights in (0, 1], drawn on the GPU by the
+    tensor version of the generator.  The oracle's own run would take hours on one core, so parity
+    is checked by what holds at any size: a valid canonical partition, and its modularity recomputed
+    by the oracle's Eq. 1 on the host (fp64) equal to the library's within 1e-10."""
+    import oracle
+    import paper_2312_04876_gb300 as lv
+    from graphgen import device as gd
+    o, t, w = gd.rmat(27, 16, 0.57, 0.19, 0.19, 22, fp_weights=True, device="cuda")
+    torch.cuda.empty_cache()
+    assert o.numel() == (1 << 27) + 1 and t.numel() > (1 << 32)
+    L = lv.Louvain(0)
+    mem, r = L.run(o, t, w, mode="fast", validate=0)
+    nc = r.n_communities
+    assert int(mem.min()) == 0 and int(mem.max()) == nc - 1
+    assert int(torch.unique(mem).numel()) == nc
+    assert abs(L.modularity(o, t, w, mem) - r.modularity) <= 1e-10
+    L.close()
+    q_host = oracle.modularity(o.cpu().numpy(), t.cpu().numpy(), w.cpu().numpy(), mem.cpu().numpy())
+    assert abs(q_host - r.modularity) <= 1e-10
+    assert r.modularity > 0.0

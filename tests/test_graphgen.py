@@ -72,3 +72,24 @@ def test_batch_params_ranges():
         n, k, p_in, p_out, seed = gg.batch_sbm_params(4, gi)
         assert 1000 <= n <= 200000 and 2 <= k <= 64
         assert 0 < p_out < p_in <= 1 and abs(p_out / p_in - 0.02) < 1e-12
+
+
+@pytest.mark.parametrize("scale,fp", [(9, False), (11, True), (12, False)])
+def test_tensor_rmat_equals_c_generator(scale, fp):
+    """The tensor R-MAT (used on the GPU for scale 27) draws exactly graphgen.rmat's CSR; run here
+    on CPU tensors, in small chunks so the chunk loop is exercised."""
+    torch = pytest.importorskip("torch")
+    from graphgen import device as gd
+    o, t, w = gd.rmat(scale, 16, 0.57, 0.19, 0.19, 30 + scale, fp_weights=fp, device="cpu", chunk=1 << 13)
+    g = gg.rmat(scale, 16, 0.57, 0.19, 0.19, 30 + scale, gg.W_FP32 if fp else gg.W_INT8)
+    assert np.array_equal(o.numpy(), g.offsets)
+    assert np.array_equal(t.numpy(), g.targets)
+    assert np.array_equal(w.numpy(), g.weights)
+
+
+def test_tensor_hash3_equals_c_hash3():
+    torch = pytest.importorskip("torch")
+    from graphgen import device as gd
+    for a, b, c in [(0, 0, 0), (22, 12345, 3), (2**63 + 5, 2**40, 7)]:
+        x = gd.hash3(torch.tensor(gd._s64(a)), gd._s64(b), gd._s64(c))
+        assert int(x) & ((1 << 64) - 1) == gg.hash3(a, b, c)

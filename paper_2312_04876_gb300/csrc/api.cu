@@ -113,6 +113,12 @@ struct louvain_handle_s {
   size_t pin_bytes = 0;
   std::vector<cudaEvent_t> events;
   Profile prof;
+  // CUDA-graph replay of local-moving iterations: one side stream per degree bucket (the buckets of
+  // a colour / random class run concurrently) and fork / join events
+  cudaStream_t side[kNumBuckets] = {};
+  cudaStream_t cap = nullptr;  // capture origin (the caller's stream may be the legacy one)
+  std::vector<cudaEvent_t> fork_ev, join_ev;
+  bool use_graphs = true;
 };
 
 namespace {
@@ -408,6 +414,12 @@ louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, i
   return LOUVAIN_OK;
 }
 
+template <class M>
+louvain_status capture_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st,
+                                 const std::vector<int64_t>& ho, const std::vector<int64_t>& gofs, int32_t ncol,
+                                 bool det, bool pruning, GraphCtl* gc, int32_t n_graphs, cudaGraphExec_t* exec,
+                                 int64_t* launches);
+
 // One local-moving phase (Algorithm 2) on g from the state in ws (K, Sig, Cp, flags set).
 // Fills *li and *moves.  Deterministic mode colours g first.
 template <class M>
@@ -476,8 +488,26 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   const bool pruning = p.pruning != 0;
   int enq = 0;
   const int batch = det ? 2 : 4;
+  // Without per-launch profiling, one iteration is captured once per pass as a CUDA graph -- per
+  // class a fork to one stream per degree bucket and a join -- and replayed for every iteration.
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_launches = 0;
+  if (!h->prof.on && h->use_graphs) {
+    if ((s = capture_iteration<M>(h, c, g, st, ho, gofs, ncol, det, pruning, gc, n_graphs, &exec, &graph_launches)) !=
+        LOUVAIN_OK)
+      return s;
+  }
+  struct ExecGuard {
+    cudaGraphExec_t e;
+    ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+  } guard{exec};
   while (true) {
     for (int k = 0; k < batch && enq < p.max_iterations; k++, enq++) {
+      if (exec) {
+        cudaGraphLaunch(exec, c.s);
+        c.launches += graph_launches;
+        continue;
+      }
       for (int cl = 0; cl < ncol; cl++) {
         const size_t base = (size_t)cl * kNumBuckets;
         for (int b = 0; b < kNumBuckets; b++) {
@@ -506,6 +536,76 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
       return LOUVAIN_OK;
     }
   }
+}
+
+// Captures one local-moving iteration (every class: buckets on their side streams, the deterministic
+// apply, then the convergence test) into an executable CUDA graph.  *launches = kernels per replay.
+template <class M>
+louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<typename M::w_t>& g, const PassState<M>& st,
+                                 const std::vector<int64_t>& ho, const std::vector<int64_t>& gofs, int32_t ncol,
+                                 bool det, bool pruning, GraphCtl* gc, int32_t n_graphs, cudaGraphExec_t* exec,
+                                 int64_t* launches) {
+  Workspace& ws = h->ws;
+  *exec = nullptr;
+  if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_err(h, cudaGetLastError(), "capture stream creation");
+  Ctx c = c0;  // launches are recorded on the private capture stream, the graph runs on c0.s
+  c.s = h->cap;
+  c.launches = 0;
+  for (int b = 0; b < kNumBuckets; b++)
+    if (!h->side[b] && cudaStreamCreateWithFlags(&h->side[b], cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_err(h, cudaGetLastError(), "side stream creation");
+  const size_t need = (size_t)ncol;
+  while (h->fork_ev.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_err(h, cudaGetLastError(), "event creation");
+    h->fork_ev.push_back(e);
+  }
+  while (h->join_ev.size() < need * kNumBuckets) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_err(h, cudaGetLastError(), "event creation");
+    h->join_ev.push_back(e);
+  }
+  move_prepare();
+  const int64_t l0 = c.launches;
+  cudaError_t e = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_err(h, e, "graph capture begin");
+  for (int cl = 0; cl < ncol; cl++) {
+    const size_t base = (size_t)cl * kNumBuckets;
+    cudaEventRecord(h->fork_ev[cl], c.s);
+    for (int b = 0; b < kNumBuckets; b++) {
+      const int64_t cnt = ho[base + b + 1] - ho[base + b];
+      if (cnt <= 0) continue;
+      Ctx cb = c;
+      cb.s = h->side[b];
+      cb.launches = 0;
+      cudaStreamWaitEvent(cb.s, h->fork_ev[cl], 0);
+      if (b < kNumBuckets - 1) move_bucket<M>(cb, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
+      else giant_move<M>(cb, g, st, ws.glist, gofs[cl], gofs[cl + 1], ws.gp, !det, pruning);
+      c.launches += cb.launches;
+      cudaEventRecord(h->join_ev[base + b], cb.s);
+      cudaStreamWaitEvent(c.s, h->join_ev[base + b], 0);
+    }
+    if (det) move_apply<M>(c, st, ws.perm + ho[base], ho[base + kNumBuckets] - ho[base]);
+  }
+  if (gc) batch_finish<M>(c, ws.ctrl, gc, n_graphs);
+  else move_finish<M>(c, ws.ctrl);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(c.s, &graph);
+  *launches = c.launches - l0;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_err(h, e, "graph capture end");
+  }
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *exec = nullptr;
+    return cuda_err(h, e, "graph instantiation");
+  }
+  return LOUVAIN_OK;
 }
 
 template <class M>
@@ -903,6 +1003,11 @@ void louvain_destroy(louvain_handle h) {
   free_all(h->ws.batch_alloc);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->fork_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->join_ev) cudaEventDestroy(e);
+  for (cudaStream_t st : h->side)
+    if (st) cudaStreamDestroy(st);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pin) cudaFreeHost(h->pin);
   delete h;
 }

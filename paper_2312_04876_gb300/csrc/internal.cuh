@@ -114,6 +114,8 @@ struct GlobalTable {
 template <class M>
 void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
                  const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning);
+// Shared-memory opt-ins of the local-move kernels (call before capturing launches into a graph).
+void move_prepare();
 // Deterministic mode: Sigma updates of the moves decided in list[0, count).
 template <class M>
 void move_apply(Ctx& c, const PassState<M>& st, const int32_t* list, int64_t count);

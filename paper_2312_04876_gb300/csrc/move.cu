@@ -12,6 +12,8 @@
 // A moved vertex re-marks its neighbours for processing (vertex pruning, Section 4.1.6).  The
 // sum of the performed N is accumulated exactly (128-bit) and move_finish applies the
 // per-iteration tolerance test of Algorithm 2 on the device, so iterations need no host sync.
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace lv {
@@ -252,11 +254,36 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
 }
 
 template <class M, int G, int LOG, bool GLOBAL>
+static constexpr size_t lm_smem() {
+  return (size_t)(G <= 32 ? kBlock / G : 1) * (GLOBAL ? 1 : (1 << LOG)) * (sizeof(int32_t) + sizeof(typename M::h_t));
+}
+
+// Opts a kernel into more than 48 KB of dynamic shared memory, once per device (outside any graph
+// capture: move_prepare runs it for every instantiation before an iteration is captured).
+template <class M, int G, int LOG, bool GLOBAL>
+static void lm_attr() {
+  constexpr size_t smem = lm_smem<M, G, LOG, GLOBAL>();
+  if (smem <= 48 * 1024) return;
+  static std::atomic<unsigned long long> done{0};  // one bit per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && (done.load() >> dev) & 1ULL) return;
+  cudaFuncSetAttribute(lm_kernel<M, G, LOG, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (dev < 64) done.fetch_or(1ULL << dev);
+}
+
+void move_prepare() {
+  lm_attr<IntMode, 32, 10, false>();
+  lm_attr<IntMode, 256, 13, false>();
+  lm_attr<FpMode, 32, 10, false>();
+  lm_attr<FpMode, 256, 13, false>();
+}
+
+template <class M, int G, int LOG, bool GLOBAL>
 static void launch_lm(Ctx& c, const LmArgs<M>& a, int max_blocks) {
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
-  constexpr size_t smem = (size_t)GPB * (GLOBAL ? 1 : (1 << LOG)) * (sizeof(int32_t) + sizeof(typename M::h_t));
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(lm_kernel<M, G, LOG, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr size_t smem = lm_smem<M, G, LOG, GLOBAL>();
+  lm_attr<M, G, LOG, GLOBAL>();
   int grid = grid_for(a.count, GPB, max_blocks);
   lm_kernel<M, G, LOG, GLOBAL><<<grid, kBlock, smem, c.s>>>(a);
   c.launches++;

@@ -103,6 +103,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def replica_time(ms: float, ws: int, device="cpu") -> float:
+    """Slowest rank's time: one MAX all-reduce over the replicas (identity for one process)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, steps: int, ws: int, ms_max: float) -> float:
+    """Whole-job throughput: the units every replica processed over the slowest rank's time."""
+    return ws * steps * units_per_rank / (ms_max / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -209,6 +225,8 @@ def run_batch_bench(args):
     import paper_2312_04876_gb300 as lv
 
     ws, rank, local = dist_env()
+    if rank != 0:
+        return 0  # a one-GPU measurement: under torchrun the other ranks leave at once
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
@@ -287,6 +305,8 @@ def run_serve_bench(args):
     from concurrent.futures import ThreadPoolExecutor
 
     ws, rank, local = dist_env()
+    if rank != 0:
+        return 0  # a one-GPU measurement: under torchrun the other ranks leave at once
     torch.cuda.set_device(local)
     R = args.serve_requests
     t0 = time.perf_counter()
@@ -439,18 +459,13 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replica_time(ev0.elapsed_time(ev1), ws, dev)
     ms_step = ms / args.steps
     msha = None
     if args.mode == "deterministic":
         import hashlib
         msha = hashlib.sha256(mem.cpu().numpy().astype("<i4").tobytes()).hexdigest()
-    value = ws * args.steps * g.n_arcs / (ms / 1e3)
+    value = replica_value(g.n_arcs, args.steps, ws, ms)
     launches = sum(r.kernel_launches for r in results)
     last = results[-1]
 
@@ -467,13 +482,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(k2):
             L.run_host(ho, ht, hw, params, membership=hm)
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ws * k2 * g.n_arcs / dt, "unit": "edges/s",
+        dt = replica_time(1e3 * (time.perf_counter() - t0), ws, dev)
+        e2e = {"value": replica_value(g.n_arcs, k2, ws, dt), "unit": "edges/s",
                "h2d_bytes_per_step": int(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes),
                "d2h_bytes_per_step": int(4 * g.n), "steps": k2}
 

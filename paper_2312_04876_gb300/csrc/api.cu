@@ -35,8 +35,11 @@ struct Workspace {
   void *K0 = nullptr, *K = nullptr, *Sig = nullptr, *tot = nullptr;  // 8-byte accumulators
   int32_t *Cp = nullptr, *colour = nullptr, *csize = nullptr, *mv_from = nullptr, *mv_to = nullptr;
   int32_t *perm = nullptr, *cperm = nullptr, *occ = nullptr, *counts = nullptr, *cursor = nullptr;
-  int32_t *cverts = nullptr, *jcnt = nullptr, *jl0 = nullptr, *jl1 = nullptr, *tmp_mem = nullptr;
-  unsigned long long* jrc = nullptr;
+  int32_t *cverts = nullptr, *jcnt = nullptr, *jl0 = nullptr, *jl1 = nullptr, *jbig = nullptr;
+  unsigned long long *jrc = nullptr, *jbc = nullptr, *jround = nullptr;
+  int64_t* jboff = nullptr;
+  unsigned* jused = nullptr;
+  int64_t jused_cap = 0;
   uint8_t* flags = nullptr;
   int64_t *newid = nullptr, *coff = nullptr, *cdeg = nullptr, *len = nullptr, *tile_tmp = nullptr;
   RowSet rows[2];
@@ -188,7 +191,10 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
        dalloc(h, d, &ws.mv_from, n1) && dalloc(h, d, &ws.mv_to, n1) && dalloc(h, d, &ws.perm, n1) &&
        dalloc(h, d, &ws.cperm, n1) && dalloc(h, d, &ws.occ, n1) && dalloc(h, d, &ws.counts, n1) &&
        dalloc(h, d, &ws.cursor, n1) && dalloc(h, d, &ws.cverts, n1) && dalloc(h, d, &ws.jcnt, n1) &&
-       dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.tmp_mem, n1);
+       dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.jbig, n1);
+  ws.jused_cap = ac / 32 + n1 + 64;
+  ok = ok && dalloc(h, d, &ws.jboff, n1 + 1) && dalloc(h, d, &ws.jused, ws.jused_cap) &&
+       dalloc(h, d, &ws.jbc, n1 + 64) && dalloc(h, d, &ws.jround, 1);
   ok = ok && dalloc(h, d, &ws.flags, n1) && dalloc(h, d, &ws.dperm, n1) && dalloc(h, d, &ws.csz, n1);
   // giant plans: giant rows have > 4096 arcs, so there are at most A / 4097 of them; chunks of >= 512
   // arcs over their rows: <= gcap + A / 512; slices of >= 128 slots over tables of < 4 x the arcs:
@@ -206,7 +212,7 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   }
   ok = ok && dalloc(h, d, &ws.glist, gcap);
   ok = ok && dalloc(h, d, &ws.newid, n1 + 1) && dalloc(h, d, &ws.coff, n1 + 1) && dalloc(h, d, &ws.cdeg, n1 + 1) &&
-       dalloc(h, d, &ws.len, n1 + 1) && dalloc(h, d, &ws.jrc, n1 + 16) &&
+       dalloc(h, d, &ws.len, n1 + 1) && dalloc(h, d, &ws.jrc, n1 + 64) &&
        dalloc(h, d, &ws.tile_tmp, scan_tmp_elems((int64_t)kNumBuckets * n1 + 8) + 8);  // class sort scans 5 n keys
   for (int r = 0; r < 2 && ok; r++)
     ok = dalloc(h, d, &ws.rows[r].hoff, n1 + 1) && dalloc(h, d, &ws.rows[r].hend, n1) &&
@@ -441,7 +447,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   int32_t ncol = 1;
   if (det) {
     GraphView<int32_t> gs{g.n, g.rbeg, g.rend, g.tg, nullptr};
-    JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1, ws.n_cap + 1, ws.jrc};
+    JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1, ws.n_cap + 1, ws.jrc, ws.jbc, ws.jbig, ws.jboff, ws.jused, ws.jused_cap,
+                 ws.jround, ws.tile_tmp};
     if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
     cudaError_t ce;
     const int pm = prof_begin(h, c);
@@ -1275,7 +1282,8 @@ louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const
   GraphView<int32_t> g{n, d_offsets, d_offsets + 1, d_targets, nullptr};
   int64_t hb[kNumBuckets + 1], gslots;
   if ((s = degree_buckets(h, c, g, hb, &gslots)) != LOUVAIN_OK) return s;
-  JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1, h->ws.n_cap + 1, h->ws.jrc};
+  JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1, h->ws.n_cap + 1, h->ws.jrc, h->ws.jbc, h->ws.jbig, h->ws.jboff,
+               h->ws.jused, h->ws.jused_cap, h->ws.jround, h->ws.tile_tmp};
   cudaError_t ce;
   int32_t nc = jp_colour(c, g, h->ws.dperm, hb, seed, pass, d_colour, jb, ctrl, h->pin, &ce);
   if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");

@@ -4,12 +4,23 @@
 // (Section 2).  Here: priority p(v) = hash3(seed, pass, v), u before v iff (p(u), u) > (p(v), v).
 // A vertex is coloured once every higher-priority neighbour is, with the smallest colour none of
 // them holds -- exactly greedy colouring in decreasing priority, whatever the round structure.
-// Push form: cnt[v] = number of higher-priority neighbour arcs; a coloured vertex decrements the
-// counters of its lower-priority neighbours and appends those reaching zero to the next ready
-// list.  Rounds are launched in batches; a round with an empty ready list returns at once.
+//
+// Push form.  cnt[v] = number of higher-priority neighbour arcs; used[v] = a bitmap of the colours
+// its coloured higher-priority neighbours hold, ceil((deg + 1) / 32) words (its colour is at most
+// its degree, so larger colours need no bit).  A round takes the ready list (cnt = 0): each vertex
+// reads the first free bit of its bitmap as its colour, then pushes to every lower-priority
+// neighbour -- sets the colour's bit and decrements the counter, appending the neighbours that
+// reach zero to the next ready list.  The push of a vertex with more than kBigDeg arcs is spread
+// over the whole grid by a second kernel, so a chain of hubs (a dense core needs one round per
+// member) costs microseconds per round, not a warp's walk over 10^5 arcs.  The round index lives
+// on the device, so a batch of rounds is captured once as a CUDA graph and replayed until every
+// vertex is coloured; a round with an empty ready list returns at once.
 #include "internal.cuh"
 
 namespace lv {
+
+constexpr int64_t kBigDeg = 1024;  // pushes of longer rows are spread over the grid
+constexpr int kRoundsPerGraph = 16;
 
 struct JpArgs {
   GraphView<int32_t> g;
@@ -18,11 +29,26 @@ struct JpArgs {
   int32_t* colour;
   int32_t* cnt;
   int32_t* lists[2];
-  int64_t list_cap;             // capacity of each ready list
+  int64_t list_cap;             // capacity of each ready list (and of the big list)
   unsigned long long* rcount;   // rcount[r] = size of the ready list of round r (zeroed up front)
+  unsigned long long* bcount;   // bcount[r] = vertices of round r whose push is spread (zeroed up front)
+  int32_t* big;                 // those vertices
+  const int64_t* boff;          // [n + 1] first bitmap word of each vertex
+  unsigned* used;               // the bitmaps (zeroed up front)
+  unsigned long long* round;    // current round (device)
   Ctrl* ctrl;                   // cnt[3] coloured total, cnt[4] max colour + 1, cnt[7] guard trips
   Segs seg;                     // batched run: priorities hash graph-local ids
 };
+
+__device__ __forceinline__ uint64_t prio(const JpArgs& a, int32_t v) {
+  return hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, v));
+}
+
+// Bitmap words of every vertex: ceil((deg + 1) / 32).
+__global__ void jp_words(GraphView<int32_t> g, int64_t* words) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x)
+    words[v] = (g.rend[v] - g.rbeg[v] + 1 + 31) / 32;
+}
 
 template <int G>
 __global__ void __launch_bounds__(kBlock) jp_count(JpArgs a, const int32_t* list, int64_t count) {
@@ -32,11 +58,11 @@ __global__ void __launch_bounds__(kBlock) jp_count(JpArgs a, const int32_t* list
   const unsigned lane = Grp<G>::lane();
   for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
     const int32_t v = list[idx];
-    const uint64_t pv = hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, v));
+    const uint64_t pv = prio(a, v);
     int32_t k = 0;
     for (int64_t e = a.g.rbeg[v] + lane; e < a.g.rend[v]; e += G) {
       const int32_t u = a.g.tg[e];
-      if (u != v && higher(hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, u)), u, pv, v)) k++;
+      if (u != v && higher(prio(a, u), u, pv, v)) k++;
     }
     k = group_sum<G>(k, red);
     if (lane == 0) {
@@ -51,11 +77,26 @@ __global__ void __launch_bounds__(kBlock) jp_count(JpArgs a, const int32_t* list
   }
 }
 
-// One round: a warp per ready vertex; mex over windows of 1024 colours in a shared bitmap.
-__global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
-  __shared__ unsigned bm[kBlock / 32][32];
+// Push of the colour c of v along arc e: the neighbour u of lower priority records c and, when its
+// last higher-priority neighbour is done, joins the next ready list.
+__device__ __forceinline__ void jp_push(const JpArgs& a, int32_t v, uint64_t pv, int32_t c, int32_t u, int32_t* out,
+                                        unsigned long long* next_count) {
+  if (u == v || !higher(pv, v, prio(a, u), u)) return;
+  const int64_t w0 = a.boff[u], nw = a.boff[u + 1] - w0;
+  if ((int64_t)(c >> 5) < nw) atomicOr(&a.used[w0 + (c >> 5)], 1u << (c & 31));
+  if (atomicSub(&a.cnt[u], 1) == 1) {
+    const unsigned long long pos = atomicAdd(next_count, 1ULL);
+    if ((int64_t)pos < a.list_cap) out[pos] = u;
+    else atomicAdd(&a.ctrl->cnt[7], 1ULL);
+  }
+}
+
+// One round, part 1: a warp per ready vertex takes the first free colour of its bitmap, then
+// pushes along its arcs (rows longer than kBigDeg go to the big list instead).
+__global__ void __launch_bounds__(kBlock) jp_round(JpArgs a) {
   __shared__ unsigned long long done_blk;
   __shared__ int32_t max_blk;
+  const unsigned long long r = *(volatile unsigned long long*)a.round;
   const int32_t* in = a.lists[r & 1];
   int32_t* out = a.lists[(r + 1) & 1];
   unsigned long long count = *(volatile unsigned long long*)&a.rcount[r];
@@ -63,61 +104,47 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
   if ((int64_t)count > a.list_cap) count = (unsigned long long)a.list_cap;
   if (threadIdx.x == 0) { done_blk = 0; max_blk = 0; }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
-  for (int64_t k = (int64_t)blockIdx.x * (kBlock / 32) + warp; k < (int64_t)count; k += nw) {
+  for (int64_t k = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); k < (int64_t)count; k += nw) {
     const int32_t v = in[k];
     // guard: a ready vertex is uncoloured; anything else is recorded and skipped
-    int32_t prev = 0;
-    if (lane == 0) prev = a.colour[v];
-    prev = __shfl_sync(0xffffffffu, prev, 0);
+    const int32_t prev = a.colour[v];
     if (prev != -1) {
       if (lane == 0) atomicAdd(&a.ctrl->cnt[7], 1ULL);
       continue;
     }
-    const uint64_t pv = hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, v));
-    const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
-    int32_t mex = -1;
-    // colours of higher-priority neighbours are final; mex <= degree, so windows are bounded
-    for (int32_t base = 0; base <= (int32_t)(end - beg); base += 1024) {
-      bm[warp][lane] = 0u;
-      __syncwarp();
-      for (int64_t e = beg + lane; e < end; e += 32) {
-        const int32_t u = a.g.tg[e];
-        if (u == v || !higher(hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, u)), u, pv, v)) continue;
-        const int32_t cu = a.colour[u] - base;
-        if (cu >= 0 && cu < 1024) atomicOr(&bm[warp][cu >> 5], 1u << (cu & 31));
-      }
-      __syncwarp();
-      const unsigned freeb = ~bm[warp][lane];
+    // first free bit; it exists: the colours recorded number at most the degree
+    const int64_t w0 = a.boff[v], words = a.boff[v + 1] - w0;
+    int32_t col = -1;
+    for (int64_t wb = 0; wb < words; wb += 32) {
+      const unsigned freeb = wb + lane < words ? ~a.used[w0 + wb + lane] : 0u;
       const unsigned ball = __ballot_sync(0xffffffffu, freeb != 0u);
-      __syncwarp();
       if (ball) {
         const int L = __ffs(ball) - 1;
         const unsigned fw = __shfl_sync(0xffffffffu, freeb, L);
-        mex = base + 32 * L + (__ffs(fw) - 1);
+        col = (int32_t)(32 * (wb + L)) + (__ffs(fw) - 1);
         break;
       }
     }
-    if (mex < 0) {  // unreachable: some colour <= degree is always free
+    if (col < 0) {  // unreachable
       if (lane == 0) atomicOr(&a.ctrl->error, kErrRange);
-      mex = 0;
+      col = 0;
     }
+    const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
     if (lane == 0) {
-      a.colour[v] = mex;
+      a.colour[v] = col;
       atomicAdd(&done_blk, 1ULL);
-      atomicMax(&max_blk, mex + 1);
-    }
-    __syncwarp();
-    for (int64_t e = beg + lane; e < end; e += 32) {
-      const int32_t u = a.g.tg[e];
-      if (u == v || !higher(pv, v, hash3(a.seed, (uint64_t)a.pass, local_id(a.seg, u)), u)) continue;
-      if (atomicSub(&a.cnt[u], 1) == 1) {
-        const unsigned long long pos = atomicAdd(&a.rcount[r + 1], 1ULL);
-        if ((int64_t)pos < a.list_cap) out[pos] = u;
+      atomicMax(&max_blk, col + 1);
+      if (end - beg > kBigDeg) {
+        const unsigned long long pos = atomicAdd(&a.bcount[r], 1ULL);
+        if ((int64_t)pos < a.list_cap) a.big[pos] = v;
         else atomicAdd(&a.ctrl->cnt[7], 1ULL);
       }
     }
+    if (end - beg > kBigDeg) continue;
+    const uint64_t pv = prio(a, v);
+    for (int64_t e = beg + lane; e < end; e += 32) jp_push(a, v, pv, col, a.g.tg[e], out, &a.rcount[r + 1]);
   }
   __syncthreads();
   if (threadIdx.x == 0 && done_blk) {
@@ -126,10 +153,32 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a, int r) {
   }
 }
 
-__global__ void k_jp_reset(Ctrl* c) {
+// One round, part 2: the pushes of the big vertices, every arc of every one spread over the grid.
+__global__ void __launch_bounds__(kBlock) jp_round_big(JpArgs a) {
+  const unsigned long long r = *(volatile unsigned long long*)a.round;
+  unsigned long long nb = *(volatile unsigned long long*)&a.bcount[r];
+  if (nb == 0) return;
+  if ((int64_t)nb > a.list_cap) nb = (unsigned long long)a.list_cap;
+  int32_t* out = a.lists[(r + 1) & 1];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (unsigned long long k = 0; k < nb; k++) {
+    const int32_t v = a.big[k];
+    const uint64_t pv = prio(a, v);
+    const int32_t col = a.colour[v];
+    const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
+    for (int64_t e = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < end; e += stride)
+      jp_push(a, v, pv, col, a.g.tg[e], out, &a.rcount[r + 1]);
+  }
+}
+
+// Advances the round once both parts are done.
+__global__ void jp_next(unsigned long long* round) { *round += 1; }
+
+__global__ void k_jp_reset(Ctrl* c, unsigned long long* round) {
   c->cnt[3] = 0;
   c->cnt[4] = 0;
   c->cnt[7] = 0;
+  *round = 0;
 }
 
 int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, const int64_t* hb, uint64_t seed,
@@ -138,16 +187,26 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
   *err = cudaSuccess;
   const int64_t listed = hb[kNumBuckets] - hb[0];
   // Each round colours at least one vertex while any is left, so `listed` rounds always suffice.
-  const int batch = 8;
-  const int64_t max_rounds = listed + batch;
+  const int64_t max_rounds = listed + kRoundsPerGraph;
   // isolated vertices (left out of the bucket lists) get colour 0
   fill_i32(c, colour, 0, g.n);
-  cudaMemsetAsync(jb.rcount, 0, (size_t)(max_rounds + 2) * sizeof(unsigned long long), c.s);
-  k_jp_reset<<<1, 1, 0, c.s>>>(ctrl);
+  // the last replay may run up to kRoundsPerGraph - 1 rounds past max_rounds (they find empty lists)
+  const size_t nrc = (size_t)(max_rounds + kRoundsPerGraph + 2);
+  cudaMemsetAsync(jb.rcount, 0, nrc * sizeof(unsigned long long), c.s);
+  cudaMemsetAsync(jb.bcount, 0, nrc * sizeof(unsigned long long), c.s);
+  // bitmap offsets (scan of the word counts) and zeroed bitmaps
+  if (g.n > 0) {
+    jp_words<<<grid_for(g.n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(g, jb.boff);
+    c.launches++;
+  }
+  scan_exclusive_i64(c, jb.boff, jb.boff, g.n, jb.tile_tmp);
+  cudaMemsetAsync(jb.used, 0, (size_t)jb.used_cap * sizeof(unsigned), c.s);
+  k_jp_reset<<<1, 1, 0, c.s>>>(ctrl, jb.round);
   c.launches++;
   JpArgs a;
   a.g = g; a.seed = seed; a.pass = pass; a.colour = colour; a.cnt = jb.cnt;
-  a.lists[0] = jb.list0; a.lists[1] = jb.list1; a.list_cap = jb.list_cap; a.rcount = jb.rcount; a.ctrl = ctrl;
+  a.lists[0] = jb.list0; a.lists[1] = jb.list1; a.list_cap = jb.list_cap; a.rcount = jb.rcount;
+  a.bcount = jb.bcount; a.big = jb.big; a.boff = jb.boff; a.used = jb.used; a.round = jb.round; a.ctrl = ctrl;
   a.seg = seg;
   const int cap = c.num_sms * 16;
   for (int b = 0; b < kNumBuckets; b++) {
@@ -164,19 +223,39 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
     c.launches++;
   }
   if ((*err = cudaGetLastError()) != cudaSuccess) return -1;
+  // kRoundsPerGraph rounds (3 kernels each) captured once on a private stream, replayed on c.s
+  cudaGraphExec_t exec = nullptr;
+  {
+    cudaStream_t cs = nullptr;
+    if ((*err = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return -1;
+    cudaGraph_t graph = nullptr;
+    *err = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (*err == cudaSuccess) {
+      for (int k = 0; k < kRoundsPerGraph; k++) {
+        jp_round<<<c.num_sms * 8, kBlock, 0, cs>>>(a);
+        jp_round_big<<<c.num_sms * 8, kBlock, 0, cs>>>(a);
+        jp_next<<<1, 1, 0, cs>>>(jb.round);
+      }
+      *err = cudaStreamEndCapture(cs, &graph);
+    }
+    if (*err == cudaSuccess) *err = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (*err != cudaSuccess) return -1;
+  }
   int64_t r = 0;
   h_pinned[3] = 0;
   while (r < max_rounds) {
-    for (int k = 0; k < batch && r < max_rounds; k++, r++) {
-      jp_round<<<c.num_sms * 8, kBlock, 0, c.s>>>(a, (int)r);
-      c.launches++;
-    }
-    if ((*err = cudaGetLastError()) != cudaSuccess) return -1;
+    cudaGraphLaunch(exec, c.s);
+    r += kRoundsPerGraph;
+    c.launches += 3 * kRoundsPerGraph;
     cudaMemcpyAsync(h_pinned, &ctrl->cnt[0], 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.s);
     *err = cudaStreamSynchronize(c.s);
-    if (*err != cudaSuccess) return -1;
+    if (*err != cudaSuccess) break;
     if ((int64_t)h_pinned[3] >= listed || h_pinned[7]) break;
   }
+  cudaGraphExecDestroy(exec);
+  if (*err != cudaSuccess) return -1;
   if ((int64_t)h_pinned[3] != listed || h_pinned[7]) {
     h_pinned[5] = (unsigned long long)listed;
     h_pinned[6] = (unsigned long long)r;

@@ -128,7 +128,14 @@ struct JpBuffers {
   int32_t* list0;               // [list_cap] ready lists
   int32_t* list1;
   int64_t list_cap;
-  unsigned long long* rcount;   // [n + 16] per-round ready-list sizes
+  unsigned long long* rcount;   // [n + 64] per-round ready-list sizes
+  unsigned long long* bcount;   // [n + 64] per-round counts of vertices whose push is spread
+  int32_t* big;                 // [list_cap] those vertices
+  int64_t* boff;                // [n + 1] bitmap word offsets
+  unsigned* used;               // [used_cap] colour bitmaps, ceil((deg + 1) / 32) words per vertex
+  int64_t used_cap;             // >= A / 32 + n
+  unsigned long long* round;    // [1] current round
+  int64_t* tile_tmp;            // scan scratch
 };
 // Jones-Plassmann colouring of g (self-loops ignored).  Returns the number of colours.
 // Uses ctrl->cnt[3, 4, 7]; synchronises the stream once per batch of rounds.

@@ -391,6 +391,8 @@ def main():
                     help="batch workload: time the one-at-a-time path on the first K graphs only (0 = all)")
     ap.add_argument("--fast-classes", type=int, default=None, help="random vertex classes of the fast schedule")
     ap.add_argument("--compact", type=int, default=None, help="1: compact super-vertex graphs, 0: keep holey CSR")
+    ap.add_argument("--fast-giant-class", type=int, default=None,
+                    help="fast mode: 1 puts every giant row of a pass in one class")
     ap.add_argument("--ncu-window", action="store_true",
                     help="after warm-up run ONE step between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints no bench line")
@@ -425,6 +427,8 @@ def main():
         knobs["fast_classes"] = args.fast_classes
     if args.compact is not None:
         knobs["compact"] = args.compact
+    if args.fast_giant_class is not None:
+        knobs["fast_giant_class"] = args.fast_giant_class
     params = lv.default_params(mode=args.mode, validate=0, **knobs)
     mem = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()

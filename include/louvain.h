@@ -78,7 +78,8 @@ typedef struct {
   int32_t fast_classes;          /* fast mode: vertices are split into this many random classes
                                     (hash3(seed, pass, v) mod K) processed one after another; moves
                                     inside a class stay asynchronous.  Default 16; 1 = all at once */
-  int32_t reserved;
+  int32_t fast_giant_class;      /* fast mode: 1 = every giant row (> 4096 arcs) of a pass in one class
+                                    (one multi-block giant pipeline per iteration); 0 = hash classes */
 } louvain_params;
 
 typedef struct {

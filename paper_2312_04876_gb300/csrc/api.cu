@@ -203,7 +203,7 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   for (GiantPlan* gp : {&ws.gp, &ws.gpv})
     ok = ok && dalloc(h, d, &gp->chunk_off, gcap + 1) && dalloc(h, d, &gp->tab_off, gcap + 1) &&
          dalloc(h, d, &gp->slice_off, gcap + 1) && dalloc(h, d, (int32_t**)&gp->kid, gcap) &&
-         dalloc(h, d, &gp->moved, gcap) && dalloc(h, d, &gp->active, gcap) &&
+         dalloc(h, d, &gp->moved, gcap) && dalloc(h, d, &gp->active, gcap) && dalloc(h, d, &gp->rdone, gcap) &&
          dalloc(h, d, (long long**)&gp->part_s, scap) &&
          dalloc(h, d, &gp->part_c, scap) && dalloc(h, d, &gp->cowner, ccap) && dalloc(h, d, &gp->sowner, scap);
   for (GiantPlan* gp : {&ws.gp, &ws.gpv}) {
@@ -470,6 +470,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
     KeyDesc kd{3, ncol, pass, p.seed ^ 0x46A57C1A55E5ULL};
     kd.seg = seg;
+    // giant rows all in one class per pass (one giant pipeline per iteration instead of one per class)
+    if (p.fast_giant_class) kd.giant_class = (int)(hash3(p.seed, (uint64_t)pass, 0x6A09E667ULL) % (uint64_t)ncol);
     bucket_sort(c, kd, g.n, g.rbeg, g.rend, nullptr, nullptr, nkeys, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
                 nullptr);
     const int64_t* q = read_i64(h, c, ws.keyoffs, nkeys + 1, &s, "fast classes");

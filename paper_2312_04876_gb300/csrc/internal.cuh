@@ -51,6 +51,7 @@ struct KeyDesc {
   int pass = 0;
   uint64_t seed = 0;
   Segs seg;  // kind 3 hashes the graph-local id
+  int giant_class = -1;  // kind 3: >= 0 puts every giant row in this class
 };
 
 // Counting sort of vertex ids by key.  key_kind 0: degree bucket of (rend - rbeg); 1: colour *
@@ -186,6 +187,7 @@ struct GiantPlan {
   void* kid = nullptr;           // [cap] K_i->d accumulators (h_t)
   uint8_t* moved = nullptr;      // [cap]
   uint8_t* active = nullptr;     // [cap] local move: processed in the current class iteration
+  unsigned* rdone = nullptr;     // [cap] local move: ranges scanned in the current iteration
   void* part_s = nullptr;        // [slice_cap] best score per slice (s_t)
   int32_t* part_c = nullptr;     // [slice_cap] its community
   int32_t* cowner = nullptr;     // [chunk_cap] giant of each chunk

@@ -131,8 +131,12 @@ __device__ __forceinline__ int sort_key(KeyDesc kd, int64_t i, const int64_t* rb
   if (kd.kind == 2) return degree_bucket(deg64[i]);
   int b = degree_bucket(rend[i] - rbeg[i]);
   if (kd.kind == 0 || b < 0) return b;
-  if (kd.kind == 3)  // hash class of the fast schedule
-    return (int)(hash3(kd.seed, (uint64_t)kd.pass, local_id(kd.seg, (int32_t)i)) % (uint64_t)kd.classes) * kNumBuckets + b;
+  if (kd.kind == 3) {  // hash class of the fast schedule; giant rows optionally all in one class
+    const uint64_t h = kd.giant_class >= 0 && b == kNumBuckets - 1
+                           ? (uint64_t)kd.giant_class
+                           : hash3(kd.seed, (uint64_t)kd.pass, local_id(kd.seg, (int32_t)i));
+    return (int)(h % (uint64_t)kd.classes) * kNumBuckets + b;
+  }
   return colour[i] * kNumBuckets + b;
 }
 

@@ -91,6 +91,8 @@ typedef struct {
   int64_t n_communities;         /* |Gamma| after the local-moving phase */
   double modularity;             /* Q after the local-moving phase (NaN unless pass_modularity) */
   float ms_colour, ms_move, ms_aggregate, ms_other;
+  int32_t colours;               /* deterministic mode: colour classes of the pass (0 in fast mode) */
+  int32_t colour_rounds;         /* deterministic mode: Jones-Plassmann rounds that coloured vertices */
 } louvain_pass_stats;
 
 typedef struct {

@@ -203,7 +203,7 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   for (GiantPlan* gp : {&ws.gp, &ws.gpv})
     ok = ok && dalloc(h, d, &gp->chunk_off, gcap + 1) && dalloc(h, d, &gp->tab_off, gcap + 1) &&
          dalloc(h, d, &gp->slice_off, gcap + 1) && dalloc(h, d, (int32_t**)&gp->kid, gcap) &&
-         dalloc(h, d, &gp->moved, gcap) && dalloc(h, d, &gp->active, gcap) && dalloc(h, d, &gp->rdone, gcap) &&
+         dalloc(h, d, &gp->moved, gcap) && dalloc(h, d, &gp->active, gcap) &&
          dalloc(h, d, (long long**)&gp->part_s, scap) &&
          dalloc(h, d, &gp->part_c, scap) && dalloc(h, d, &gp->cowner, ccap) && dalloc(h, d, &gp->sowner, scap);
   for (GiantPlan* gp : {&ws.gp, &ws.gpv}) {
@@ -432,7 +432,8 @@ template <class M>
 louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const int64_t hb[],
                                 int64_t giant_slots, const louvain_params& p, int32_t pass, double tau, int32_t* li,
                                 int64_t* moves, size_t ev_colour_done, GraphCtl* gc = nullptr,
-                                const int32_t* vg = nullptr, int32_t n_graphs = 0) {
+                                const int32_t* vg = nullptr, int32_t n_graphs = 0, int32_t* colours = nullptr,
+                                int32_t* colour_rounds = nullptr) {
   Workspace& ws = h->ws;
   PassState<M> st{reinterpret_cast<typename M::a_t*>(ws.K), reinterpret_cast<typename M::a_t*>(ws.Sig), ws.Cp,
                   ws.flags, ws.csize, ws.mv_from, ws.mv_to, ws.ctrl};
@@ -452,10 +453,13 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
     cudaError_t ce;
     const int pm = prof_begin(h, c);
-    ncol = jp_colour(c, gs, ws.dperm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce, seg);
+    int64_t rounds = 0;
+    ncol = jp_colour(c, gs, ws.dperm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce, seg, &rounds);
     prof_end(h, c, kColour, pm);
     if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
     if (ncol < 0) return colour_failure(h);
+    if (colours) *colours = ncol;
+    if (colour_rounds) *colour_rounds = (int32_t)rounds;
     const int64_t nkeys = (int64_t)ncol * kNumBuckets;
     if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
     bucket_sort(c, KeyDesc{1, 1, 0, 0}, g.n, g.rbeg, g.rend, ws.colour, nullptr, nkeys, ws.perm, ws.keyoffs, ws.keycur, ws.tile_tmp,
@@ -700,7 +704,10 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
     // (a2-a5) local-moving phase
     int32_t li = 0;
     int64_t moves = 0;
-    if ((s = local_move_phase<M>(h, c, g, hb, gslots, p, lp, tau, &li, &moves, e0 + 2)) != LOUVAIN_OK) return s;
+    int32_t ncolours = 0, nrounds = 0;
+    if ((s = local_move_phase<M>(h, c, g, hb, gslots, p, lp, tau, &li, &moves, e0 + 2, nullptr, nullptr, 0, &ncolours,
+                                 &nrounds)) != LOUVAIN_OK)
+      return s;
     cudaEventRecord(h->events[e0 + 3], c.s);
     pending = true;
     out->passes = lp + 1;
@@ -722,6 +729,7 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
     if (ps) {
       ps->pass = lp; ps->iterations = li; ps->moves = moves; ps->n_vertices = n_cur; ps->n_arcs = g_arcs;
       ps->n_communities = nc; ps->modularity = pass_q;
+      ps->colours = ncolours; ps->colour_rounds = nrounds;
       if (n_stats) *n_stats = lp + 1;
     }
     const bool stop = li <= 1 || (double)nc / (double)n_cur > p.aggregation_tolerance;

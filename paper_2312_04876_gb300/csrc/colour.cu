@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a) {
   if (count == 0) return;
   if ((int64_t)count > a.list_cap) count = (unsigned long long)a.list_cap;
   if (threadIdx.x == 0) { done_blk = 0; max_blk = 0; }
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicMax(&a.ctrl->cnt[6], r + 1);  // rounds with work
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
@@ -177,13 +178,14 @@ __global__ void jp_next(unsigned long long* round) { *round += 1; }
 __global__ void k_jp_reset(Ctrl* c, unsigned long long* round) {
   c->cnt[3] = 0;
   c->cnt[4] = 0;
+  c->cnt[6] = 0;
   c->cnt[7] = 0;
   *round = 0;
 }
 
 int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, const int64_t* hb, uint64_t seed,
                   int32_t pass, int32_t* colour, const JpBuffers& jb, Ctrl* ctrl, unsigned long long* h_pinned,
-                  cudaError_t* err, Segs seg) {
+                  cudaError_t* err, Segs seg, int64_t* rounds_out) {
   *err = cudaSuccess;
   const int64_t listed = hb[kNumBuckets] - hb[0];
   // Each round colours at least one vertex while any is left, so `listed` rounds always suffice.
@@ -261,6 +263,7 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
     h_pinned[6] = (unsigned long long)r;
     return -1;
   }
+  if (rounds_out) *rounds_out = (int64_t)h_pinned[6];
   int32_t ncol = (int32_t)h_pinned[4];
   return ncol > 0 ? ncol : 1;
 }

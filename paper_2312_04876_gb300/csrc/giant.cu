@@ -62,7 +62,6 @@ __global__ void k_gplan_counts(int kind, const int32_t* list, int64_t m, const i
     reinterpret_cast<uint32_t*>(p.kid)[k] = 0u;  // 0u is also 0.0f
     p.moved[k] = 0;
     p.active[k] = 0;
-    p.rdone[k] = 0u;
   }
 }
 
@@ -241,69 +240,17 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
   if (!ok) atomicOr(&ctrl->error, kErrTableFull);
 }
 
-// ---------------------------------------------------------------- local move: decide (+ apply)
-// The move of giant k from the best of its ranges' partial results, exactly as the per-vertex
-// kernels make it; run by the warp that completes k's last range.
-template <class M>
-__device__ __forceinline__ void glm_decide(const int32_t* list, int64_t k, const PassState<M>& st, const GiantPlan& p,
-                                           int fast) {
-  typedef typename M::a_t A;
-  typedef typename M::s_t S;
-  const int lane = threadIdx.x & 31;
-  const int64_t q0 = p.slice_off[k], q1 = p.slice_off[k + 1];
-  S best = M::lowest();
-  int32_t bc = 0x7fffffff;
-  for (int64_t q = q0 + lane; q < q1; q += 32) {
-    // partial results of other warps: read around L1
-    const S s = (S)__ldcg(reinterpret_cast<const S*>(p.part_s) + q);
-    const int32_t c = __ldcg(p.part_c + q);
-    if (better(s, c, best, bc)) { best = s; bc = c; }
-  }
-  group_argmax<32>(best, bc, (S*)nullptr, (int32_t*)nullptr);
-  if (lane != 0) return;
-  const int32_t i = list[k];
-  const int32_t d = st.Cp[i];
-  if (bc == 0x7fffffff || !(best > S(0))) return;
-  if (fast && st.csize[d] == 1 && st.csize[bc] == 1 && bc > d) return;
-  const A ki = st.K[i];
-  if (fast) {
-    atomic_add_a(&st.Sig[d], -ki);
-    atomic_add_a(&st.Sig[bc], ki);
-    atomicSub(&st.csize[d], 1);
-    atomicAdd(&st.csize[bc], 1);
-  } else {
-    st.mv_from[i] = d;
-    st.mv_to[i] = bc;
-  }
-  st.Cp[i] = bc;
-  p.moved[k] = 1;
-  Ctrl* ctrl = st.ctrl;
-  atomicAdd(&ctrl->moves, 1ULL);
-  atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][4], 1ULL);
-  if (st.gc) {
-    GraphCtl* gcv = st.gc + st.vg[i];
-    if (M::is_fp) atomicAdd(&gcv->sum_f, (double)best);
-    else atomic_add_u128(&gcv->sum_lo, &gcv->sum_hi, (unsigned long long)best, 0ULL);
-  } else if (M::is_fp) {
-    atomicAdd(&ctrl->sum_f, (double)best);
-  } else {
-    atomic_add_u128(&ctrl->sum_lo, &ctrl->sum_hi, (unsigned long long)best, 0ULL);
-  }
-}
-
-// ---------------------------------------------------------------- local move: range scan + decide
+// ---------------------------------------------------------------- local move: range scan
 // One warp per range of 256 slots of an active giant's table: 2 steps of one 16-byte key load per
 // lane (tables are >= 64 slots and 64-slot aligned, so loads are aligned and never straddle two
-// tables); the Sigma gathers of a step are issued together.  The warp writes the range's best,
-// then counts the range done; the warp that completes a giant's last range makes its decision
-// (the partial results are published with a fence before the count).
+// tables); the Sigma gathers of a step are issued together.  Writes the range's best to part_s/c.
 template <class M>
-__global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_t k0, int64_t k1, PassState<M> st,
-                                                     GiantPlan p, int fast) {
+__global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_t k0, int64_t k1, const int32_t* Cp,
+                                                     const typename M::a_t* K, const typename M::a_t* Sig,
+                                                     GiantPlan p, Ctrl* ctrl, const GraphCtl* gc, const int32_t* vg) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
-  Ctrl* ctrl = st.ctrl;
   if (*(volatile int32_t*)&ctrl->done) return;
   const int64_t r0 = p.slice_off[k0], r1 = p.slice_off[k1];
   const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
@@ -314,11 +261,11 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
     const int64_t k = p.sowner[q];
     if (!p.active[k]) continue;  // uniform over the warp
     const int32_t i = list[k];
-    const int32_t d = st.Cp[i];
+    const int32_t d = Cp[i];
     const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
     const H kid = reinterpret_cast<const H*>(p.kid)[k];
-    const A ki = st.K[i], sd = st.Sig[d];
-    const A two_m = st.gc ? (M::is_fp ? (A)st.gc[st.vg[i]].two_m_f : (A)st.gc[st.vg[i]].two_m_i) : two_m_all;
+    const A ki = K[i], sd = Sig[d];
+    const A two_m = gc ? (M::is_fp ? (A)gc[vg[i]].two_m_f : (A)gc[vg[i]].two_m_i) : two_m_all;
     int32_t* tk = p.keys + off;
     H* tv = reinterpret_cast<H*>(p.vals) + off;
     const int64_t sb = (q - p.slice_off[k]) << kRangeLog;
@@ -337,7 +284,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
         sg[u] = A(0);
         if (ks[u] != kEmpty) {
           vv[u] = tv[s + u];
-          sg[u] = st.Sig[ks[u]];
+          sg[u] = Sig[ks[u]];
           tk[s + u] = kEmpty;
           tv[s + u] = H(0);
         }
@@ -351,24 +298,84 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
       }
     }
     group_argmax<32>(best, bc, (S*)nullptr, (int32_t*)nullptr);
-    int last = 0;
     if (lane == 0) {
       reinterpret_cast<S*>(p.part_s)[q] = best;
       p.part_c[q] = bc;
-      __threadfence();
-      const unsigned prev = atomicAdd(&p.rdone[k], 1u);
-      last = prev + 1 == (unsigned)(p.slice_off[k + 1] - p.slice_off[k]) ? 1 : 0;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      if (lane == 0) p.rdone[k] = 0u;  // ready for the next iteration
-      glm_decide<M>(list, k, st, p, fast);
     }
   }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
   if ((threadIdx.x & 31) == 0 && cand) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][3], cand);
+}
+
+// ---------------------------------------------------------------- local move: decide (+ apply)
+template <class M>
+__global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int64_t k0, int64_t k1, PassState<M> st,
+                                                       GiantPlan p, int fast) {
+  typedef typename M::a_t A;
+  typedef typename M::s_t S;
+  Ctrl* ctrl = st.ctrl;
+  if (*(volatile int32_t*)&ctrl->done) return;
+  unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
+  double acc_f = 0.0;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
+  for (int64_t k = k0 + (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); k < k1; k += nw) {
+    if (!p.active[k]) continue;
+    const int64_t q0 = p.slice_off[k], q1 = p.slice_off[k + 1];
+    S best = M::lowest();
+    int32_t bc = 0x7fffffff;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+      const S s = reinterpret_cast<const S*>(p.part_s)[q];
+      const int32_t c = p.part_c[q];
+      if (better(s, c, best, bc)) { best = s; bc = c; }
+    }
+    group_argmax<32>(best, bc, (S*)nullptr, (int32_t*)nullptr);
+    if (lane != 0) continue;
+    const int32_t i = list[k];
+    const int32_t d = st.Cp[i];
+    if (bc == 0x7fffffff || !(best > S(0))) continue;
+    if (fast && st.csize[d] == 1 && st.csize[bc] == 1 && bc > d) continue;
+    const A ki = st.K[i];
+    if (fast) {
+      atomic_add_a(&st.Sig[d], -ki);
+      atomic_add_a(&st.Sig[bc], ki);
+      atomicSub(&st.csize[d], 1);
+      atomicAdd(&st.csize[bc], 1);
+    } else {
+      st.mv_from[i] = d;
+      st.mv_to[i] = bc;
+    }
+    st.Cp[i] = bc;
+    p.moved[k] = 1;
+    if (st.gc) {
+      GraphCtl* gcv = st.gc + st.vg[i];
+      if (M::is_fp) atomicAdd(&gcv->sum_f, (double)best);
+      else atomic_add_u128(&gcv->sum_lo, &gcv->sum_hi, (unsigned long long)best, 0ULL);
+    } else if (M::is_fp) {
+      acc_f += (double)best;
+    } else {
+      const unsigned long long b = (unsigned long long)best;
+      acc_lo += b;
+      if (acc_lo < b) acc_hi++;
+    }
+    acc_mv++;
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, acc_lo, o), hi2 = __shfl_xor_sync(0xffffffffu, acc_hi, o);
+    unsigned long long s = acc_lo + lo2;
+    acc_hi += hi2 + (s < acc_lo ? 1ULL : 0ULL);
+    acc_lo = s;
+    acc_mv += __shfl_xor_sync(0xffffffffu, acc_mv, o);
+    if (M::is_fp) acc_f += __shfl_xor_sync(0xffffffffu, acc_f, o);
+  }
+  if (lane == 0 && acc_mv) {
+    atomicAdd(&ctrl->moves, acc_mv);
+    atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][4], acc_mv);
+    if (M::is_fp) atomicAdd(&ctrl->sum_f, acc_f);
+    else atomic_add_u128(&ctrl->sum_lo, &ctrl->sum_hi, acc_lo, acc_hi);
+  }
 }
 
 // ---------------------------------------------------------------- local move: mark neighbours
@@ -415,8 +422,9 @@ void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>&
   k_glm_activate<typename M::w_t><<<grid_for(k1 - k0, kBlock, c.num_sms * 2), kBlock, 0, c.s>>>(
       g, list, k0, k1, st.flags, pruning ? 1 : 0, st.gc, st.vg, p, st.ctrl);
   k_glm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.Cp, p, st.ctrl);
-  k_glm_scan<M><<<grid, kBlock, 0, c.s>>>(list, k0, k1, st, p, fast ? 1 : 0);
-  c.launches += 3;
+  k_glm_scan<M><<<grid, kBlock, 0, c.s>>>(list, k0, k1, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg);
+  k_glm_decide<M><<<grid_for(k1 - k0, kBlock / 32, c.num_sms * 2), kBlock, 0, c.s>>>(list, k0, k1, st, p, fast ? 1 : 0);
+  c.launches += 4;
   if (pruning) {
     k_glm_mark<typename M::w_t><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, p, st.ctrl);
     c.launches++;

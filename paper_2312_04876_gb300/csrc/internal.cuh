@@ -143,7 +143,8 @@ struct JpBuffers {
 // In a batched run `seg` makes the priority hash the graph-local id.
 int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g_struct, const int32_t* perm, const int64_t* h_bucket_offs,
                   uint64_t seed, int32_t pass, int32_t* colour, const JpBuffers& jb, Ctrl* ctrl,
-                  unsigned long long* h_pinned, cudaError_t* err, Segs seg = Segs());
+                  unsigned long long* h_pinned, cudaError_t* err, Segs seg = Segs(),
+                  int64_t* rounds_out = nullptr);
 
 // ---------------------------------------------------------------- aggregate.cu
 // counts[c] = members, cdeg[c] = sum of member degrees (both zeroed by the caller).
@@ -187,7 +188,6 @@ struct GiantPlan {
   void* kid = nullptr;           // [cap] K_i->d accumulators (h_t)
   uint8_t* moved = nullptr;      // [cap]
   uint8_t* active = nullptr;     // [cap] local move: processed in the current class iteration
-  unsigned* rdone = nullptr;     // [cap] local move: ranges scanned in the current iteration
   void* part_s = nullptr;        // [slice_cap] best score per slice (s_t)
   int32_t* part_c = nullptr;     // [slice_cap] its community
   int32_t* cowner = nullptr;     // [chunk_cap] giant of each chunk

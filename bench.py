@@ -393,6 +393,7 @@ def main():
     ap.add_argument("--compact", type=int, default=None, help="1: compact super-vertex graphs, 0: keep holey CSR")
     ap.add_argument("--fast-giant-class", type=int, default=None,
                     help="fast mode: 1 puts every giant row of a pass in one class")
+    ap.add_argument("--lm-blocks-per-sm", type=int, default=None, help="grid cap of the local-moving kernels")
     ap.add_argument("--ncu-window", action="store_true",
                     help="after warm-up run ONE step between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints no bench line")
@@ -429,6 +430,8 @@ def main():
         knobs["compact"] = args.compact
     if args.fast_giant_class is not None:
         knobs["fast_giant_class"] = args.fast_giant_class
+    if args.lm_blocks_per_sm is not None:
+        knobs["lm_blocks_per_sm"] = args.lm_blocks_per_sm
     params = lv.default_params(mode=args.mode, validate=0, **knobs)
     mem = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()

@@ -80,6 +80,10 @@ typedef struct {
                                     inside a class stay asynchronous.  Default 16; 1 = all at once */
   int32_t fast_giant_class;      /* fast mode: 1 = every giant row (> 4096 arcs) of a pass in one class
                                     (one multi-block giant pipeline per iteration); 0 = hash classes */
+  int32_t lm_blocks_per_sm;      /* grid cap of the local-moving kernels in blocks per SM (0 = 16); the
+                                    degree buckets of a class run concurrently, so smaller grids let
+                                    them share the SMs */
+  int32_t reserved;
 } louvain_params;
 
 typedef struct {

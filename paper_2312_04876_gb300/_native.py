@@ -18,7 +18,8 @@ class Params(ctypes.Structure):
                 ("aggregation_tolerance", ctypes.c_double), ("pruning", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("validate", ctypes.c_int32),
                 ("compact", ctypes.c_int32), ("pass_modularity", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("fast_classes", ctypes.c_int32), ("fast_giant_class", ctypes.c_int32)]
+                ("fast_classes", ctypes.c_int32), ("fast_giant_class", ctypes.c_int32),
+                ("lm_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PassStats(ctypes.Structure):

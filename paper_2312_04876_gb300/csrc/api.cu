@@ -359,6 +359,7 @@ float elapsed(louvain_handle h, size_t a, size_t b) {
 bool valid_params(const louvain_params* p) {
   return p && p->max_passes >= 0 && p->max_iterations >= 0 && p->tolerance >= 0.0 && p->tolerance_drop > 0.0 &&
          p->aggregation_tolerance >= 0.0 && p->fast_classes >= 0 && p->fast_classes <= 4096 &&
+         p->lm_blocks_per_sm >= 0 && p->lm_blocks_per_sm <= 64 &&
          (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
 }
 
@@ -443,6 +444,7 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   seg.vg = vg;
   seg.gc = gc;
   const bool det = p.mode == LOUVAIN_MODE_DETERMINISTIC;
+  if (p.lm_blocks_per_sm > 0) c.lm_blocks_per_sm = p.lm_blocks_per_sm;
   louvain_status s;
   std::vector<int64_t> ho;  // class-bucket offsets (deterministic) or bucket offsets (fast)
   int32_t ncol = 1;

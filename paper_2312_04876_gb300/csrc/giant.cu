@@ -418,7 +418,7 @@ template <class M>
 void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t k0,
                 int64_t k1, const GiantPlan& p, bool fast, bool pruning) {
   if (k1 <= k0) return;
-  const int grid = c.num_sms * 8;
+  const int grid = c.num_sms * (c.lm_blocks_per_sm < 8 ? c.lm_blocks_per_sm : 8);
   k_glm_activate<typename M::w_t><<<grid_for(k1 - k0, kBlock, c.num_sms * 2), kBlock, 0, c.s>>>(
       g, list, k0, k1, st.flags, pruning ? 1 : 0, st.gc, st.vg, p, st.ctrl);
   k_glm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.Cp, p, st.ctrl);

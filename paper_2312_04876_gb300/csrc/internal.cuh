@@ -13,6 +13,7 @@ struct Ctx {
   cudaStream_t s = nullptr;
   int64_t launches = 0;
   int num_sms = 152;
+  int lm_blocks_per_sm = 16;  // grid cap of the local-moving kernels (blocks per SM)
 };
 
 inline int grid_for(int64_t work_items, int items_per_block, int cap) {

@@ -301,7 +301,7 @@ void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const 
   a.fast = fast ? 1 : 0;
   a.pruning = pruning ? 1 : 0;
   a.bucket = bucket < kNumBuckets ? bucket : kNumBuckets - 1;
-  const int cap = c.num_sms * 16;
+  const int cap = c.num_sms * c.lm_blocks_per_sm;
   switch (bucket) {
     case 0: launch_lm<M, 4, 3, false>(c, a, cap); break;
     case 1: launch_lm<M, 8, 5, false>(c, a, cap); break;

@@ -54,6 +54,7 @@ struct Workspace {
   int32_t* keycur = nullptr;
   DevAlloc gt_alloc;
   int64_t gt_slots_total = 0;
+  unsigned* gt_bits = nullptr;
   GlobalTable gt;
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
   int32_t* glist = nullptr;   // [gcap] giant vertices of a pass, class by class
@@ -248,22 +249,27 @@ louvain_status ensure_pool(louvain_handle h, Ctx& c, int64_t slots) {
   if (slots > ws.gt_slots_total) {
     free_all(ws.gt_alloc);
     ws.gt_slots_total = 0;
-    const int64_t total = slots + slots / 4 + 4096;
+    const int64_t total = (slots + slots / 4 + 4096 + 63) / 64 * 64;
     int32_t* k = nullptr;
     int32_t* v = nullptr;
-    if (!dalloc(h, ws.gt_alloc, &k, total) || !dalloc(h, ws.gt_alloc, &v, total)) {
+    unsigned* bits = nullptr;
+    if (!dalloc(h, ws.gt_alloc, &k, total) || !dalloc(h, ws.gt_alloc, &v, total) ||
+        !dalloc(h, ws.gt_alloc, &bits, total / 32)) {
       free_all(ws.gt_alloc);
       return set_err(h, LOUVAIN_ERR_OOM, "giant hash-table pool allocation failed");
     }
     cudaMemsetAsync(k, 0xFF, (size_t)total * 4, c.s);
     cudaMemsetAsync(v, 0, (size_t)total * 4, c.s);
+    cudaMemsetAsync(bits, 0, (size_t)(total / 32) * 4, c.s);
     ws.gt.keys = k;
     ws.gt.vals = v;
+    ws.gt_bits = bits;
     ws.gt_slots_total = total;
   }
   for (GiantPlan* gp : {&ws.gp, &ws.gpv}) {
     gp->keys = ws.gt.keys;
     gp->vals = ws.gt.vals;
+    gp->bits = ws.gt_bits;
     gp->pool_slots = ws.gt_slots_total;
   }
   return LOUVAIN_OK;

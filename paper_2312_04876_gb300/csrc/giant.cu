@@ -11,7 +11,7 @@
 //           iteration of a class only decides which of its giants are active (pruning flags);
 //   insert  grid-stride over chunks of 512 arcs (local move) or 2048 arcs (merge): K_i->c into the
 //           giant's global table with L2 atomics, K_i->d in registers (scanCommunities);
-//   scan    local move: one warp per range of 256 table slots (16-byte key loads) scores every
+//   scan    local move: one warp per range of 1024 table slots (one occupancy-bitmap word per lane) scores every
 //           candidate with the Eq. 2 numerator and keeps the range's best; merge: one warp per
 //           128-slot slice emits the slice's (community, weight) pairs into the holey row of the
 //           community.  Every occupied slot is cleared, so the pool is all-empty between uses;
@@ -28,7 +28,7 @@ constexpr int kChunk = 2048;    // arcs per chunk (merge, modularity, compaction
 constexpr int kLmChunk = 512;   // arcs per chunk of the local-moving phase (2 per thread)
 constexpr int kSliceLog = 7;    // merge: 128 table slots per slice, one 16-byte key load per lane
 constexpr int kSlice = 1 << kSliceLog;
-constexpr int kRangeLog = 8;    // local move: 256 table slots per warp range (2 key loads per lane)
+constexpr int kRangeLog = 10;   // local move: 1024 table slots (32 bitmap words) per warp range
 constexpr int kLocLog = 12;     // shared pre-aggregation table: 4096 slots >= 2 x kChunk keys
 
 // ---------------------------------------------------------------- plan
@@ -193,6 +193,28 @@ __global__ void k_glm_activate(GraphView<W> g, const int32_t* list, int64_t k0, 
 }
 
 // ---------------------------------------------------------------- local move: insert
+// tbl_add for a giant's table at pool offset `base` that also sets the slot's bit in the pool's
+// occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
+template <class V>
+__device__ __forceinline__ bool tbl_add_mark(int32_t* keys, V* vals, unsigned size, int shift, int32_t key, V w,
+                                             unsigned* bits, int64_t base) {
+  unsigned s = tbl_home(key, shift);
+  for (unsigned p = 0; p < size; p++) {
+    const int32_t k = *((volatile int32_t*)&keys[s]);
+    if (k == key) { atomicAdd(&vals[s], w); return true; }
+    if (k == kEmpty) {
+      const int32_t old = atomicCAS(&keys[s], kEmpty, key);
+      if (old == kEmpty) {
+        atomicOr(&bits[(base + s) >> 5], 1u << ((base + s) & 31));
+        atomicAdd(&vals[s], w);
+        return true;
+      }
+      if (old == key) { atomicAdd(&vals[s], w); return true; }
+    }
+    s = (s + 1) & (size - 1);
+  }
+  return false;
+}
 // One block per chunk of an active giant; each thread loads its U arcs before their C'[j] gathers
 // and table updates (U memory requests in flight per thread).
 template <class M>
@@ -232,7 +254,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
     for (int u = 0; u < U; u++) {
       if (jj[u] == i) continue;
       if (cc[u] == d) kid += ww[u];
-      else ok &= tbl_add(tk, tv, (unsigned)ts, 32 - lg, cc[u], ww[u]);
+      else ok &= tbl_add_mark(tk, tv, (unsigned)ts, 32 - lg, cc[u], ww[u], p.bits, off);
     }
     kid = group_sum<kBlock>(kid, red);
     if (threadIdx.x == 0 && kid != H(0)) atomicAdd(reinterpret_cast<H*>(p.kid) + k, kid);
@@ -241,9 +263,9 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
 }
 
 // ---------------------------------------------------------------- local move: range scan
-// One warp per range of 256 slots of an active giant's table: 2 steps of one 16-byte key load per
-// lane (tables are >= 64 slots and 64-slot aligned, so loads are aligned and never straddle two
-// tables); the Sigma gathers of a step are issued together.  Writes the range's best to part_s/c.
+// One warp per range of 1024 slots of an active giant's table: each lane reads one word of the
+// occupancy bitmap and visits only its occupied slots (key, value and Sigma loads of up to four
+// slots issued together), clearing slots and bits.  Writes the range's best to part_s/c.
 template <class M>
 __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_t k0, int64_t k1, const int32_t* Cp,
                                                      const typename M::a_t* K, const typename M::a_t* Sig,
@@ -268,34 +290,49 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
     const A two_m = gc ? (M::is_fp ? (A)gc[vg[i]].two_m_f : (A)gc[vg[i]].two_m_i) : two_m_all;
     int32_t* tk = p.keys + off;
     H* tv = reinterpret_cast<H*>(p.vals) + off;
+    // the range's bitmap words, one per lane (tables are >= 64 slots and 64-slot aligned)
     const int64_t sb = (q - p.slice_off[k]) << kRangeLog;
     const int64_t se = sb + (1 << kRangeLog) < ts ? sb + (1 << kRangeLog) : ts;
+    const int nwords = (int)((se - sb) >> 5);
+    unsigned* wp = p.bits + ((off + sb) >> 5) + lane;
+    unsigned word = lane < nwords ? *wp : 0u;
+    if (word) *wp = 0u;
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
-    for (int64_t s = sb + 4 * lane; s < se; s += 128) {
-      const int4 kk = *reinterpret_cast<const int4*>(tk + s);
-      if ((kk.x & kk.y & kk.z & kk.w) == kEmpty) continue;  // all four empty
-      const int32_t ks[4] = {kk.x, kk.y, kk.z, kk.w};
-      H vv[4];
-      A sg[4];
+    const int64_t s0 = sb + 32 * lane;
+    while (word) {
+      // up to 4 occupied slots at a time: their key, value and Sigma loads are issued together
+      int64_t ss[4];
+      int nb = 0;
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        vv[u] = H(0);
-        sg[u] = A(0);
-        if (ks[u] != kEmpty) {
-          vv[u] = tv[s + u];
-          sg[u] = Sig[ks[u]];
-          tk[s + u] = kEmpty;
-          tv[s + u] = H(0);
+        ss[u] = -1;
+        if (word) {
+          ss[u] = s0 + (__ffs(word) - 1);
+          word &= word - 1;
+          nb++;
         }
       }
+      int32_t ks[4];
+      H vv[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        if (ks[u] == kEmpty) continue;
+        ks[u] = ss[u] >= 0 ? tk[ss[u]] : kEmpty;
+        vv[u] = ss[u] >= 0 ? tv[ss[u]] : H(0);
+      }
+      A sg[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) sg[u] = ks[u] != kEmpty ? Sig[ks[u]] : A(0);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        if (ss[u] < 0) continue;
+        tk[ss[u]] = kEmpty;
+        tv[ss[u]] = H(0);
         cand++;
         const S sc = M::score(vv[u], kid, ki, sg[u], sd, two_m);
         if (better(sc, ks[u], best, bc)) { best = sc; bc = ks[u]; }
       }
+      (void)nb;
     }
     group_argmax<32>(best, bc, (S*)nullptr, (int32_t*)nullptr);
     if (lane == 0) {

@@ -196,6 +196,7 @@ struct GiantPlan {
   int64_t chunk_cap = 0, slice_cap = 0;
   int32_t* keys = nullptr;       // shared table pool, all kEmpty between uses
   void* vals = nullptr;          // (h_t), all zero between uses
+  unsigned* bits = nullptr;      // occupancy bitmap of the pool (local move), all zero between uses
   int64_t pool_slots = 0;
 };
 // Plan of the local-moving phase over every giant vertex of a pass, list[0, m) ordered class by

@@ -11,10 +11,11 @@
 //           iteration of a class only decides which of its giants are active (pruning flags);
 //   insert  grid-stride over chunks of 512 arcs (local move) or 2048 arcs (merge): K_i->c into the
 //           giant's global table with L2 atomics, K_i->d in registers (scanCommunities);
-//   scan    local move: one warp per range of 1024 table slots (one occupancy-bitmap word per lane) scores every
-//           candidate with the Eq. 2 numerator and keeps the range's best; merge: one warp per
-//           128-slot slice emits the slice's (community, weight) pairs into the holey row of the
-//           community.  Every occupied slot is cleared, so the pool is all-empty between uses;
+//   scan    one warp per range of 1024 table slots, one word of the pool's occupancy bitmap per
+//           lane (an insert that claims a slot sets its bit), so only occupied slots are read:
+//           local move scores every candidate with the Eq. 2 numerator and keeps the range's best;
+//           merge emits the range's (community, weight) pairs into the holey row of the community.
+//           Every occupied slot and bit is cleared, so the pool is all-empty between uses;
 //   decide  (local move) per giant: best over its ranges, then the move exactly as the per-vertex
 //           kernels make it;
 //   mark    (local move, pruning) grid-stride over chunks of the giants that moved.
@@ -26,8 +27,7 @@ namespace lv {
 
 constexpr int kChunk = 2048;    // arcs per chunk (merge, modularity, compaction)
 constexpr int kLmChunk = 512;   // arcs per chunk of the local-moving phase (2 per thread)
-constexpr int kSliceLog = 7;    // merge: 128 table slots per slice, one 16-byte key load per lane
-constexpr int kSlice = 1 << kSliceLog;
+constexpr int kSliceLog = 10;   // merge: 1024 table slots (32 bitmap words) per slice
 constexpr int kRangeLog = 10;   // local move: 1024 table slots (32 bitmap words) per warp range
 constexpr int kLocLog = 12;     // shared pre-aggregation table: 4096 slots >= 2 x kChunk keys
 
@@ -129,6 +129,29 @@ void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t*
   c.launches += 3;
 }
 
+// tbl_add for a giant's table at pool offset `base` that also sets the slot's bit in the pool's
+// occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
+template <class V>
+__device__ __forceinline__ bool tbl_add_mark(int32_t* keys, V* vals, unsigned size, int shift, int32_t key, V w,
+                                             unsigned* bits, int64_t base) {
+  unsigned s = tbl_home(key, shift);
+  for (unsigned p = 0; p < size; p++) {
+    const int32_t k = *((volatile int32_t*)&keys[s]);
+    if (k == key) { atomicAdd(&vals[s], w); return true; }
+    if (k == kEmpty) {
+      const int32_t old = atomicCAS(&keys[s], kEmpty, key);
+      if (old == kEmpty) {
+        atomicOr(&bits[(base + s) >> 5], 1u << ((base + s) & 31));
+        atomicAdd(&vals[s], w);
+        return true;
+      }
+      if (old == key) { atomicAdd(&vals[s], w); return true; }
+    }
+    s = (s + 1) & (size - 1);
+  }
+  return false;
+}
+
 // ---------------------------------------------------------------- shared pre-aggregation
 // Sums a chunk's (key, weight) pairs in the block's shared table, then flushes each distinct key
 // once into the global table (tk, tv, size 2^lg).  Every thread of the block must call both.
@@ -144,13 +167,14 @@ __device__ __forceinline__ void local_clear(LocalAgg<H>& la) {
 }
 
 template <class H>
-__device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* tk, H* tv, unsigned size, int lg) {
+__device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* tk, H* tv, unsigned size, int lg, unsigned* bits,
+                                            int64_t base) {
   bool ok = true;
   __syncthreads();
   for (int s = threadIdx.x; s < (1 << kLocLog); s += kBlock) {
     const int32_t key = la.keys[s];
     if (key != kEmpty) {
-      ok &= tbl_add(tk, tv, size, 32 - lg, key, la.vals[s]);
+      ok &= tbl_add_mark(tk, tv, size, 32 - lg, key, la.vals[s], bits, base);
       la.keys[s] = kEmpty;
       la.vals[s] = H(0);
     }
@@ -193,28 +217,7 @@ __global__ void k_glm_activate(GraphView<W> g, const int32_t* list, int64_t k0, 
 }
 
 // ---------------------------------------------------------------- local move: insert
-// tbl_add for a giant's table at pool offset `base` that also sets the slot's bit in the pool's
-// occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
-template <class V>
-__device__ __forceinline__ bool tbl_add_mark(int32_t* keys, V* vals, unsigned size, int shift, int32_t key, V w,
-                                             unsigned* bits, int64_t base) {
-  unsigned s = tbl_home(key, shift);
-  for (unsigned p = 0; p < size; p++) {
-    const int32_t k = *((volatile int32_t*)&keys[s]);
-    if (k == key) { atomicAdd(&vals[s], w); return true; }
-    if (k == kEmpty) {
-      const int32_t old = atomicCAS(&keys[s], kEmpty, key);
-      if (old == kEmpty) {
-        atomicOr(&bits[(base + s) >> 5], 1u << ((base + s) & 31));
-        atomicAdd(&vals[s], w);
-        return true;
-      }
-      if (old == key) { atomicAdd(&vals[s], w); return true; }
-    }
-    s = (s + 1) & (size - 1);
-  }
-  return false;
-}
+
 // One block per chunk of an active giant; each thread loads its U arcs before their C'[j] gathers
 // and table updates (U memory requests in flight per thread).
 template <class M>
@@ -493,7 +496,8 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_insert(GraphView<typename M
     while ((1u << lg) < ts) lg++;
     int32_t* tk = p.keys + off;
     H* tv = reinterpret_cast<H*>(p.vals) + off;
-    for (int64_t e = g.rbeg[i] + lane; e < g.rend[i]; e += G) ok &= tbl_add(tk, tv, ts, 32 - lg, Cp[g.tg[e]], (H)g.w[e]);
+    for (int64_t e = g.rbeg[i] + lane; e < g.rend[i]; e += G)
+      ok &= tbl_add_mark(tk, tv, ts, 32 - lg, Cp[g.tg[e]], (H)g.w[e], p.bits, off);
   }
   if (!ok) atomicOr(&ctrl->error, kErrTableFull);
 }
@@ -522,13 +526,14 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_insert_chunks(GraphView<typ
       ok &= tbl_add(la.keys, la.vals, 1u << kLocLog, 32 - kLocLog, Cp[g.tg[e]], (H)g.w[e]);
     int lg = 0;
     while ((1u << lg) < ts) lg++;
-    ok &= local_flush(la, p.keys + off, reinterpret_cast<H*>(p.vals) + off, ts, lg);
+    ok &= local_flush(la, p.keys + off, reinterpret_cast<H*>(p.vals) + off, ts, lg, p.bits, off);
   }
   if (!ok) atomicOr(&ctrl->error, kErrTableFull);
 }
 
-// Emits the occupied slots of every slice into the holey row of its community; hend[c] starts at
-// hoff[c] and is advanced atomically (one atomic per warp and 16-byte key group).
+// Emits the occupied slots of every slice into the holey row of its community: one warp per slice
+// of 1024 slots, one occupancy-bitmap word per lane, a warp prefix of the words' populations and
+// one atomic per warp on hend[c] (hend starts at hoff[c]).  Slots and bits are cleared.
 template <class M>
 __global__ void __launch_bounds__(kBlock) k_giant_mg_emit(const int32_t* list, int64_t m, int64_t* hend,
                                                           int32_t* otg, typename M::w_t* ow, GiantPlan p, Ctrl* ctrl) {
@@ -543,38 +548,36 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_emit(const int32_t* list, i
     const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
     int32_t* tk = p.keys + off;
     H* tv = reinterpret_cast<H*>(p.vals) + off;
-    {  // one warp per 128-slot slice, one 16-byte key load per lane
-      const int64_t s = (q - p.slice_off[k]) * kSlice + 4 * lane;
-      int4 kk = make_int4(kEmpty, kEmpty, kEmpty, kEmpty);
-      if (s < ts) kk = *reinterpret_cast<const int4*>(tk + s);
-      const int32_t ks[4] = {kk.x, kk.y, kk.z, kk.w};
-      int cnt = 0;
+    const int64_t sb = (q - p.slice_off[k]) << kSliceLog;
+    const int64_t se = sb + (1 << kSliceLog) < ts ? sb + (1 << kSliceLog) : ts;
+    const int nwords = (int)((se - sb) >> 5);
+    unsigned* wp = p.bits + ((off + sb) >> 5) + lane;
+    unsigned word = lane < nwords ? *wp : 0u;
+    const int cnt = __popc(word);
+    int incl = cnt;
 #pragma unroll
-      for (int u = 0; u < 4; u++) cnt += ks[u] != kEmpty;
-      // warp prefix of the per-lane counts, one atomic per warp
-      int incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-      if (wtot == 0) continue;
-      unsigned long long base = 0;
-      if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned long long*>(&hend[c]), (unsigned long long)wtot);
-      base = __shfl_sync(0xffffffffu, base, 31);
-      int64_t pos = (int64_t)base + incl - cnt;
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        if (ks[u] == kEmpty) continue;
-        otg[pos] = ks[u];
-        ow[pos] = (typename M::w_t)tv[s + u];
-        tk[s + u] = kEmpty;
-        tv[s + u] = H(0);
-        pos++;
-      }
-      written += (unsigned long long)cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
+    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+    if (wtot == 0) continue;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned long long*>(&hend[c]), (unsigned long long)wtot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    int64_t pos = (int64_t)base + incl - cnt;
+    if (word) *wp = 0u;
+    const int64_t s0 = sb + 32 * lane;
+    while (word) {
+      const int64_t s = s0 + (__ffs(word) - 1);
+      word &= word - 1;
+      otg[pos] = tk[s];
+      ow[pos] = (typename M::w_t)tv[s];
+      tk[s] = kEmpty;
+      tv[s] = H(0);
+      pos++;
+    }
+    written += (unsigned long long)cnt;
   }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) written += __shfl_xor_sync(0xffffffffu, written, o);

@@ -195,7 +195,7 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
        dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.jbig, n1);
   ws.jused_cap = ac / 32 + n1 + 64;
   ok = ok && dalloc(h, d, &ws.jboff, n1 + 1) && dalloc(h, d, &ws.jused, ws.jused_cap) &&
-       dalloc(h, d, &ws.jbc, n1 + 64) && dalloc(h, d, &ws.jround, 1);
+       dalloc(h, d, &ws.jbc, n1 + 64) && dalloc(h, d, &ws.jround, 4);
   ok = ok && dalloc(h, d, &ws.flags, n1) && dalloc(h, d, &ws.dperm, n1) && dalloc(h, d, &ws.csz, n1);
   // giant plans: giant rows have > 4096 arcs, so there are at most A / 4097 of them; chunks of >= 512
   // arcs over their rows: <= gcap + A / 512; slices of >= 128 slots over tables of < 4 x the arcs:

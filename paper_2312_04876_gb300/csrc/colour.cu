@@ -92,17 +92,16 @@ __device__ __forceinline__ void jp_push(const JpArgs& a, int32_t v, uint64_t pv,
 }
 
 // One round, part 1: a warp per ready vertex takes the first free colour of its bitmap, then
-// pushes along its arcs (rows longer than kBigDeg go to the big list instead).
-__global__ void __launch_bounds__(kBlock) jp_round(JpArgs a) {
-  __shared__ unsigned long long done_blk;
-  __shared__ int32_t max_blk;
-  const unsigned long long r = *(volatile unsigned long long*)a.round;
+// pushes along its arcs (rows longer than kBigDeg go to the big list instead).  Every thread of
+// the block calls it.
+__device__ __forceinline__ void jp_round_body(const JpArgs& a, unsigned long long r, unsigned long long* done_blk,
+                                              int32_t* max_blk) {
   const int32_t* in = a.lists[r & 1];
   int32_t* out = a.lists[(r + 1) & 1];
   unsigned long long count = *(volatile unsigned long long*)&a.rcount[r];
   if (count == 0) return;
   if ((int64_t)count > a.list_cap) count = (unsigned long long)a.list_cap;
-  if (threadIdx.x == 0) { done_blk = 0; max_blk = 0; }
+  if (threadIdx.x == 0) { *done_blk = 0; *max_blk = 0; }
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicMax(&a.ctrl->cnt[6], r + 1);  // rounds with work
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -135,8 +134,8 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a) {
     const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
     if (lane == 0) {
       a.colour[v] = col;
-      atomicAdd(&done_blk, 1ULL);
-      atomicMax(&max_blk, col + 1);
+      atomicAdd(done_blk, 1ULL);
+      atomicMax(max_blk, col + 1);
       if (end - beg > kBigDeg) {
         const unsigned long long pos = atomicAdd(&a.bcount[r], 1ULL);
         if ((int64_t)pos < a.list_cap) a.big[pos] = v;
@@ -148,15 +147,20 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a) {
     for (int64_t e = beg + lane; e < end; e += 32) jp_push(a, v, pv, col, a.g.tg[e], out, &a.rcount[r + 1]);
   }
   __syncthreads();
-  if (threadIdx.x == 0 && done_blk) {
-    atomicAdd(&a.ctrl->cnt[3], done_blk);
-    atomicMax(reinterpret_cast<unsigned long long*>(&a.ctrl->cnt[4]), (unsigned long long)max_blk);
+  if (threadIdx.x == 0 && *done_blk) {
+    atomicAdd(&a.ctrl->cnt[3], *done_blk);
+    atomicMax(reinterpret_cast<unsigned long long*>(&a.ctrl->cnt[4]), (unsigned long long)*max_blk);
   }
 }
 
+__global__ void __launch_bounds__(kBlock) jp_round(JpArgs a) {
+  __shared__ unsigned long long done_blk;
+  __shared__ int32_t max_blk;
+  jp_round_body(a, *(volatile unsigned long long*)a.round, &done_blk, &max_blk);
+}
+
 // One round, part 2: the pushes of the big vertices, every arc of every one spread over the grid.
-__global__ void __launch_bounds__(kBlock) jp_round_big(JpArgs a) {
-  const unsigned long long r = *(volatile unsigned long long*)a.round;
+__device__ __forceinline__ void jp_big_body(const JpArgs& a, unsigned long long r) {
   unsigned long long nb = *(volatile unsigned long long*)&a.bcount[r];
   if (nb == 0) return;
   if ((int64_t)nb > a.list_cap) nb = (unsigned long long)a.list_cap;
@@ -169,6 +173,62 @@ __global__ void __launch_bounds__(kBlock) jp_round_big(JpArgs a) {
     const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
     for (int64_t e = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < end; e += stride)
       jp_push(a, v, pv, col, a.g.tg[e], out, &a.rcount[r + 1]);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) jp_round_big(JpArgs a) { jp_big_body(a, *(volatile unsigned long long*)a.round); }
+
+// ---------------------------------------------------------------- persistent form
+// All rounds in one cooperative launch (every block resident): two grid barriers per round
+// instead of three kernel launches.  The barrier spins with a bound; a block that gives up sets
+// ctrl->error (kErrTimeout) and every block leaves at its next barrier, so the kernel always ends.
+constexpr long long kBarrierSpins = 1LL << 22;  // x ~64 ns sleep: about 0.3 s
+
+struct GridBar {
+  unsigned* count;
+  unsigned* gen;
+};
+
+// Returns false (on every block, at this or the next barrier) once any block has timed out.
+__device__ __forceinline__ bool grid_barrier(const GridBar& b, Ctrl* ctrl) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = *(volatile unsigned*)b.gen;
+    __threadfence();
+    if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
+      *(volatile unsigned*)b.count = 0u;
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*(volatile unsigned*)b.gen == g) {
+        if (++spins > kBarrierSpins || (*(volatile int32_t*)&ctrl->error & kErrTimeout)) {
+          atomicOr(&ctrl->error, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int32_t*)&ctrl->error & kErrTimeout) ok = 0;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(kBlock) jp_persistent(JpArgs a, GridBar bar, unsigned long long max_rounds) {
+  __shared__ unsigned long long done_blk;
+  __shared__ int32_t max_blk;
+  for (unsigned long long r = 0; r < max_rounds; r++) {
+    if (*(volatile unsigned long long*)&a.rcount[r] == 0) break;  // nothing ready: coloured (or stuck)
+    jp_round_body(a, r, &done_blk, &max_blk);
+    if (!grid_barrier(bar, a.ctrl)) return;
+    jp_big_body(a, r);
+    if (!grid_barrier(bar, a.ctrl)) return;
   }
 }
 
@@ -225,6 +285,33 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
     c.launches++;
   }
   if ((*err = cudaGetLastError()) != cudaSuccess) return -1;
+  // Preferred: every round in one cooperative launch (grid barriers between the parts)
+  {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jp_persistent, kBlock, 0) == cudaSuccess && per_sm > 0) {
+      GridBar bar{reinterpret_cast<unsigned*>(jb.round + 1), reinterpret_cast<unsigned*>(jb.round + 2)};
+      cudaMemsetAsync(jb.round + 1, 0, 2 * sizeof(unsigned long long), c.s);
+      unsigned long long mr = (unsigned long long)max_rounds;
+      void* args[] = {(void*)&a, (void*)&bar, (void*)&mr};
+      const int blocks = c.num_sms * (per_sm < 2 ? per_sm : 2);
+      if (cudaLaunchCooperativeKernel((const void*)jp_persistent, blocks, kBlock, args, 0, c.s) == cudaSuccess) {
+        c.launches++;
+        cudaMemcpyAsync(h_pinned, &ctrl->cnt[0], 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.s);
+        if ((*err = cudaStreamSynchronize(c.s)) != cudaSuccess) return -1;
+        if ((int64_t)h_pinned[3] != listed || h_pinned[7]) {
+          h_pinned[5] = (unsigned long long)listed;
+          h_pinned[6] = (unsigned long long)max_rounds;
+          return -1;
+        }
+        if (rounds_out) *rounds_out = (int64_t)h_pinned[6];
+        const int32_t ncol = (int32_t)h_pinned[4];
+        return ncol > 0 ? ncol : 1;
+      }
+      cudaGetLastError();  // not launchable cooperatively here: replayed rounds below
+    } else {
+      cudaGetLastError();
+    }
+  }
   // kRoundsPerGraph rounds (3 kernels each) captured once on a private stream, replayed on c.s
   cudaGraphExec_t exec = nullptr;
   {

@@ -136,7 +136,7 @@ struct JpBuffers {
   int64_t* boff;                // [n + 1] bitmap word offsets
   unsigned* used;               // [used_cap] colour bitmaps, ceil((deg + 1) / 32) words per vertex
   int64_t used_cap;             // >= A / 32 + n
-  unsigned long long* round;    // [1] current round
+  unsigned long long* round;    // [4] current round, grid-barrier counter and generation
   int64_t* tile_tmp;            // scan scratch
 };
 // Jones-Plassmann colouring of g (self-loops ignored).  Returns the number of colours.

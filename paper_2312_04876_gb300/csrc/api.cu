@@ -36,7 +36,10 @@ struct Workspace {
   int32_t *Cp = nullptr, *colour = nullptr, *csize = nullptr, *mv_from = nullptr, *mv_to = nullptr;
   int32_t *perm = nullptr, *cperm = nullptr, *occ = nullptr, *counts = nullptr, *cursor = nullptr;
   int32_t *cverts = nullptr, *jcnt = nullptr, *jl0 = nullptr, *jl1 = nullptr, *jbig = nullptr;
-  unsigned long long *jrc = nullptr, *jbc = nullptr, *jround = nullptr;
+  unsigned long long *jrc = nullptr, *jbc = nullptr, *jround = nullptr, *jcc = nullptr;
+  int64_t* jbcb = nullptr;
+  int32_t* jcown = nullptr;
+  int64_t jchunk_cap = 0;
   int64_t* jboff = nullptr;
   unsigned* jused = nullptr;
   int64_t jused_cap = 0;
@@ -194,6 +197,8 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
        dalloc(h, d, &ws.cursor, n1) && dalloc(h, d, &ws.cverts, n1) && dalloc(h, d, &ws.jcnt, n1) &&
        dalloc(h, d, &ws.jl0, n1) && dalloc(h, d, &ws.jl1, n1) && dalloc(h, d, &ws.jbig, n1);
   ws.jused_cap = ac / 32 + n1 + 64;
+  ws.jchunk_cap = ac / 256 + n1 + 64;
+  ok = ok && dalloc(h, d, &ws.jbcb, n1) && dalloc(h, d, &ws.jcown, ws.jchunk_cap) && dalloc(h, d, &ws.jcc, n1 + 64);
   ok = ok && dalloc(h, d, &ws.jboff, n1 + 1) && dalloc(h, d, &ws.jused, ws.jused_cap) &&
        dalloc(h, d, &ws.jbc, n1 + 64) && dalloc(h, d, &ws.jround, 4);
   ok = ok && dalloc(h, d, &ws.flags, n1) && dalloc(h, d, &ws.dperm, n1) && dalloc(h, d, &ws.csz, n1);
@@ -456,8 +461,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   int32_t ncol = 1;
   if (det) {
     GraphView<int32_t> gs{g.n, g.rbeg, g.rend, g.tg, nullptr};
-    JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1, ws.n_cap + 1, ws.jrc, ws.jbc, ws.jbig, ws.jboff, ws.jused, ws.jused_cap,
-                 ws.jround, ws.tile_tmp};
+    JpBuffers jb{ws.jcnt, ws.jl0, ws.jl1, ws.n_cap + 1, ws.jrc, ws.jbc, ws.jbig, ws.jbcb, ws.jcown, ws.jchunk_cap,
+                 ws.jcc, ws.jboff, ws.jused, ws.jused_cap, ws.jround, ws.tile_tmp};
     if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
     cudaError_t ce;
     const int pm = prof_begin(h, c);
@@ -1300,8 +1305,9 @@ louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const
   GraphView<int32_t> g{n, d_offsets, d_offsets + 1, d_targets, nullptr};
   int64_t hb[kNumBuckets + 1], gslots;
   if ((s = degree_buckets(h, c, g, hb, &gslots)) != LOUVAIN_OK) return s;
-  JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1, h->ws.n_cap + 1, h->ws.jrc, h->ws.jbc, h->ws.jbig, h->ws.jboff,
-               h->ws.jused, h->ws.jused_cap, h->ws.jround, h->ws.tile_tmp};
+  JpBuffers jb{h->ws.jcnt, h->ws.jl0, h->ws.jl1, h->ws.n_cap + 1, h->ws.jrc, h->ws.jbc, h->ws.jbig, h->ws.jbcb,
+               h->ws.jcown, h->ws.jchunk_cap, h->ws.jcc, h->ws.jboff, h->ws.jused, h->ws.jused_cap, h->ws.jround,
+               h->ws.tile_tmp};
   cudaError_t ce;
   int32_t nc = jp_colour(c, g, h->ws.dperm, hb, seed, pass, d_colour, jb, ctrl, h->pin, &ce);
   if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");

@@ -19,7 +19,8 @@
 
 namespace lv {
 
-constexpr int64_t kBigDeg = 1024;  // pushes of longer rows are spread over the grid
+constexpr int64_t kBigDeg = 32;    // pushes of longer rows are spread over the grid in chunks
+constexpr int64_t kPushChunk = kBlock;  // arcs per chunk (one per thread of a block)
 constexpr int kRoundsPerGraph = 16;
 
 struct JpArgs {
@@ -33,6 +34,10 @@ struct JpArgs {
   unsigned long long* rcount;   // rcount[r] = size of the ready list of round r (zeroed up front)
   unsigned long long* bcount;   // bcount[r] = vertices of round r whose push is spread (zeroed up front)
   int32_t* big;                 // those vertices
+  int64_t* big_cb;              // first push chunk of each of them
+  int32_t* cown;                // [chunk_cap] big-list entry of each push chunk of the round
+  int64_t chunk_cap;
+  unsigned long long* ccount;   // ccount[r] = push chunks of round r (zeroed up front)
   const int64_t* boff;          // [n + 1] first bitmap word of each vertex
   unsigned* used;               // the bitmaps (zeroed up front)
   unsigned long long* round;    // current round (device)
@@ -136,13 +141,27 @@ __device__ __forceinline__ void jp_round_body(const JpArgs& a, unsigned long lon
       a.colour[v] = col;
       atomicAdd(done_blk, 1ULL);
       atomicMax(max_blk, col + 1);
-      if (end - beg > kBigDeg) {
-        const unsigned long long pos = atomicAdd(&a.bcount[r], 1ULL);
-        if ((int64_t)pos < a.list_cap) a.big[pos] = v;
-        else atomicAdd(&a.ctrl->cnt[7], 1ULL);
-      }
     }
-    if (end - beg > kBigDeg) continue;
+    if (end - beg > kBigDeg) {
+      // spread the push: the vertex joins the big list and reserves its chunks of kPushChunk arcs
+      const int64_t nch = (end - beg + kPushChunk - 1) / kPushChunk;
+      unsigned long long pos = 0, cb = 0;
+      if (lane == 0) {
+        pos = atomicAdd(&a.bcount[r], 1ULL);
+        cb = atomicAdd(&a.ccount[r], (unsigned long long)nch);
+        if ((int64_t)pos < a.list_cap && (int64_t)(cb + nch) <= a.chunk_cap) {
+          a.big[pos] = v;
+          a.big_cb[pos] = (int64_t)cb;
+        } else {
+          atomicAdd(&a.ctrl->cnt[7], 1ULL);
+        }
+      }
+      pos = __shfl_sync(0xffffffffu, pos, 0);
+      cb = __shfl_sync(0xffffffffu, cb, 0);
+      if ((int64_t)pos < a.list_cap && (int64_t)(cb + nch) <= a.chunk_cap)
+        for (int64_t t = lane; t < nch; t += 32) a.cown[cb + t] = (int32_t)pos;
+      continue;
+    }
     const uint64_t pv = prio(a, v);
     for (int64_t e = beg + lane; e < end; e += 32) jp_push(a, v, pv, col, a.g.tg[e], out, &a.rcount[r + 1]);
   }
@@ -159,20 +178,20 @@ __global__ void __launch_bounds__(kBlock) jp_round(JpArgs a) {
   jp_round_body(a, *(volatile unsigned long long*)a.round, &done_blk, &max_blk);
 }
 
-// One round, part 2: the pushes of the big vertices, every arc of every one spread over the grid.
+// One round, part 2: the pushes of the big vertices, one block per chunk of kPushChunk arcs.
 __device__ __forceinline__ void jp_big_body(const JpArgs& a, unsigned long long r) {
-  unsigned long long nb = *(volatile unsigned long long*)&a.bcount[r];
-  if (nb == 0) return;
-  if ((int64_t)nb > a.list_cap) nb = (unsigned long long)a.list_cap;
+  unsigned long long nc = *(volatile unsigned long long*)&a.ccount[r];
+  if (nc == 0) return;
+  if ((int64_t)nc > a.chunk_cap) nc = (unsigned long long)a.chunk_cap;
   int32_t* out = a.lists[(r + 1) & 1];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (unsigned long long k = 0; k < nb; k++) {
-    const int32_t v = a.big[k];
-    const uint64_t pv = prio(a, v);
-    const int32_t col = a.colour[v];
-    const int64_t beg = a.g.rbeg[v], end = a.g.rend[v];
-    for (int64_t e = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < end; e += stride)
-      jp_push(a, v, pv, col, a.g.tg[e], out, &a.rcount[r + 1]);
+  unsigned long long nb = *(volatile unsigned long long*)&a.bcount[r];
+  if ((int64_t)nb > a.list_cap) nb = (unsigned long long)a.list_cap;
+  for (unsigned long long q = blockIdx.x; q < nc; q += gridDim.x) {
+    const int32_t pos = a.cown[q];
+    if (pos < 0 || (unsigned long long)pos >= nb) continue;  // defensive: every chunk is owned
+    const int32_t v = a.big[pos];
+    const int64_t e = a.g.rbeg[v] + ((int64_t)q - a.big_cb[pos]) * kPushChunk + threadIdx.x;
+    if (e < a.g.rend[v]) jp_push(a, v, prio(a, v), a.colour[v], a.g.tg[e], out, &a.rcount[r + 1]);
   }
 }
 
@@ -256,6 +275,7 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
   const size_t nrc = (size_t)(max_rounds + kRoundsPerGraph + 2);
   cudaMemsetAsync(jb.rcount, 0, nrc * sizeof(unsigned long long), c.s);
   cudaMemsetAsync(jb.bcount, 0, nrc * sizeof(unsigned long long), c.s);
+  cudaMemsetAsync(jb.ccount, 0, nrc * sizeof(unsigned long long), c.s);
   // bitmap offsets (scan of the word counts) and zeroed bitmaps
   if (g.n > 0) {
     jp_words<<<grid_for(g.n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(g, jb.boff);
@@ -268,7 +288,8 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
   JpArgs a;
   a.g = g; a.seed = seed; a.pass = pass; a.colour = colour; a.cnt = jb.cnt;
   a.lists[0] = jb.list0; a.lists[1] = jb.list1; a.list_cap = jb.list_cap; a.rcount = jb.rcount;
-  a.bcount = jb.bcount; a.big = jb.big; a.boff = jb.boff; a.used = jb.used; a.round = jb.round; a.ctrl = ctrl;
+  a.bcount = jb.bcount; a.big = jb.big; a.big_cb = jb.big_cb; a.cown = jb.cown; a.chunk_cap = jb.chunk_cap;
+  a.ccount = jb.ccount; a.boff = jb.boff; a.used = jb.used; a.round = jb.round; a.ctrl = ctrl;
   a.seg = seg;
   const int cap = c.num_sms * 16;
   for (int b = 0; b < kNumBuckets; b++) {

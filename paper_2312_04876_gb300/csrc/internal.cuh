@@ -133,6 +133,10 @@ struct JpBuffers {
   unsigned long long* rcount;   // [n + 64] per-round ready-list sizes
   unsigned long long* bcount;   // [n + 64] per-round counts of vertices whose push is spread
   int32_t* big;                 // [list_cap] those vertices
+  int64_t* big_cb;              // [list_cap] their first push chunk
+  int32_t* cown;                // [chunk_cap] big-list entry of each push chunk
+  int64_t chunk_cap;            // >= A / 256 + n
+  unsigned long long* ccount;   // [n + 64] per-round push-chunk counts
   int64_t* boff;                // [n + 1] bitmap word offsets
   unsigned* used;               // [used_cap] colour bitmaps, ceil((deg + 1) / 32) words per vertex
   int64_t used_cap;             // >= A / 32 + n

@@ -174,14 +174,38 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
     const A sd = a.st.Sig[d];
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
-    for (unsigned s0 = lane; s0 < size; s0 += (unsigned)G * U) {
+    unsigned scan_size = size;
+    if constexpr (G == 32) {
+      // Warp tables (up to 1024 slots): compact the occupied slots to the front of the table first
+      // (in place: an entry moves only to a slot already read), so the scoring loop below runs over
+      // the candidates only and its Sigma gathers are as few and as dense as possible.
+      unsigned ncand = 0;
+      for (unsigned s0 = 0; s0 < size; s0 += 32) {
+        const unsigned s = s0 + lane;
+        const int32_t key = s < size ? tk[s] : kEmpty;
+        const H val = key != kEmpty ? tv[s] : H(0);
+        __syncwarp();
+        if (key != kEmpty) { tk[s] = kEmpty; tv[s] = H(0); }
+        const unsigned ball = __ballot_sync(0xffffffffu, key != kEmpty);
+        __syncwarp();
+        if (key != kEmpty) {
+          const unsigned pos = ncand + __popc(ball & lanemask_lt());
+          tk[pos] = key;
+          tv[pos] = val;
+        }
+        ncand += __popc(ball);
+      }
+      __syncwarp();
+      scan_size = ncand;
+    }
+    for (unsigned s0 = lane; s0 < scan_size; s0 += (unsigned)G * U) {
       int32_t ck[U];
       H vv[U];
       A sg[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const unsigned s = s0 + (unsigned)u * G;
-        ck[u] = s < size ? tk[s] : kEmpty;
+        ck[u] = s < scan_size ? tk[s] : kEmpty;
         vv[u] = H(0);
         if (ck[u] != kEmpty) {
           vv[u] = tv[s];

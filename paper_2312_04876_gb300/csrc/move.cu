@@ -174,43 +174,52 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
     const A sd = a.st.Sig[d];
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
+    // Warp and block groups: each warp compacts the occupied slots of its own segment of the table
+    // (size / warps slots) to the segment's front, in place (an entry only moves to a slot already
+    // read), then scores just those candidates, U per lane with their Sigma gathers issued
+    // together; the segment is left all-empty.  Sub-warp groups scan their small tables directly.
+    constexpr unsigned kStride = G >= 32 ? 32u : (unsigned)G;
     unsigned scan_size = size;
-    if constexpr (G == 32) {
-      // Warp tables (up to 1024 slots): compact the occupied slots to the front of the table first
-      // (in place: an entry moves only to a slot already read), so the scoring loop below runs over
-      // the candidates only and its Sigma gathers are as few and as dense as possible.
+    int32_t* sk = tk;
+    H* sv = tv;
+    const unsigned slane = G >= 32 ? (threadIdx.x & 31u) : lane;
+    if constexpr (G >= 32) {
+      const unsigned seg = size / (unsigned)(G / 32);
+      const unsigned w = G == 32 ? 0u : (threadIdx.x >> 5);
+      sk = tk + w * seg;
+      sv = tv + w * seg;
       unsigned ncand = 0;
-      for (unsigned s0 = 0; s0 < size; s0 += 32) {
-        const unsigned s = s0 + lane;
-        const int32_t key = s < size ? tk[s] : kEmpty;
-        const H val = key != kEmpty ? tv[s] : H(0);
+      for (unsigned s0 = 0; s0 < seg; s0 += 32) {
+        const unsigned s = s0 + slane;
+        const int32_t key = s < seg ? sk[s] : kEmpty;
+        const H val = key != kEmpty ? sv[s] : H(0);
         __syncwarp();
-        if (key != kEmpty) { tk[s] = kEmpty; tv[s] = H(0); }
+        if (key != kEmpty) { sk[s] = kEmpty; sv[s] = H(0); }
         const unsigned ball = __ballot_sync(0xffffffffu, key != kEmpty);
         __syncwarp();
         if (key != kEmpty) {
           const unsigned pos = ncand + __popc(ball & lanemask_lt());
-          tk[pos] = key;
-          tv[pos] = val;
+          sk[pos] = key;
+          sv[pos] = val;
         }
         ncand += __popc(ball);
       }
       __syncwarp();
       scan_size = ncand;
     }
-    for (unsigned s0 = lane; s0 < scan_size; s0 += (unsigned)G * U) {
+    for (unsigned s0 = slane; s0 < scan_size; s0 += kStride * U) {
       int32_t ck[U];
       H vv[U];
       A sg[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const unsigned s = s0 + (unsigned)u * G;
-        ck[u] = s < scan_size ? tk[s] : kEmpty;
+        const unsigned s = s0 + (unsigned)u * kStride;
+        ck[u] = s < scan_size ? sk[s] : kEmpty;
         vv[u] = H(0);
         if (ck[u] != kEmpty) {
-          vv[u] = tv[s];
-          tk[s] = kEmpty;
-          tv[s] = H(0);
+          vv[u] = sv[s];
+          sk[s] = kEmpty;
+          sv[s] = H(0);
         }
       }
 #pragma unroll

@@ -114,19 +114,8 @@ __device__ __forceinline__ bool merge_members(const MergeArgs<M>& a, int64_t k0,
 #pragma unroll
       for (int u = 0; u < U; u++) cc[u] = ee[u] >= 0 ? a.Cp[jj[u]] : kEmpty;
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        if constexpr (W == 32 && !M::is_fp) {
-          // warp aggregation of equal communities before the shared-memory atomics (the trip
-          // count of this loop is uniform over the warp)
-          const bool ins = ee[u] >= 0;
-          const int32_t key = ins ? cc[u] : kEmpty;
-          const unsigned peers = __match_any_sync(0xffffffffu, key);
-          const unsigned tot = __reduce_add_sync(peers, ins ? (unsigned)ww[u] : 0u);
-          if (ins && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) ok &= tbl_add(tk, tv, size, shift, key, (H)tot);
-        } else {
-          if (ee[u] >= 0) ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
-        }
-      }
+      for (int u = 0; u < U; u++)
+        if (ee[u] >= 0) ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
     }
   }
   return ok;

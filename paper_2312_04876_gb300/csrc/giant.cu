@@ -255,20 +255,9 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
     H kid = H(0);
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const bool self = jj[u] == i;
-      if (!self && cc[u] == d) kid += ww[u];
-      const bool ins = !self && cc[u] != d;
-      if constexpr (!M::is_fp) {
-        // warp aggregation: lanes holding the same community add once (a hub's arcs concentrate on
-        // few communities, and same-address global atomics serialise in L2)
-        const int32_t key = ins ? cc[u] : kEmpty;
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const unsigned tot = __reduce_add_sync(peers, ins ? (unsigned)ww[u] : 0u);
-        if (ins && (__ffs(peers) - 1) == (int)(threadIdx.x & 31))
-          ok &= tbl_add_mark(tk, tv, (unsigned)ts, 32 - lg, key, (H)tot, p.bits, off);
-      } else {
-        if (ins) ok &= tbl_add_mark(tk, tv, (unsigned)ts, 32 - lg, cc[u], ww[u], p.bits, off);
-      }
+      if (jj[u] == i) continue;
+      if (cc[u] == d) kid += ww[u];
+      else ok &= tbl_add_mark(tk, tv, (unsigned)ts, 32 - lg, cc[u], ww[u], p.bits, off);
     }
     kid = group_sum<kBlock>(kid, red);
     if (threadIdx.x == 0 && kid != H(0)) atomicAdd(reinterpret_cast<H*>(p.kid) + k, kid);

@@ -145,10 +145,7 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
     // independent memory requests in flight.
     H kid = H(0);
     bool ok = true;
-    // the trip count is uniform over the group (every lane runs every step), so warp-wide
-    // collectives are legal inside the loop
-    for (int64_t b0 = beg; b0 < end; b0 += (int64_t)G * U) {
-      const int64_t e0 = b0 + lane;
+    for (int64_t e0 = beg + lane; e0 < end; e0 += (int64_t)G * U) {
       int32_t jj[U];
       H ww[U];
 #pragma unroll
@@ -162,19 +159,9 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
       for (int u = 0; u < U; u++) cc[u] = jj[u] != i ? a.st.Cp[jj[u]] : kEmpty;
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const bool self = jj[u] == i;  // padding or i's self-loop
-        if (!self && cc[u] == d) kid += ww[u];
-        const bool ins = !self && cc[u] != d;
-        if constexpr (G >= 32 && !M::is_fp) {
-          // warp aggregation: lanes holding the same community add once (shared-memory atomics
-          // on one address serialise, and R-MAT rows concentrate on few communities)
-          const int32_t key = ins ? cc[u] : kEmpty;
-          const unsigned peers = __match_any_sync(0xffffffffu, key);
-          const unsigned tot = __reduce_add_sync(peers, ins ? (unsigned)ww[u] : 0u);
-          if (ins && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) ok &= tbl_add(tk, tv, size, shift, key, (H)tot);
-        } else {
-          if (ins) ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
-        }
+        if (jj[u] == i) continue;  // padding or i's self-loop
+        if (cc[u] == d) kid += ww[u];
+        else ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
       }
     }
     if (!ok) atomicOr(&ctrl->error, kErrTableFull);

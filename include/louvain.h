@@ -83,7 +83,8 @@ typedef struct {
   int32_t lm_blocks_per_sm;      /* grid cap of the local-moving kernels in blocks per SM (0 = 16); the
                                     degree buckets of a class run concurrently, so smaller grids let
                                     them share the SMs */
-  int32_t reserved;
+  int32_t giant_min_degree;      /* rows longer than this take the multi-block giant path; 2048..4096
+                                    (0 = 4096: rows of 2049..4096 arcs use one block with a 64 KB table) */
 } louvain_params;
 
 typedef struct {
@@ -167,6 +168,25 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
                                  const int64_t* d_offsets, const int32_t* d_targets, const void* d_weights,
                                  louvain_wtype wtype, const louvain_params* p, void* stream, int32_t* d_membership,
                                  louvain_graph_result* results, louvain_result* res);
+
+/* Autotuning (a systems extension; the paper tunes nothing at run time).  Times full runs of the
+ * given graph (device time, best of `reps`) under every combination of the performance knobs that
+ * leave the arithmetic unchanged -- giant_min_degree in {4096, 2048} (which kernel takes rows of
+ * 2049..4096 arcs: the one-block 64 KB table or the multi-block giant path), lm_blocks_per_sm in
+ * {16, 4} and compact in {1, 0} -- and writes *p with the fastest combination into *tuned (other
+ * fields copied; *best_ms its time).  In deterministic mode every candidate returns the same
+ * membership; d_membership (device, n entries) receives the last run's.  Costs 8 x reps runs. */
+louvain_status louvain_autotune(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                const louvain_params* p, void* stream, int32_t* d_membership, int32_t reps,
+                                louvain_params* tuned, float* best_ms);
+
+/* louvain_autotune for a batch (the arguments of louvain_run_batch). */
+louvain_status louvain_autotune_batch(louvain_handle h, int32_t n_graphs, const int64_t* graph_vtx_offs,
+                                      int64_t n_arcs, const int64_t* d_offsets, const int32_t* d_targets,
+                                      const void* d_weights, louvain_wtype wtype, const louvain_params* p,
+                                      void* stream, int32_t* d_membership, int32_t reps, louvain_params* tuned,
+                                      float* best_ms);
 
 /* ---------------------------------------------------------------------------------------------
  * Serving: a continuous-batching request loop (a throughput extension; the paper has no

@@ -268,6 +268,40 @@ class Louvain:
         return membership, graphs, RunResult(res.modularity, res.passes, res.total_iterations, res.n_communities,
                                              res.ms_total, res.kernel_launches)
 
+    def autotune(self, offsets, targets, weights, params: Params | None = None, reps: int = 1, stream=None,
+                 **overrides):
+        """louvain_autotune: (tuned Params, best ms) for this graph."""
+        import torch
+        p = params if params is not None else default_params(**overrides)
+        n = offsets.numel() - 1
+        mem = torch.empty(max(n, 1), dtype=torch.int32, device=offsets.device)
+        out = Params()
+        ms = ctypes.c_float()
+        rc = self._lib.louvain_autotune(self._h, n, targets.numel(), offsets.data_ptr(), targets.data_ptr(),
+                                        weights.data_ptr(), _wtype(weights), ctypes.byref(p), _stream_ptr(stream),
+                                        mem.data_ptr(), reps, ctypes.byref(out), ctypes.byref(ms))
+        self._check(rc)
+        return out, float(ms.value)
+
+    def autotune_batch(self, graph_vtx_offs, offsets, targets, weights, params: Params | None = None, reps: int = 1,
+                       stream=None, **overrides):
+        """louvain_autotune_batch: (tuned Params, best ms) for this batch."""
+        import numpy as np
+        import torch
+        p = params if params is not None else default_params(**overrides)
+        vo = np.ascontiguousarray(np.asarray(graph_vtx_offs, dtype=np.int64))
+        n = int(vo[-1])
+        mem = torch.empty(max(n, 1), dtype=torch.int32, device=offsets.device)
+        out = Params()
+        ms = ctypes.c_float()
+        rc = self._lib.louvain_autotune_batch(self._h, len(vo) - 1, vo.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                              targets.numel(), offsets.data_ptr(), targets.data_ptr(),
+                                              weights.data_ptr(), _wtype(weights), ctypes.byref(p),
+                                              _stream_ptr(stream), mem.data_ptr(), reps, ctypes.byref(out),
+                                              ctypes.byref(ms))
+        self._check(rc)
+        return out, float(ms.value)
+
     # ---------------------------------------------------------------- steps
     def modularity(self, offsets, targets, weights, membership, stream=None) -> float:
         q = ctypes.c_double()

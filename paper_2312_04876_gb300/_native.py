@@ -19,7 +19,7 @@ class Params(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("seed", ctypes.c_uint64), ("validate", ctypes.c_int32),
                 ("compact", ctypes.c_int32), ("pass_modularity", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("fast_classes", ctypes.c_int32), ("fast_giant_class", ctypes.c_int32),
-                ("lm_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lm_blocks_per_sm", ctypes.c_int32), ("giant_min_degree", ctypes.c_int32)]
 
 
 class PassStats(ctypes.Structure):
@@ -79,6 +79,10 @@ SIGNATURES = {
     "louvain_serve_submit": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, _V, ctypes.POINTER(ctypes.c_uint64)]),
     "louvain_serve_poll": (_I32, [_V, ctypes.c_uint64, _I32, ctypes.POINTER(ServeResult)]),
     "louvain_serve_destroy": (None, [_V]),
+    "louvain_autotune": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V, _V, _I32,
+                                ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_float)]),
+    "louvain_autotune_batch": (_I32, [_V, _I32, ctypes.POINTER(_I64), _I64, _V, _V, _V, _I32, ctypes.POINTER(Params),
+                                      _V, _V, _I32, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_float)]),
     "louvain_run_batch": (_I32, [_V, _I32, ctypes.POINTER(_I64), _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V,
                                  _V, ctypes.POINTER(GraphResult), ctypes.POINTER(Result)]),
 }

@@ -371,6 +371,7 @@ bool valid_params(const louvain_params* p) {
   return p && p->max_passes >= 0 && p->max_iterations >= 0 && p->tolerance >= 0.0 && p->tolerance_drop > 0.0 &&
          p->aggregation_tolerance >= 0.0 && p->fast_classes >= 0 && p->fast_classes <= 4096 &&
          p->lm_blocks_per_sm >= 0 && p->lm_blocks_per_sm <= 64 &&
+         (p->giant_min_degree == 0 || (p->giant_min_degree >= 2048 && p->giant_min_degree <= 4096)) &&
          (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
 }
 
@@ -939,6 +940,41 @@ louvain_status check_graph_args(louvain_handle h, int64_t n, int64_t n_arcs, con
 
 }  // namespace
 
+// ------------------------------------------------------------------ autotuning
+// Candidates of the performance knobs that leave the arithmetic unchanged: the giant-row
+// threshold (which kernel takes rows of 2049..4096 arcs), the local-move grid cap and super-graph
+// compaction.  Each is timed by full runs (device time, best of `reps`); the fastest wins.
+template <class RunFn>
+static louvain_status autotune_impl(louvain_handle h, const louvain_params* p, int32_t reps, RunFn run,
+                                    louvain_params* tuned, float* best_ms) {
+  static const int32_t kGiant[] = {4096, 2048};
+  static const int32_t kGrid[] = {16, 4};
+  static const int32_t kCompact[] = {1, 0};
+  louvain_params best = *p;
+  float best_t = -1.f;
+  for (int32_t gm : kGiant)
+    for (int32_t gr : kGrid)
+      for (int32_t cp : kCompact) {
+        louvain_params q = *p;
+        q.giant_min_degree = gm;
+        q.lm_blocks_per_sm = gr;
+        q.compact = cp;
+        q.profile = 0;
+        float t = -1.f;
+        for (int32_t r = 0; r < (reps > 0 ? reps : 1); r++) {
+          float ms = 0.f;
+          louvain_status s = run(q, &ms);
+          if (s != LOUVAIN_OK) return s;
+          if (t < 0.f || ms < t) t = ms;
+        }
+        if (best_t < 0.f || t < best_t) { best_t = t; best = q; }
+      }
+  best.profile = p->profile;
+  *tuned = best;
+  if (best_ms) *best_ms = best_t;
+  return LOUVAIN_OK;
+}
+
 // ------------------------------------------------------------------ hooks of the serving runtime
 namespace lv {
 size_t handle_device_bytes(louvain_handle h) { return h ? total_bytes(h->ws) : 0; }
@@ -1066,6 +1102,7 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
   Ctx c;
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
+  if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
   h->prof.on = p->profile != 0;
   h->prof.used = 0;
   h->prof.recs.clear();
@@ -1155,6 +1192,7 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
   Ctx c;
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
+  if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
   if (res) std::memset(res, 0, sizeof(*res));
   if (n_stats) *n_stats = 0;
   h->prof.on = p->profile != 0;
@@ -1329,6 +1367,7 @@ louvain_status louvain_local_move(louvain_handle h, int64_t n, int64_t n_arcs, c
   Ctx c;
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
+  if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
   if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
   if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
   const bool fp = wtype == LOUVAIN_W_FP32;
@@ -1431,6 +1470,37 @@ louvain_status louvain_kernel_profile(louvain_handle h, louvain_kernel_stat* out
   }
   *n = k;
   return LOUVAIN_OK;
+}
+
+louvain_status louvain_autotune(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                const louvain_params* p, void* stream, int32_t* d_membership, int32_t reps,
+                                louvain_params* tuned, float* best_ms) {
+  if (!h || !p || !tuned) return LOUVAIN_ERR_INVALID;
+  if (!valid_params(p)) return set_err(h, LOUVAIN_ERR_INVALID, "invalid louvain_params");
+  return autotune_impl(h, p, reps, [&](const louvain_params& q, float* ms) {
+    louvain_result r;
+    louvain_status s = louvain_run(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype, &q, stream, d_membership, &r,
+                                   nullptr, 0, nullptr);
+    *ms = r.ms_total;
+    return s;
+  }, tuned, best_ms);
+}
+
+louvain_status louvain_autotune_batch(louvain_handle h, int32_t n_graphs, const int64_t* graph_vtx_offs,
+                                      int64_t n_arcs, const int64_t* d_offsets, const int32_t* d_targets,
+                                      const void* d_weights, louvain_wtype wtype, const louvain_params* p,
+                                      void* stream, int32_t* d_membership, int32_t reps, louvain_params* tuned,
+                                      float* best_ms) {
+  if (!h || !p || !tuned) return LOUVAIN_ERR_INVALID;
+  if (!valid_params(p)) return set_err(h, LOUVAIN_ERR_INVALID, "invalid louvain_params");
+  return autotune_impl(h, p, reps, [&](const louvain_params& q, float* ms) {
+    louvain_result r;
+    louvain_status s = louvain_run_batch(h, n_graphs, graph_vtx_offs, n_arcs, d_offsets, d_targets, d_weights, wtype,
+                                         &q, stream, d_membership, nullptr, &r);
+    *ms = r.ms_total;
+    return s;
+  }, tuned, best_ms);
 }
 
 louvain_status louvain_exclusive_scan(louvain_handle h, const int64_t* d_in, int64_t* d_out, int64_t count,

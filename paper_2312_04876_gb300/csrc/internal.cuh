@@ -14,6 +14,7 @@ struct Ctx {
   int64_t launches = 0;
   int num_sms = 152;
   int lm_blocks_per_sm = 16;  // grid cap of the local-moving kernels (blocks per SM)
+  int64_t giant_min = 4096;   // rows longer than this take the giant path (2048..4096)
 };
 
 inline int grid_for(int64_t work_items, int items_per_block, int cap) {
@@ -53,6 +54,7 @@ struct KeyDesc {
   uint64_t seed = 0;
   Segs seg;  // kind 3 hashes the graph-local id
   int giant_class = -1;  // kind 3: >= 0 puts every giant row in this class
+  int64_t giant_min = 4096;  // rows longer than this are giant (set by bucket_sort from the Ctx)
 };
 
 // Counting sort of vertex ids by key.  key_kind 0: degree bucket of (rend - rbeg); 1: colour *

@@ -126,10 +126,18 @@ void iota_i32(Ctx& c, int32_t* p, int64_t n) {
 }
 
 // ---------------------------------------------------------------- counting sort by key
+// Degree bucket with the run's giant threshold: rows of 2049..4096 arcs go to the 8192-slot block
+// kernel, or to the giant path when the threshold is lower.
+__device__ __forceinline__ int bucket_of(int64_t deg, int64_t giant_min) {
+  int b = degree_bucket(deg);
+  if (b == kNumBuckets - 2 && deg > giant_min) b = kNumBuckets - 1;
+  return b;
+}
+
 __device__ __forceinline__ int sort_key(KeyDesc kd, int64_t i, const int64_t* rbeg, const int64_t* rend,
                                         const int32_t* colour, const int64_t* deg64) {
-  if (kd.kind == 2) return degree_bucket(deg64[i]);
-  int b = degree_bucket(rend[i] - rbeg[i]);
+  if (kd.kind == 2) return bucket_of(deg64[i], kd.giant_min);
+  int b = bucket_of(rend[i] - rbeg[i], kd.giant_min);
   if (kd.kind == 0 || b < 0) return b;
   if (kd.kind == 3) {  // hash class of the fast schedule; giant rows optionally all in one class
     const uint64_t h = kd.giant_class >= 0 && b == kNumBuckets - 1
@@ -158,7 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(KeyDesc kind, int64_t n, co
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const long long dg = kind.kind == 2 ? deg64[i] : rend[i] - rbeg[i];
     mx = dg > mx ? dg : mx;
-    if (giant_slots && degree_bucket(dg) == kNumBuckets - 1)
+    if (giant_slots && bucket_of(dg, kind.giant_min) == kNumBuckets - 1)
       gs += 1ULL << tbl_log2(dg < n_bound ? dg : n_bound, 6, 31);
     int k = sort_key(kind, i, rbeg, rend, colour, deg64);
     if (k < 0) continue;
@@ -232,6 +240,7 @@ void bucket_sort(Ctx& c, KeyDesc key_kind, int64_t n, const int64_t* rbeg, const
                  const int64_t* deg64, int64_t nkeys, int32_t* perm, int64_t* offsets, int32_t* cursor,
                  int64_t* tile_tmp, unsigned long long* max_deg, unsigned long long* giant_slots,
                  int64_t n_bound) {
+  key_kind.giant_min = c.giant_min;
   cudaMemsetAsync(offsets, 0, (size_t)(nkeys + 1) * sizeof(int64_t), c.s);
   cudaMemsetAsync(cursor, 0, (size_t)nkeys * sizeof(int32_t), c.s);
   if (n <= 0) return;

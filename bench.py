@@ -394,6 +394,9 @@ def main():
     ap.add_argument("--fast-giant-class", type=int, default=None,
                     help="fast mode: 1 puts every giant row of a pass in one class")
     ap.add_argument("--lm-blocks-per-sm", type=int, default=None, help="grid cap of the local-moving kernels")
+    ap.add_argument("--giant-min-degree", type=int, default=None, help="rows longer than this take the giant path")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: pick the exact-arithmetic performance knobs with louvain_autotune before warm-up")
     ap.add_argument("--ncu-window", action="store_true",
                     help="after warm-up run ONE step between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints no bench line")
@@ -432,7 +435,13 @@ def main():
         knobs["fast_giant_class"] = args.fast_giant_class
     if args.lm_blocks_per_sm is not None:
         knobs["lm_blocks_per_sm"] = args.lm_blocks_per_sm
+    if args.giant_min_degree is not None:
+        knobs["giant_min_degree"] = args.giant_min_degree
     params = lv.default_params(mode=args.mode, validate=0, **knobs)
+    tuned_ms = None
+    if args.autotune and not knobs:
+        # untimed: the knobs it picks leave the arithmetic unchanged (see louvain_autotune)
+        params, tuned_ms = L.autotune(offs, tg, w, params, reps=1)
     mem = torch.empty(g.n, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -497,6 +506,8 @@ def main():
     # per-kernel device time (CUDA events around every launch on the run's stream) and algorithmic
     # bytes (device counters), from a profiled repeat of the timed steps
     pparams = lv.default_params(mode=args.mode, validate=0, profile=1, **knobs)
+    for f in ("giant_min_degree", "lm_blocks_per_sm", "compact"):
+        setattr(pparams, f, getattr(params, f))
     agg = {}
     for _ in range(args.steps):
         L.run(offs, tg, w, pparams, membership=mem)
@@ -526,6 +537,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "n": g.n, "arcs": g.n_arcs, "mode": args.mode,
+                   "knobs": {"giant_min_degree": params.giant_min_degree, "lm_blocks_per_sm": params.lm_blocks_per_sm,
+                             "compact": params.compact, "fast_classes": params.fast_classes,
+                             "autotuned": tuned_ms is not None},
                    "parallelism": "replicas" if ws > 1 else "single", "l2": "inputs larger than L2 "
                    f"(CSR {(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes) / 1e9:.2f} GB vs 0.13 GB L2)"},
         "modularity": last.modularity, "oracle_match": oracle_match(args.workload, args.mode, last.modularity, msha),

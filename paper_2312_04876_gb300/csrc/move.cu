@@ -72,7 +72,7 @@ __device__ __forceinline__ void flush_move_acc(Ctrl* ctrl, unsigned long long lo
 }
 
 template <class M, int G, int LOG, bool GLOBAL>
-__global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
+__global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M> a) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
@@ -134,6 +134,10 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
     }
     const int64_t deg = end - beg;
     if (lane == 0) { ctr[1]++; ctr[2] += (unsigned long long)deg; }
+    // K_i and Sigma_d are needed only for scoring; loaded here they overlap the arc loads (in the
+    // deterministic schedule Sigma does not change during a class; the fast schedule reads live values)
+    const A ki = a.st.K[i];
+    const A sd = a.st.Sig[d];
     int lg;
     if (GLOBAL) lg = tbl_log2(deg < n_cur ? deg : n_cur, 6, a.glog);
     else lg = tbl_log2(deg, 1, LOG);
@@ -170,8 +174,6 @@ __global__ void __launch_bounds__(kBlock) lm_kernel(LmArgs<M> a) {
 
     // best community by the Eq. 2 numerator; the scan also clears the table.  The Sigma gathers of
     // U slots per lane are issued together.
-    const A ki = a.st.K[i];
-    const A sd = a.st.Sig[d];
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
     // Warp and block groups: each warp compacts the occupied slots of its own segment of the table

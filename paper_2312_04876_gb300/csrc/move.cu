@@ -71,6 +71,13 @@ __device__ __forceinline__ void flush_move_acc(Ctrl* ctrl, unsigned long long lo
   }
 }
 
+// Threads per block: warps with 1024-slot tables run in two-warp blocks, so a block (and its
+// shared memory) retires after two vertices instead of waiting for the slowest of eight.
+template <int G, int LOG>
+__host__ __device__ constexpr int lm_block() {
+  return (G == 32 && LOG >= 10) ? 64 : kBlock;
+}
+
 template <class M, int G, int LOG, bool GLOBAL>
 __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M> a) {
   typedef typename M::h_t H;
@@ -78,7 +85,8 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
   typedef typename M::s_t S;
   Ctrl* ctrl = a.st.ctrl;
   if (*(volatile int32_t*)&ctrl->done) return;
-  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  constexpr int BS = lm_block<G, LOG>();
+  constexpr int GPB = G <= 32 ? BS / G : 1;
   constexpr int SL = GLOBAL ? 1 : (1 << LOG);
   constexpr int U = G >= 32 ? 4 : 2;  // arcs (and table slots) per lane per step
   extern __shared__ __align__(16) unsigned char lm_dyn[];  // GPB tables of SL (key, value) slots
@@ -99,7 +107,7 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
     tk = a.gkeys + (int64_t)blockIdx.x * a.gslots;
     tv = a.gvals + (int64_t)blockIdx.x * a.gslots;
   } else {
-    for (int t = threadIdx.x; t < GPB * SL; t += kBlock) { skeys[t] = kEmpty; svals[t] = H(0); }
+    for (int t = threadIdx.x; t < GPB * SL; t += BS) { skeys[t] = kEmpty; svals[t] = H(0); }
     __syncthreads();
     tk = skeys + gib * SL;
     tv = svals + gib * SL;
@@ -290,7 +298,8 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
 
 template <class M, int G, int LOG, bool GLOBAL>
 static constexpr size_t lm_smem() {
-  return (size_t)(G <= 32 ? kBlock / G : 1) * (GLOBAL ? 1 : (1 << LOG)) * (sizeof(int32_t) + sizeof(typename M::h_t));
+  return (size_t)(G <= 32 ? lm_block<G, LOG>() / G : 1) * (GLOBAL ? 1 : (1 << LOG)) *
+         (sizeof(int32_t) + sizeof(typename M::h_t));
 }
 
 // Opts a kernel into more than 48 KB of dynamic shared memory, once per device (outside any graph
@@ -316,11 +325,12 @@ void move_prepare() {
 
 template <class M, int G, int LOG, bool GLOBAL>
 static void launch_lm(Ctx& c, const LmArgs<M>& a, int max_blocks) {
-  constexpr int GPB = G <= 32 ? kBlock / G : 1;
+  constexpr int BS = lm_block<G, LOG>();
+  constexpr int GPB = G <= 32 ? BS / G : 1;
   constexpr size_t smem = lm_smem<M, G, LOG, GLOBAL>();
   lm_attr<M, G, LOG, GLOBAL>();
-  int grid = grid_for(a.count, GPB, max_blocks);
-  lm_kernel<M, G, LOG, GLOBAL><<<grid, kBlock, smem, c.s>>>(a);
+  int grid = grid_for(a.count, GPB, max_blocks * (kBlock / BS));
+  lm_kernel<M, G, LOG, GLOBAL><<<grid, BS, smem, c.s>>>(a);
   c.launches++;
 }
 

@@ -390,6 +390,8 @@ def main():
     ap.add_argument("--single-sample", type=int, default=0,
                     help="batch workload: time the one-at-a-time path on the first K graphs only (0 = all)")
     ap.add_argument("--fast-classes", type=int, default=None, help="random vertex classes of the fast schedule")
+    ap.add_argument("--fast-classes-later", type=int, default=None,
+                    help="fast mode: class groups of the iterations after the first of a pass")
     ap.add_argument("--compact", type=int, default=None, help="1: compact super-vertex graphs, 0: keep holey CSR")
     ap.add_argument("--fast-giant-class", type=int, default=None,
                     help="fast mode: 1 puts every giant row of a pass in one class")
@@ -429,6 +431,8 @@ def main():
     knobs = {}
     if args.fast_classes is not None:
         knobs["fast_classes"] = args.fast_classes
+    if args.fast_classes_later is not None:
+        knobs["fast_classes_later"] = args.fast_classes_later
     if args.compact is not None:
         knobs["compact"] = args.compact
     if args.fast_giant_class is not None:
@@ -539,6 +543,7 @@ def main():
         "config": {"workload": WORKLOADS[args.workload][1], "n": g.n, "arcs": g.n_arcs, "mode": args.mode,
                    "knobs": {"giant_min_degree": params.giant_min_degree, "lm_blocks_per_sm": params.lm_blocks_per_sm,
                              "compact": params.compact, "fast_classes": params.fast_classes,
+                             "fast_classes_later": params.fast_classes_later,
                              "autotuned": tuned_ms is not None},
                    "parallelism": "replicas" if ws > 1 else "single", "l2": "inputs larger than L2 "
                    f"(CSR {(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes) / 1e9:.2f} GB vs 0.13 GB L2)"},

@@ -85,6 +85,14 @@ typedef struct {
                                     them share the SMs */
   int32_t giant_min_degree;      /* rows longer than this take the multi-block giant path; 2048..4096
                                     (0 = 4096: rows of 2049..4096 arcs use one block with a 64 KB table) */
+  int32_t fast_classes_later;    /* fast mode: iterations after the first of a pass may run the classes
+                                    in as few as this many groups of consecutive classes (default 1;
+                                    0 = fast_classes, every class on its own).  The group count is
+                                    raised to fast_classes * (1024 * SMs) / |V'| so that a group is
+                                    grouped only where it is much larger than the vertices the GPU
+                                    holds in flight (small graphs keep every class on its own).  The
+                                    first iteration, where most vertices move, takes every class on
+                                    its own */
 } louvain_params;
 
 typedef struct {

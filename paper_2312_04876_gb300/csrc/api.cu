@@ -370,7 +370,7 @@ float elapsed(louvain_handle h, size_t a, size_t b) {
 bool valid_params(const louvain_params* p) {
   return p && p->max_passes >= 0 && p->max_iterations >= 0 && p->tolerance >= 0.0 && p->tolerance_drop > 0.0 &&
          p->aggregation_tolerance >= 0.0 && p->fast_classes >= 0 && p->fast_classes <= 4096 &&
-         p->lm_blocks_per_sm >= 0 && p->lm_blocks_per_sm <= 64 &&
+         p->lm_blocks_per_sm >= 0 && p->lm_blocks_per_sm <= 64 && p->fast_classes_later >= 0 &&
          (p->giant_min_degree == 0 || (p->giant_min_degree >= 2048 && p->giant_min_degree <= 4096)) &&
          (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
 }
@@ -433,11 +433,111 @@ louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, i
   return LOUVAIN_OK;
 }
 
+// One step of a local-moving iteration: the vertices of one colour class (deterministic) or of
+// one group of random classes (fast), as perm ranges per degree bucket, the giant range of the
+// class-ordered giant list, and (deterministic) the perm range the Sigma apply covers.
+constexpr int64_t kInFlightPerSm = 1024;  // vertices a local-moving launch holds per SM (4-lane groups)
+
+struct ClassStep {
+  int64_t start[kNumBuckets] = {};
+  int64_t count[kNumBuckets] = {};
+  int64_t g0 = 0, g1 = 0;
+  int64_t apply_start = 0, apply_count = 0;
+};
+
+// Launches one iteration (every step; the convergence test at the end).  With `streams` the
+// degree buckets of a step fork to one side stream each and join before the next step (used
+// while capturing a CUDA graph); otherwise they run in order on c.s with per-launch profiling.
 template <class M>
-louvain_status capture_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st,
-                                 const std::vector<int64_t>& ho, const std::vector<int64_t>& gofs, int32_t ncol,
-                                 bool det, bool pruning, GraphCtl* gc, int32_t n_graphs, cudaGraphExec_t* exec,
-                                 int64_t* launches);
+void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st,
+                       const std::vector<ClassStep>& steps, const int32_t* glist, bool det, bool pruning,
+                       GraphCtl* gc, int32_t n_graphs, bool streams) {
+  Workspace& ws = h->ws;
+  for (size_t k = 0; k < steps.size(); k++) {
+    const ClassStep& cs = steps[k];
+    if (streams) cudaEventRecord(h->fork_ev[k], c.s);
+    for (int b = 0; b < kNumBuckets; b++) {
+      const bool giant = b == kNumBuckets - 1;
+      const int64_t cnt = giant ? cs.g1 - cs.g0 : cs.count[b];
+      if (cnt <= 0) continue;
+      if (streams) {
+        Ctx cb = c;
+        cb.s = h->side[b];
+        cb.launches = 0;
+        cudaStreamWaitEvent(cb.s, h->fork_ev[k], 0);
+        if (!giant) move_bucket<M>(cb, b, g, st, ws.perm + cs.start[b], cnt, ws.gt, !det, pruning);
+        else giant_move<M>(cb, g, st, glist, cs.g0, cs.g1, ws.gp, !det, pruning);
+        c.launches += cb.launches;
+        cudaEventRecord(h->join_ev[k * kNumBuckets + b], cb.s);
+        cudaStreamWaitEvent(c.s, h->join_ev[k * kNumBuckets + b], 0);
+      } else {
+        const int pm = prof_begin(h, c);
+        if (!giant) move_bucket<M>(c, b, g, st, ws.perm + cs.start[b], cnt, ws.gt, !det, pruning);
+        else giant_move<M>(c, g, st, glist, cs.g0, cs.g1, ws.gp, !det, pruning);
+        prof_end(h, c, kLm0 + b, pm);
+      }
+    }
+    if (det && cs.apply_count > 0) {
+      const int pm = streams ? -1 : prof_begin(h, c);
+      move_apply<M>(c, st, ws.perm + cs.apply_start, cs.apply_count);
+      if (!streams) prof_end(h, c, kApply, pm);
+    }
+  }
+  if (gc) batch_finish<M>(c, ws.ctrl, gc, n_graphs);
+  else move_finish<M>(c, ws.ctrl);
+}
+
+// Captures one iteration into an executable CUDA graph (launches recorded on a private stream, the
+// graph runs on the caller's).  *launches = kernels per replay.
+template <class M>
+louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<typename M::w_t>& g, const PassState<M>& st,
+                                 const std::vector<ClassStep>& steps, const int32_t* glist, bool det, bool pruning,
+                                 GraphCtl* gc, int32_t n_graphs, cudaGraphExec_t* exec, int64_t* launches) {
+  *exec = nullptr;
+  if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return cuda_err(h, cudaGetLastError(), "capture stream creation");
+  Ctx c = c0;
+  c.s = h->cap;
+  c.launches = 0;
+  for (int b = 0; b < kNumBuckets; b++)
+    if (!h->side[b] && cudaStreamCreateWithFlags(&h->side[b], cudaStreamNonBlocking) != cudaSuccess)
+      return cuda_err(h, cudaGetLastError(), "side stream creation");
+  while (h->fork_ev.size() < steps.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_err(h, cudaGetLastError(), "event creation");
+    h->fork_ev.push_back(e);
+  }
+  while (h->join_ev.size() < steps.size() * kNumBuckets) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_err(h, cudaGetLastError(), "event creation");
+    h->join_ev.push_back(e);
+  }
+  move_prepare();
+  cudaError_t e = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_err(h, e, "graph capture begin");
+  enqueue_iteration<M>(h, c, g, st, steps, glist, det, pruning, gc, n_graphs, true);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(c.s, &graph);
+  *launches = c.launches;
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_err(h, e, "graph capture end");
+  }
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    *exec = nullptr;
+    return cuda_err(h, e, "graph instantiation");
+  }
+  return LOUVAIN_OK;
+}
+
+struct ExecGuard {
+  cudaGraphExec_t e = nullptr;
+  ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+};
 
 // One local-moving phase (Algorithm 2) on g from the state in ws (K, Sig, Cp, flags set).
 // Fills *li and *moves.  Deterministic mode colours g first.
@@ -458,7 +558,7 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   const bool det = p.mode == LOUVAIN_MODE_DETERMINISTIC;
   if (p.lm_blocks_per_sm > 0) c.lm_blocks_per_sm = p.lm_blocks_per_sm;
   louvain_status s;
-  std::vector<int64_t> ho;  // class-bucket offsets (deterministic) or bucket offsets (fast)
+  std::vector<int64_t> ho;  // bucket-sort offsets: colour-major (deterministic) or bucket-major (fast)
   int32_t ncol = 1;
   if (det) {
     GraphView<int32_t> gs{g.n, g.rbeg, g.rend, g.tg, nullptr};
@@ -482,7 +582,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     if (!q) return s;
     ho.assign(q, q + nkeys + 1);
   } else {
-    // fast schedule: random vertex classes processed one after another, asynchronous inside a class
+    // fast schedule: random vertex classes processed one after another, asynchronous inside a class;
+    // keys bucket-major, so a bucket's vertices of consecutive classes are one contiguous range
     ncol = p.fast_classes > 0 ? p.fast_classes : 1;
     const int64_t nkeys = (int64_t)ncol * kNumBuckets;
     if ((s = ensure_keys(h, nkeys)) != LOUVAIN_OK) return s;
@@ -497,62 +598,93 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     ho.assign(q, q + nkeys + 1);
   }
   if (event_at(h, ev_colour_done)) cudaEventRecord(h->events[ev_colour_done], c.s);
-  // giant vertices of every class in one list and one plan for the whole pass (each giant owns a
-  // table of the pool; the scans leave every table empty)
+  // giant vertices of every class in one class-ordered list and one plan for the whole pass (each
+  // giant owns a table of the pool; the scans leave every table empty)
   std::vector<int64_t> gofs((size_t)ncol + 1, 0);
-  for (int cl = 0; cl < ncol; cl++) {
-    const size_t base = (size_t)cl * kNumBuckets;
-    const int64_t cnt = ho[base + kNumBuckets] - ho[base + kNumBuckets - 1];
-    if (cnt > 0)
-      cudaMemcpyAsync(ws.glist + gofs[cl], ws.perm + ho[base + kNumBuckets - 1], (size_t)cnt * sizeof(int32_t),
-                      cudaMemcpyDeviceToDevice, c.s);
-    gofs[cl + 1] = gofs[cl] + (cnt > 0 ? cnt : 0);
+  const int32_t* glist = ws.glist;
+  if (det) {
+    for (int cl = 0; cl < ncol; cl++) {
+      const size_t base = (size_t)cl * kNumBuckets;
+      const int64_t cnt = ho[base + kNumBuckets] - ho[base + kNumBuckets - 1];
+      if (cnt > 0)
+        cudaMemcpyAsync(ws.glist + gofs[cl], ws.perm + ho[base + kNumBuckets - 1], (size_t)cnt * sizeof(int32_t),
+                        cudaMemcpyDeviceToDevice, c.s);
+      gofs[cl + 1] = gofs[cl] + (cnt > 0 ? cnt : 0);
+    }
+  } else {
+    const size_t gb = (size_t)(kNumBuckets - 1) * ncol;  // the giants of all classes, in class order
+    glist = ws.perm + ho[gb];
+    for (int cl = 0; cl <= ncol; cl++) gofs[cl] = ho[gb + cl] - ho[gb];
   }
   if (giant_slots > 0 && (s = ensure_pool(h, c, giant_slots)) != LOUVAIN_OK) return s;
-  if (gofs[ncol] > 0) giant_move_plan<M>(c, g, ws.glist, gofs[ncol], ws.gp, ws.ctrl);
+  if (gofs[ncol] > 0) giant_move_plan<M>(c, g, glist, gofs[ncol], ws.gp, ws.ctrl);
+  // the steps of an iteration: every class on its own; in fast mode the iterations after the first
+  // may merge consecutive classes into groups (fewer, larger launches once most vertices are pruned)
+  auto make_steps = [&](int group) {
+    std::vector<ClassStep> v;
+    for (int c0 = 0; c0 < ncol; c0 += group) {
+      const int c1 = c0 + group < ncol ? c0 + group : ncol;
+      ClassStep cs;
+      for (int b = 0; b < kNumBuckets - 1; b++) {
+        if (det) {
+          cs.start[b] = ho[(size_t)c0 * kNumBuckets + b];
+          cs.count[b] = ho[(size_t)c0 * kNumBuckets + b + 1] - cs.start[b];
+        } else {
+          cs.start[b] = ho[(size_t)b * ncol + c0];
+          cs.count[b] = ho[(size_t)b * ncol + c1] - cs.start[b];
+        }
+      }
+      cs.g0 = gofs[c0];
+      cs.g1 = gofs[c1];
+      if (det) {
+        cs.apply_start = ho[(size_t)c0 * kNumBuckets];
+        cs.apply_count = ho[(size_t)c0 * kNumBuckets + kNumBuckets] - cs.apply_start;
+      }
+      v.push_back(cs);
+    }
+    return v;
+  };
+  // Grouping keeps the share of vertices that decide at the same time at or below one class's
+  // (1/fast_classes) only where a group is much larger than what the GPU holds in flight
+  // (kInFlightPerSm vertices per SM); a small graph sits wholly in flight, so there each class stays
+  // on its own.  A batch counts by its mean graph, as moves never cross graphs.
+  int later = ncol;
+  if (!det && p.fast_classes_later > 0 && p.fast_classes_later < ncol) {
+    const int64_t n_eff = gc && n_graphs > 0 ? g.n / n_graphs : g.n;
+    const int64_t window = (int64_t)c.num_sms * kInFlightPerSm;
+    const int64_t need = n_eff > 0 ? ((int64_t)ncol * window + n_eff - 1) / n_eff : ncol;
+    later = (int)std::min<int64_t>(ncol, std::max<int64_t>(p.fast_classes_later, need));
+  }
+  const std::vector<ClassStep> first = make_steps(1);
+  const std::vector<ClassStep> rest = later == ncol ? first : make_steps((ncol + later - 1) / later);
   move_setup(c, ws.ctrl, tau, p.max_iterations);
   if (gc) batch_move_setup(c, gc, n_graphs, p.max_iterations);
   const bool pruning = p.pruning != 0;
   int enq = 0;
   const int batch = det ? 2 : 4;
-  // Without per-launch profiling, one iteration is captured once per pass as a CUDA graph -- per
-  // class a fork to one stream per degree bucket and a join -- and replayed for every iteration.
-  cudaGraphExec_t exec = nullptr;
-  int64_t graph_launches = 0;
+  // Without per-launch profiling, an iteration is captured once per pass as a CUDA graph -- per
+  // step a fork to one stream per degree bucket and a join -- and replayed for every iteration.
+  ExecGuard g_first, g_rest;
+  int64_t l_first = 0, l_rest = 0;
   if (!h->prof.on && h->use_graphs) {
-    if ((s = capture_iteration<M>(h, c, g, st, ho, gofs, ncol, det, pruning, gc, n_graphs, &exec, &graph_launches)) !=
+    if ((s = capture_iteration<M>(h, c, g, st, first, glist, det, pruning, gc, n_graphs, &g_first.e, &l_first)) !=
         LOUVAIN_OK)
       return s;
+    if (&rest != &first && rest.size() != first.size() &&
+        (s = capture_iteration<M>(h, c, g, st, rest, glist, det, pruning, gc, n_graphs, &g_rest.e, &l_rest)) !=
+            LOUVAIN_OK)
+      return s;
   }
-  struct ExecGuard {
-    cudaGraphExec_t e;
-    ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
-  } guard{exec};
   while (true) {
     for (int k = 0; k < batch && enq < p.max_iterations; k++, enq++) {
-      if (exec) {
-        cudaGraphLaunch(exec, c.s);
-        c.launches += graph_launches;
+      const bool is_first = enq == 0 || rest.size() == first.size();
+      const cudaGraphExec_t ex = is_first ? g_first.e : (g_rest.e ? g_rest.e : nullptr);
+      if (ex) {
+        cudaGraphLaunch(ex, c.s);
+        c.launches += is_first ? l_first : l_rest;
         continue;
       }
-      for (int cl = 0; cl < ncol; cl++) {
-        const size_t base = (size_t)cl * kNumBuckets;
-        for (int b = 0; b < kNumBuckets; b++) {
-          const int64_t cnt = ho[base + b + 1] - ho[base + b];
-          if (cnt <= 0) continue;
-          const int pm = prof_begin(h, c);
-          if (b < kNumBuckets - 1) move_bucket<M>(c, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
-          else giant_move<M>(c, g, st, ws.glist, gofs[cl], gofs[cl + 1], ws.gp, !det, pruning);
-          prof_end(h, c, kLm0 + b, pm);
-        }
-        if (det) {
-          const int pm = prof_begin(h, c);
-          move_apply<M>(c, st, ws.perm + ho[base], ho[base + kNumBuckets] - ho[base]);
-          prof_end(h, c, kApply, pm);
-        }
-      }
-      if (gc) batch_finish<M>(c, ws.ctrl, gc, n_graphs);
-      else move_finish<M>(c, ws.ctrl);
+      enqueue_iteration<M>(h, c, g, st, is_first ? first : rest, glist, det, pruning, gc, n_graphs, false);
     }
     const Ctrl* hc = read_ctrl(h, c, &s, "local move");
     if (!hc) return s;
@@ -563,76 +695,6 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
       return LOUVAIN_OK;
     }
   }
-}
-
-// Captures one local-moving iteration (every class: buckets on their side streams, the deterministic
-// apply, then the convergence test) into an executable CUDA graph.  *launches = kernels per replay.
-template <class M>
-louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<typename M::w_t>& g, const PassState<M>& st,
-                                 const std::vector<int64_t>& ho, const std::vector<int64_t>& gofs, int32_t ncol,
-                                 bool det, bool pruning, GraphCtl* gc, int32_t n_graphs, cudaGraphExec_t* exec,
-                                 int64_t* launches) {
-  Workspace& ws = h->ws;
-  *exec = nullptr;
-  if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
-    return cuda_err(h, cudaGetLastError(), "capture stream creation");
-  Ctx c = c0;  // launches are recorded on the private capture stream, the graph runs on c0.s
-  c.s = h->cap;
-  c.launches = 0;
-  for (int b = 0; b < kNumBuckets; b++)
-    if (!h->side[b] && cudaStreamCreateWithFlags(&h->side[b], cudaStreamNonBlocking) != cudaSuccess)
-      return cuda_err(h, cudaGetLastError(), "side stream creation");
-  const size_t need = (size_t)ncol;
-  while (h->fork_ev.size() < need) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-      return cuda_err(h, cudaGetLastError(), "event creation");
-    h->fork_ev.push_back(e);
-  }
-  while (h->join_ev.size() < need * kNumBuckets) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-      return cuda_err(h, cudaGetLastError(), "event creation");
-    h->join_ev.push_back(e);
-  }
-  move_prepare();
-  const int64_t l0 = c.launches;
-  cudaError_t e = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return cuda_err(h, e, "graph capture begin");
-  for (int cl = 0; cl < ncol; cl++) {
-    const size_t base = (size_t)cl * kNumBuckets;
-    cudaEventRecord(h->fork_ev[cl], c.s);
-    for (int b = 0; b < kNumBuckets; b++) {
-      const int64_t cnt = ho[base + b + 1] - ho[base + b];
-      if (cnt <= 0) continue;
-      Ctx cb = c;
-      cb.s = h->side[b];
-      cb.launches = 0;
-      cudaStreamWaitEvent(cb.s, h->fork_ev[cl], 0);
-      if (b < kNumBuckets - 1) move_bucket<M>(cb, b, g, st, ws.perm + ho[base + b], cnt, ws.gt, !det, pruning);
-      else giant_move<M>(cb, g, st, ws.glist, gofs[cl], gofs[cl + 1], ws.gp, !det, pruning);
-      c.launches += cb.launches;
-      cudaEventRecord(h->join_ev[base + b], cb.s);
-      cudaStreamWaitEvent(c.s, h->join_ev[base + b], 0);
-    }
-    if (det) move_apply<M>(c, st, ws.perm + ho[base], ho[base + kNumBuckets] - ho[base]);
-  }
-  if (gc) batch_finish<M>(c, ws.ctrl, gc, n_graphs);
-  else move_finish<M>(c, ws.ctrl);
-  cudaGraph_t graph = nullptr;
-  e = cudaStreamEndCapture(c.s, &graph);
-  *launches = c.launches - l0;
-  if (e != cudaSuccess) {
-    if (graph) cudaGraphDestroy(graph);
-    return cuda_err(h, e, "graph capture end");
-  }
-  e = cudaGraphInstantiate(exec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (e != cudaSuccess) {
-    *exec = nullptr;
-    return cuda_err(h, e, "graph instantiation");
-  }
-  return LOUVAIN_OK;
 }
 
 template <class M>
@@ -1033,6 +1095,7 @@ louvain_status louvain_default_params(louvain_params* p) {
   p->pass_modularity = 0;
   p->profile = 0;
   p->fast_classes = 16;
+  p->fast_classes_later = 1;
   return LOUVAIN_OK;
 }
 

@@ -143,7 +143,7 @@ __device__ __forceinline__ int sort_key(KeyDesc kd, int64_t i, const int64_t* rb
     const uint64_t h = kd.giant_class >= 0 && b == kNumBuckets - 1
                            ? (uint64_t)kd.giant_class
                            : hash3(kd.seed, (uint64_t)kd.pass, local_id(kd.seg, (int32_t)i));
-    return (int)(h % (uint64_t)kd.classes) * kNumBuckets + b;
+    return b * kd.classes + (int)(h % (uint64_t)kd.classes);  // bucket-major: classes contiguous per bucket
   }
   return colour[i] * kNumBuckets + b;
 }

@@ -121,6 +121,67 @@ __device__ __forceinline__ bool merge_members(const MergeArgs<M>& a, int64_t k0,
   return ok;
 }
 
+// Block version for the one-community-per-block buckets: all kBlock threads flatten the arcs of
+// kBlock members at a time (block-wide prefix of their row lengths in shared memory, a binary
+// search per arc), so a community dominated by one long member row keeps every warp busy.
+template <class M>
+__device__ __forceinline__ bool merge_members_block(const MergeArgs<M>& a, int64_t k0, int64_t k1, int32_t* tk,
+                                                    typename M::h_t* tv, unsigned size, int shift,
+                                                    unsigned long long& arcs, int64_t* s_incl, int64_t* s_base,
+                                                    int64_t* s_wsum) {
+  typedef typename M::h_t H;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  bool ok = true;
+  for (int64_t kb = k0; kb < k1; kb += kBlock) {
+    const int64_t k = kb + t;
+    int64_t b = 0, len = 0;
+    if (k < k1) {
+      const int32_t i = a.cverts[k];
+      b = a.g.rbeg[i];
+      len = a.g.rend[i] - b;
+    }
+    arcs += (unsigned long long)len;
+    int64_t incl = lanes_incl_scan<32>(len, 0xffffffffu);
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    int64_t before = 0;
+    for (int w = 0; w < warp; w++) before += s_wsum[w];
+    incl += before;
+    s_incl[t] = incl;
+    s_base[t] = b - (incl - len);  // arc of flat position f in this member: s_base + f
+    __syncthreads();
+    const int64_t total = s_incl[kBlock - 1];
+    constexpr int U = 4;
+    for (int64_t f0 = 0; f0 < total; f0 += (int64_t)kBlock * U) {
+      int64_t ee[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int64_t f = f0 + (int64_t)u * kBlock + t;
+        int lo = 0;  // members whose inclusive prefix is <= f
+#pragma unroll
+        for (int step = kBlock / 2; step >= 1; step >>= 1)
+          if (s_incl[lo + step - 1] <= f) lo += step;
+        ee[u] = f < total ? s_base[lo] + f : -1;
+      }
+      int32_t jj[U];
+      H ww[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        jj[u] = ee[u] >= 0 ? a.g.tg[ee[u]] : 0;
+        ww[u] = ee[u] >= 0 ? (H)a.g.w[ee[u]] : H(0);
+      }
+      int32_t cc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) cc[u] = ee[u] >= 0 ? a.Cp[jj[u]] : kEmpty;
+#pragma unroll
+      for (int u = 0; u < U; u++)
+        if (ee[u] >= 0) ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
+    }
+    __syncthreads();  // s_incl / s_base / s_wsum are rewritten
+  }
+  return ok;
+}
+
 template <class M, int G, int LOG, bool GLOBAL>
 __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int32_t* list, int64_t count,
                                                        int32_t* gkeys, typename M::h_t* gvals, int64_t gslots,
@@ -132,6 +193,7 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
   int32_t* skeys = reinterpret_cast<int32_t*>(mg_dyn);
   H* svals = reinterpret_cast<H*>(mg_dyn + sizeof(int32_t) * GPB * SL);
   __shared__ unsigned long long s_cnt;
+  __shared__ int64_t s_incl[G > 32 ? kBlock : 1], s_base[G > 32 ? kBlock : 1], s_wsum[kBlock / 32];
   const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
   const unsigned lane = Grp<G>::lane();
   int32_t* tk;
@@ -159,8 +221,7 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
       // each lane adds the row lengths of the members it loaded
       ok = merge_members<M, (G <= 32 ? G : 32)>(a, m0, m1, G, tk, tv, size, shift, Grp<G>::mask(), ctr[2]);
     } else {
-      const int warp = threadIdx.x >> 5;
-      ok = merge_members<M, 32>(a, m0 + 32 * warp, m1, 32 * (G / 32), tk, tv, size, shift, 0xffffffffu, ctr[2]);
+      ok = merge_members_block<M>(a, m0, m1, tk, tv, size, shift, ctr[2], s_incl, s_base, s_wsum);
     }
     if (!ok) atomicOr(&a.ctrl->error, kErrTableFull);
     Grp<G>::sync();

@@ -768,7 +768,8 @@ louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typenam
     if (cb[b + 1] - cb[b] <= 0) continue;
     const int pm = prof_begin(h, c);
     if (b < kNumBuckets - 1) merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.gt);
-    else giant_merge<M>(c, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.dperm, hb, ws.csz, ws.gp, ws.gpv);
+    else giant_merge<M>(c, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.csz, ws.gp, reinterpret_cast<int64_t*>(ws.tot),
+                        ws.len, ws.tile_tmp);
     prof_end(h, c, kMg0 + b, pm);
   }
   return LOUVAIN_OK;

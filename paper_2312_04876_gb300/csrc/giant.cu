@@ -19,8 +19,9 @@
 //   decide  (local move) per giant: best over its ranges, then the move exactly as the per-vertex
 //           kernels make it;
 //   mark    (local move, pruning) grid-stride over chunks of the giants that moved.
-// Merges insert member rows vertex by vertex (members of giant communities, by their own degree
-// bucket), so a giant community's arcs spread over the GPU however its members are shaped.
+// Merges cut the concatenated member rows of each giant community (community-vertex CSR order)
+// into chunks taken community after community, so a community's arcs spread over the GPU however
+// its members are shaped, while the blocks in flight touch the tables of only a few communities.
 #include "internal.cuh"
 
 namespace lv {
@@ -33,8 +34,8 @@ constexpr int kLocLog = 12;     // shared pre-aggregation table: 4096 slots >= 2
 
 // ---------------------------------------------------------------- plan
 // kind 0: local move, item = vertex list[k]: table for min(deg, n_bound) keys, chunks over its row;
-// kind 1: merge, item = community list[k]: table for min(cdeg, n_bound) keys, no chunks (rows are
-//         inserted member-wise); gix[c] = k;
+// kind 1: merge, item = community list[k]: table for min(cdeg, n_bound) keys, chunks over the
+//         concatenated rows of its members; gix[c] = k;
 // kind 2: chunks only, item = vertex list[k] whose community Cp[i] >= 0 is giant (gix >= 0);
 // kind 3: chunks only, every listed row.
 __global__ void k_gplan_counts(int kind, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
@@ -46,6 +47,7 @@ __global__ void k_gplan_counts(int kind, const int32_t* list, int64_t m, const i
     if (kind == 1) {
       const int64_t bound = cdeg[v] < n_bound ? cdeg[v] : n_bound;
       ts = (int64_t)1 << tbl_log2(bound, 6, 31);
+      nch = (cdeg[v] + kChunk - 1) / kChunk;
       gix[v] = (int32_t)k;
     } else {
       const int64_t deg = rend[v] - rbeg[v];
@@ -131,12 +133,12 @@ void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t*
 
 // tbl_add for a giant's table at pool offset `base` that also sets the slot's bit in the pool's
 // occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
+// Probing starts at slot s (the key's home) whose key was already read as k0.
 template <class V>
-__device__ __forceinline__ bool tbl_add_mark(int32_t* keys, V* vals, unsigned size, int shift, int32_t key, V w,
-                                             unsigned* bits, int64_t base) {
-  unsigned s = tbl_home(key, shift);
+__device__ __forceinline__ bool tbl_add_mark_at(int32_t* keys, V* vals, unsigned size, int32_t key, V w,
+                                                unsigned* bits, int64_t base, unsigned s, int32_t k0) {
   for (unsigned p = 0; p < size; p++) {
-    const int32_t k = *((volatile int32_t*)&keys[s]);
+    const int32_t k = p == 0 ? k0 : *((volatile int32_t*)&keys[s]);
     if (k == key) { atomicAdd(&vals[s], w); return true; }
     if (k == kEmpty) {
       const int32_t old = atomicCAS(&keys[s], kEmpty, key);
@@ -150,6 +152,13 @@ __device__ __forceinline__ bool tbl_add_mark(int32_t* keys, V* vals, unsigned si
     s = (s + 1) & (size - 1);
   }
   return false;
+}
+
+template <class V>
+__device__ __forceinline__ bool tbl_add_mark(int32_t* keys, V* vals, unsigned size, int shift, int32_t key, V w,
+                                             unsigned* bits, int64_t base) {
+  const unsigned s = tbl_home(key, shift);
+  return tbl_add_mark_at(keys, vals, size, key, w, bits, base, s, *((volatile int32_t*)&keys[s]));
 }
 
 // ---------------------------------------------------------------- shared pre-aggregation
@@ -171,13 +180,31 @@ __device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* tk, H* tv,
                                             int64_t base) {
   bool ok = true;
   __syncthreads();
-  for (int s = threadIdx.x; s < (1 << kLocLog); s += kBlock) {
-    const int32_t key = la.keys[s];
-    if (key != kEmpty) {
-      ok &= tbl_add_mark(tk, tv, size, 32 - lg, key, la.vals[s], bits, base);
-      la.keys[s] = kEmpty;
-      la.vals[s] = H(0);
+  // V slots per thread per round: the home-slot reads of the V keys are issued together
+  constexpr int V = 4;
+  for (int s0 = threadIdx.x; s0 < (1 << kLocLog); s0 += kBlock * V) {
+    int32_t key[V], seen[V];
+    H val[V];
+    unsigned home[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      const int s = s0 + v * kBlock;
+      key[v] = la.keys[s];
+      val[v] = la.vals[s];
+      if (key[v] != kEmpty) {
+        la.keys[s] = kEmpty;
+        la.vals[s] = H(0);
+      }
     }
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      home[v] = tbl_home(key[v], 32 - lg);
+      seen[v] = key[v];
+      if (key[v] != kEmpty) seen[v] = *((volatile int32_t*)&tk[home[v]]);
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++)
+      if (key[v] != kEmpty) ok &= tbl_add_mark_at(tk, tv, size, key[v], val[v], bits, base, home[v], seen[v]);
   }
   __syncthreads();
   return ok;
@@ -472,63 +499,125 @@ void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>&
 }
 
 // ---------------------------------------------------------------- merge of giant communities
-// Member rows of giant communities go into their community's table: one group per member (the
-// member's degree bucket), giant members by arc chunks.
-template <class M, int G>
-__global__ void __launch_bounds__(kBlock) k_giant_mg_insert(GraphView<typename M::w_t> g, const int32_t* list,
-                                                            int64_t count, const int32_t* Cp, const int32_t* gix,
-                                                            GiantPlan p, int64_t mc, Ctrl* ctrl) {
-  typedef typename M::h_t H;
-  if (p.slice_off[mc] == 0) return;  // no (or an over-full) plan
-  constexpr int GPB = G <= 32 ? kBlock / G : 1;
-  const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
-  const unsigned lane = Grp<G>::lane();
-  bool ok = true;
-  for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
-    const int32_t i = list[idx];
-    const int32_t ci = Cp[i];
-    if (ci < 0) continue;  // batched: the graph of i left the pass loop
-    const int32_t k = gix[ci];
-    if (k < 0) continue;
-    const int64_t off = p.tab_off[k];
-    const unsigned ts = (unsigned)(p.tab_off[k + 1] - off);
-    int lg = 0;
-    while ((1u << lg) < ts) lg++;
-    int32_t* tk = p.keys + off;
-    H* tv = reinterpret_cast<H*>(p.vals) + off;
-    for (int64_t e = g.rbeg[i] + lane; e < g.rend[i]; e += G)
-      ok &= tbl_add_mark(tk, tv, ts, 32 - lg, Cp[g.tg[e]], (H)g.w[e], p.bits, off);
+// The member rows of a giant community, concatenated in community-vertex CSR order, form one arc
+// range [memoff[coff[c]], memoff[coff[c+1]]) (memoff = exclusive scan of the member degrees in
+// cverts order).  A block takes chunks of kChunk arcs of that range in community order, so the
+// blocks in flight share the tables of a few communities, which stay in L2; each chunk is summed
+// in the block's shared table and flushed once per distinct key.
+constexpr int kMemWin = 1024;  // members of a chunk staged in shared memory at a time
+
+// deg[j] = degree of member cverts[j] for the coff[nc] listed members (vertices of graphs that left
+// the pass loop are not listed), 0 for j in [coff[nc], n).
+__global__ void k_member_degrees(const int32_t* cverts, const int64_t* coff, int64_t nc, int64_t n,
+                                 const int64_t* rbeg, const int64_t* rend, int64_t* deg) {
+  const int64_t listed = coff[nc];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    int64_t d = 0;
+    if (j < listed) {
+      const int32_t i = cverts[j];
+      d = rend[i] - rbeg[i];
+    }
+    deg[j] = d;
   }
-  if (!ok) atomicOr(&ctrl->error, kErrTableFull);
 }
 
 template <class M>
-__global__ void __launch_bounds__(kBlock) k_giant_mg_insert_chunks(GraphView<typename M::w_t> g, const int32_t* list,
-                                                                   int64_t m, const int32_t* Cp, const int32_t* gix,
-                                                                   GiantPlan pv, GiantPlan p, int64_t mc, Ctrl* ctrl) {
+__global__ void __launch_bounds__(kBlock) k_giant_mg_comm_chunks(GraphView<typename M::w_t> g, const int32_t* clist,
+                                                                 int64_t m, const int64_t* coff, const int32_t* cverts,
+                                                                 const int64_t* memoff, const int32_t* Cp, GiantPlan p,
+                                                                 Ctrl* ctrl) {
   typedef typename M::h_t H;
   __shared__ LocalAgg<H> la;
-  if (p.slice_off[mc] == 0) return;
-  const int64_t nchunks = pv.chunk_off[m];
-  if (nchunks == 0) return;
+  __shared__ int32_t s_off[kMemWin + 1];  // memoff of the staged members relative to the chunk start,
+                                          // clamped to +-2^30 (compared against [0, kChunk) only)
+  __shared__ int64_t s_rb[kMemWin];       // row start - (memoff - chunk start): arc of position r
+  __shared__ int64_t s_j0;
+  if (p.slice_off[m] == 0) return;        // no (or an over-full) plan
+  const int64_t nchunks = p.chunk_off[m];
   local_clear(la);
   bool ok = true;
+  unsigned long long n_comm = 0, n_mem = 0, n_arcs = 0;  // traffic counters (thread 0)
   for (int64_t q = blockIdx.x; q < nchunks; q += gridDim.x) {
-    const int64_t kv = pv.cowner[q];
-    const int32_t i = list[kv];
-    const int32_t k = gix[Cp[i]];
+    const int32_t k = p.cowner[q];
+    const int32_t c = clist[k];
+    const int64_t jb = coff[c], je = coff[c + 1];
+    const int64_t a0 = memoff[jb] + (q - p.chunk_off[k]) * kChunk;
+    const int64_t a1 = a0 + kChunk < memoff[je] ? a0 + kChunk : memoff[je];
+    if (threadIdx.x == 0) {  // the member holding arc a0: largest j in [jb, je) with memoff[j] <= a0
+      n_arcs += (unsigned long long)(a1 - a0);
+      if (q == p.chunk_off[k]) {
+        n_comm++;
+        n_mem += (unsigned long long)(je - jb);
+      }
+      int64_t lo = jb, hi = je;
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (memoff[mid] <= a0) lo = mid; else hi = mid;
+      }
+      s_j0 = lo;
+    }
+    __syncthreads();
+    int64_t jw = s_j0;
+    while (true) {
+      const int nm = (int)(je - jw < kMemWin ? je - jw : kMemWin);
+      for (int t = threadIdx.x; t <= nm; t += kBlock) {
+        const int64_t r = memoff[jw + t] - a0;
+        s_off[t] = (int32_t)(r < (1 << 30) ? (r > -(1 << 30) ? r : -(1 << 30)) : (1 << 30));
+        if (t < nm) s_rb[t] = g.rbeg[cverts[jw + t]] - r;
+      }
+      __syncthreads();
+      const int32_t lo = s_off[0] > 0 ? s_off[0] : 0;
+      const int32_t span = (int32_t)(a1 - a0);
+      const int32_t hi = s_off[nm] < span ? s_off[nm] : span;
+      int kk = 0;
+      constexpr int U = 4;  // arcs per thread per round: U independent load chains in flight
+      for (int32_t r0 = lo + (int32_t)threadIdx.x; r0 < hi; r0 += kBlock * U) {
+        int64_t ee[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int32_t r = r0 + u * kBlock;
+          ee[u] = -1;
+          if (r < hi) {
+            int kh = nm;  // largest kk in [kk, nm) with s_off[kk] <= r (r only grows)
+            while (kh - kk > 1) {
+              const int mid = (kk + kh) >> 1;
+              if (s_off[mid] <= r) kk = mid; else kh = mid;
+            }
+            ee[u] = s_rb[kk] + r;
+          }
+        }
+        int32_t jj[U];
+        H ww[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          jj[u] = ee[u] >= 0 ? g.tg[ee[u]] : 0;
+          ww[u] = ee[u] >= 0 ? (H)g.w[ee[u]] : H(0);
+        }
+        int32_t cc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) cc[u] = ee[u] >= 0 ? Cp[jj[u]] : kEmpty;
+#pragma unroll
+        for (int u = 0; u < U; u++)
+          if (ee[u] >= 0) ok &= tbl_add(la.keys, la.vals, 1u << kLocLog, 32 - kLocLog, cc[u], ww[u]);
+      }
+      const bool more = s_off[nm] < span && jw + nm < je;
+      __syncthreads();  // s_off / s_rb are restaged
+      if (!more) break;
+      jw += nm;
+    }
     const int64_t off = p.tab_off[k];
     const unsigned ts = (unsigned)(p.tab_off[k + 1] - off);
-    const int64_t e0 = g.rbeg[i] + (q - pv.chunk_off[kv]) * kChunk;
-    const int64_t e1 = e0 + kChunk < g.rend[i] ? e0 + kChunk : g.rend[i];
-    __syncthreads();
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += kBlock)
-      ok &= tbl_add(la.keys, la.vals, 1u << kLocLog, 32 - kLocLog, Cp[g.tg[e]], (H)g.w[e]);
     int lg = 0;
     while ((1u << lg) < ts) lg++;
     ok &= local_flush(la, p.keys + off, reinterpret_cast<H*>(p.vals) + off, ts, lg, p.bits, off);
   }
   if (!ok) atomicOr(&ctrl->error, kErrTableFull);
+  if (threadIdx.x == 0 && n_arcs) {
+    unsigned long long* st = ctrl->mg_stat[kNumBuckets - 1];
+    atomicAdd(&st[0], n_comm);
+    atomicAdd(&st[1], n_mem);
+    atomicAdd(&st[2], n_arcs);
+  }
 }
 
 // Emits the occupied slots of every slice into the holey row of its community: one warp per slice
@@ -585,37 +674,21 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_emit(const int32_t* list, i
 }
 
 template <class M>
-void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m, const int32_t* dperm,
-                 const int64_t* hb, int32_t* gix, const GiantPlan& p, const GiantPlan& pv) {
+void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m, int32_t* gix, const GiantPlan& p,
+                 int64_t* deg_tmp, int64_t* memoff, int64_t* tile_tmp) {
   if (m <= 0) return;
   const int grid = c.num_sms * 8;
-  // tables of the giant communities; gix = -1 for every other community
+  // tables and member-arc chunks of the giant communities; gix = -1 for every other community
   cudaMemsetAsync(gix, 0xFF, (size_t)a.nc * sizeof(int32_t), c.s);
   giant_plan(c, 1, clist, m, nullptr, nullptr, a.cdeg, a.nc, nullptr, gix, kSliceLog, p, a.ctrl);
-  // member rows, by the member's degree bucket
-  const int cap = c.num_sms * 16;
-  for (int b = 0; b < kNumBuckets; b++) {
-    const int64_t cnt = hb[b + 1] - hb[b];
-    if (cnt <= 0) continue;
-    const int32_t* l = dperm + hb[b];
-    switch (b) {
-      case 0: k_giant_mg_insert<M, 4><<<grid_for(cnt, kBlock / 4, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
-      case 1: k_giant_mg_insert<M, 8><<<grid_for(cnt, kBlock / 8, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
-      case 2:
-      case 3: k_giant_mg_insert<M, 32><<<grid_for(cnt, kBlock / 32, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
-      case 4:
-      case 5: k_giant_mg_insert<M, 256><<<grid_for(cnt, 1, cap), kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, p, m, a.ctrl); break;
-      default:
-        // giant members: chunk plan over their rows (members of giant communities only)
-        giant_plan(c, 2, l, cnt, a.g.rbeg, a.g.rend, nullptr, a.g.n, a.Cp, gix, kSliceLog, pv, a.ctrl);
-        k_giant_mg_insert_chunks<M><<<grid, kBlock, 0, c.s>>>(a.g, l, cnt, a.Cp, gix, pv, p, m, a.ctrl);
-        c.launches++;
-        break;
-    }
-    c.launches++;
-  }
+  const int64_t n = a.g.n;
+  k_member_degrees<<<grid_for(n, kBlock, grid), kBlock, 0, c.s>>>(a.cverts, a.coff, a.nc, n, a.g.rbeg, a.g.rend,
+                                                                    deg_tmp);
+  scan_exclusive_i64(c, deg_tmp, memoff, n, tile_tmp);
+  k_giant_mg_comm_chunks<M><<<c.num_sms * 4, kBlock, 0, c.s>>>(a.g, clist, m, a.coff, a.cverts, memoff, a.Cp, p,
+                                                               a.ctrl);
   k_giant_mg_emit<M><<<grid, kBlock, 0, c.s>>>(clist, m, a.hend, a.otg, a.ow, p, a.ctrl);
-  c.launches++;
+  c.launches += 3;
 }
 
 // ---------------------------------------------------------------- chunk-only plans (rows of list[k])
@@ -713,9 +786,9 @@ template void giant_move<FpMode>(Ctx&, const GraphView<float>&, const PassState<
 template void giant_move_plan<IntMode>(Ctx&, const GraphView<int32_t>&, const int32_t*, int64_t, const GiantPlan&,
                                        Ctrl*);
 template void giant_move_plan<FpMode>(Ctx&, const GraphView<float>&, const int32_t*, int64_t, const GiantPlan&, Ctrl*);
-template void giant_merge<IntMode>(Ctx&, const MergeArgs<IntMode>&, const int32_t*, int64_t, const int32_t*,
-                                   const int64_t*, int32_t*, const GiantPlan&, const GiantPlan&);
-template void giant_merge<FpMode>(Ctx&, const MergeArgs<FpMode>&, const int32_t*, int64_t, const int32_t*,
-                                  const int64_t*, int32_t*, const GiantPlan&, const GiantPlan&);
+template void giant_merge<IntMode>(Ctx&, const MergeArgs<IntMode>&, const int32_t*, int64_t, int32_t*,
+                                   const GiantPlan&, int64_t*, int64_t*, int64_t*);
+template void giant_merge<FpMode>(Ctx&, const MergeArgs<FpMode>&, const int32_t*, int64_t, int32_t*,
+                                  const GiantPlan&, int64_t*, int64_t*, int64_t*);
 
 }  // namespace lv

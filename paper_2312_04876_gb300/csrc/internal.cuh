@@ -218,12 +218,12 @@ void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>&
 void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
                 const int64_t* cdeg, int64_t n_bound, const int32_t* Cp, int32_t* gix, int slice_log,
                 const GiantPlan& p, Ctrl* ctrl);
-// Super-vertex rows of the giant communities clist[0, m): members inserted by their degree bucket
-// (dperm / hb of the current graph), giant members by chunks (plan pv).  gix [nc] receives each
-// community's giant index (-1 if not giant).
+// Super-vertex rows of the giant communities clist[0, m): the concatenated member rows of each
+// community (community-vertex CSR order) in chunks, community after community.  gix [nc] receives
+// each community's giant index (-1 if not giant); deg_tmp [n] and memoff [n + 1] are scratch.
 template <class M>
-void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m, const int32_t* dperm,
-                 const int64_t* hb, int32_t* gix, const GiantPlan& p, const GiantPlan& pv);
+void giant_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* clist, int64_t m, int32_t* gix, const GiantPlan& p,
+                 int64_t* deg_tmp, int64_t* memoff, int64_t* tile_tmp);
 
 // Chunk-only plan over the rows [rbeg, rend) of list[0, m).
 void giant_chunk_plan(Ctx& c, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,

@@ -61,6 +61,9 @@ struct Lane {
   louvain_handle h = nullptr;
   cudaStream_t s = nullptr;
   int64_t cap_n = -1, cap_a = -1;
+  // largest batch dimensions since the lane's caches were last dropped: the handle's workspace and
+  // the union buffers only grow, so what the lane holds is bounded by estimate_bytes(hn, ha)
+  int64_t hn = 0, ha = 0;
   int64_t* d_offs = nullptr;
   int32_t* d_tg = nullptr;
   int32_t* d_w = nullptr;
@@ -101,6 +104,8 @@ void lane_free_buffers(Lane& L) {
 
 bool lane_buffers(Lane& L, int64_t n, int64_t a) {
   if (L.cap_n >= n && L.cap_a >= a) return true;
+  n = n > L.cap_n ? n : L.cap_n;  // grow in both dimensions, never shrink one
+  a = a > L.cap_a ? a : L.cap_a;
   lane_free_buffers(L);
   const int64_t nn = n + 1, aa = a > 0 ? a : 1;
   if (cudaMalloc(&L.d_offs, sizeof(int64_t) * nn) != cudaSuccess || cudaMalloc(&L.d_tg, sizeof(int32_t) * aa) != cudaSuccess ||
@@ -187,15 +192,15 @@ void lane_main(louvain_server_s* S, int idx) {
       while (true) {
         if (S->stopping && S->queue.empty()) return;
         if (!S->queue.empty()) {
-          // the head request first (FIFO), then followers while they fit; the lane's own cache
-          // counts toward its need
+          // the head request first (FIFO), then followers while they fit; the lane's caches grow
+          // to the largest dimensions they have served, which its need covers
           const size_t others = S->reserved_total - L.reserved;
           int64_t n = 0, a = 0;
           for (Request* r : S->queue) {
             if ((int32_t)batch.size() >= S->max_graphs) break;
             if (!batch.empty() && r->wtype != batch[0]->wtype) break;
             if (!batch.empty() && S->max_arcs > 0 && a + r->a > S->max_arcs) break;
-            const size_t e = std::max(estimate_bytes(n + r->n, a + r->a), L.reserved);
+            const size_t e = std::max(estimate_bytes(std::max(L.hn, n + r->n), std::max(L.ha, a + r->a)), L.reserved);
             if (others + e > S->budget) break;
             batch.push_back(r);
             n += r->n;
@@ -206,8 +211,22 @@ void lane_main(louvain_server_s* S, int idx) {
             S->queue.erase(S->queue.begin(), S->queue.begin() + (long)batch.size());
             S->reserved_total = others + need;
             L.reserved = need;
+            L.hn = std::max(L.hn, n);
+            L.ha = std::max(L.ha, a);
             S->want_memory = false;
             break;
+          }
+          if (L.hn > 0 || L.reserved > 0) {
+            // the lane's own caches stand in the way: drop them and size the batch afresh
+            const size_t mine = L.reserved;
+            lk.unlock();
+            handle_trim(L.h);
+            lane_free_buffers(L);
+            lk.lock();
+            S->reserved_total -= mine;
+            L.reserved = 0;
+            L.hn = L.ha = 0;
+            continue;
           }
           // the head does not fit now (it fits an empty device: checked at submit): ask the idle
           // lanes to drop their caches and wait for running batches to finish
@@ -222,6 +241,7 @@ void lane_main(louvain_server_s* S, int idx) {
           lk.lock();
           S->reserved_total -= mine;
           L.reserved = 0;
+          L.hn = L.ha = 0;
           S->cv_work.notify_all();
           continue;
         }
@@ -231,10 +251,8 @@ void lane_main(louvain_server_s* S, int idx) {
     const double t0 = now_ms();
     for (Request* r : batch) r->t_start = t0;
     {
-      // the handle may use the reservation minus the lane's own union buffers
-      int64_t n = 0, a = 0;
-      for (Request* r : batch) { n += r->n; a += r->a; }
-      const size_t lane_bytes = (size_t)(12 * (n + 1) + 8 * a);
+      // the handle may use the reservation minus the lane's own union buffers (their largest size)
+      const size_t lane_bytes = (size_t)(12 * (L.hn + 1) + 8 * L.ha);
       handle_set_budget(L.h, need > lane_bytes ? need - lane_bytes : 1);
     }
     louvain_status st = run_lane_batch(S, L, batch, res);
@@ -252,6 +270,7 @@ void lane_main(louvain_server_s* S, int idx) {
     if (st != LOUVAIN_OK || held > share) {
       handle_trim(L.h);
       lane_free_buffers(L);
+      L.hn = L.ha = 0;
     }
     {
       std::lock_guard<std::mutex> lk(S->mu);

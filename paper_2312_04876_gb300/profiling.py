@@ -12,6 +12,9 @@ bucket, the giant-row kernels by phase), and writes
 
     python -m paper_2312_04876_gb300.profiling launches.csv --workload rmat22 --mode fast \
         --command "<the ncu command>" --md profiles/x.md [--traffic-json profiles/traffic_rmat22_fast.json]
+
+With --full, the csv is the raw page of one full capture (`ncu -i r.ncu-rep --page raw --csv`)
+and the Markdown lists its key counters per launch (duration, DRAM bytes, occupancy, stalls).
 """
 from __future__ import annotations
 
@@ -182,6 +185,52 @@ def traffic_json(s: dict, workload: str, mode: str, command: str, source_root: s
             "classes": classes}
 
 
+# metrics of a full (`--set full`) report worth a line in a summary, with their labels
+FULL_METRICS = [
+    ("gpu__time_duration.sum", "duration"),
+    ("dram__bytes_read.sum", "DRAM read"),
+    ("dram__bytes_write.sum", "DRAM write"),
+    ("gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed", "DRAM throughput % of peak"),
+    ("lts__t_sector_hit_rate.pct", "L2 hit rate %"),
+    ("lts__throughput.avg.pct_of_peak_sustained_elapsed", "L2 throughput % of peak"),
+    ("sm__warps_active.avg.pct_of_peak_sustained_active", "warps active % of peak"),
+    ("sm__maximum_warps_per_active_cycle_pct", "occupancy limit %"),
+    ("launch__registers_per_thread", "registers/thread"),
+    ("launch__shared_mem_per_block_dynamic", "dynamic shared memory/block"),
+    ("launch__grid_size", "grid"),
+    ("launch__block_size", "block"),
+    ("smsp__inst_executed.sum", "warp instructions"),
+    ("smsp__issue_active.avg.pct_of_peak_sustained_active", "issue active %"),
+    ("smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio", "stall long scoreboard / issue"),
+    ("smsp__average_warps_issue_stalled_short_scoreboard_per_issue_active.ratio", "stall short scoreboard / issue"),
+    ("smsp__average_warps_issue_stalled_barrier_per_issue_active.ratio", "stall barrier / issue"),
+    ("smsp__average_warps_issue_stalled_wait_per_issue_active.ratio", "stall wait / issue"),
+    ("smsp__average_warps_issue_stalled_mio_throttle_per_issue_active.ratio", "stall MIO throttle / issue"),
+    ("sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active", "tensor pipe active %"),
+]
+
+
+def full_report_markdown(raw_csv: str, title: str, command: str, note: str = "") -> str:
+    """Summary of `ncu -i <report> --page raw --csv` output: one column per captured launch."""
+    rows = [r for r in csv.reader(raw_csv.splitlines()) if r]
+    hdr, units, data = rows[0], rows[1], rows[2:]
+    col = {name: k for k, name in enumerate(hdr)}
+    out = [f"# {title}", "", "Command (run from the repository root on one GB300):", "", "```", command, "```", ""]
+    if note:
+        out += [note, ""]
+    kname = col.get("Kernel Name")
+    out += ["| metric | " + " | ".join(f"launch {k + 1}" for k in range(len(data))) + " | unit |",
+            "|---|" + "---:|" * len(data) + "---|"]
+    if kname is not None:
+        out.append("| kernel | " + " | ".join(f"`{short_name(r[kname]).split('(')[0]}`" for r in data) + " | |")
+    for metric, label in FULL_METRICS:
+        k = col.get(metric)
+        if k is None:
+            continue
+        out.append(f"| {label} | " + " | ".join(r[k] for r in data) + f" | {units[k]} |")
+    return "\n".join(out) + "\n"
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("csv")
@@ -192,7 +241,17 @@ def main(argv=None):
     ap.add_argument("--traffic-json")
     ap.add_argument("--source-root", default=ROOT,
                     help="tree whose CUDA sources ran under ncu (e.g. a checkout of the profiled commit)")
+    ap.add_argument("--full", action="store_true",
+                    help="csv is `ncu -i <report> --page raw --csv` of a full capture: write its summary to --md")
+    ap.add_argument("--title", default="")
+    ap.add_argument("--note", default="")
     a = ap.parse_args(argv)
+    if a.full:
+        with open(a.csv) as f:
+            text = full_report_markdown(f.read(), a.title or a.workload, a.command, a.note)
+        with open(a.md, "w") as f:
+            f.write(text)
+        return
     s = summarise(read_launches(a.csv))
     if a.md:
         with open(a.md, "w") as f:

@@ -106,6 +106,10 @@ typedef struct {
   float ms_colour, ms_move, ms_aggregate, ms_other;
   int32_t colours;               /* deterministic mode: colour classes of the pass (0 in fast mode) */
   int32_t colour_rounds;         /* deterministic mode: Jones-Plassmann rounds that coloured vertices */
+  float ms_graph;                /* host time of capturing the pass's iteration graphs and making them
+                                    executable (the device waits meanwhile); 0 with profile = 1 */
+  int32_t graphs_instantiated;   /* of those graphs, how many were instantiated anew (the others
+                                    updated a cached executable of the same shape in place) */
 } louvain_pass_stats;
 
 typedef struct {
@@ -178,12 +182,13 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
                                  louvain_graph_result* results, louvain_result* res);
 
 /* Autotuning (a systems extension; the paper tunes nothing at run time).  Times full runs of the
- * given graph (device time, best of `reps`) under every combination of the performance knobs that
+ * given graph (device time, best of `reps`, each candidate after one untimed run that builds its
+ * iteration graphs and buffers) under every combination of the performance knobs that
  * leave the arithmetic unchanged -- giant_min_degree in {4096, 2048} (which kernel takes rows of
  * 2049..4096 arcs: the one-block 64 KB table or the multi-block giant path), lm_blocks_per_sm in
  * {16, 4} and compact in {1, 0} -- and writes *p with the fastest combination into *tuned (other
  * fields copied; *best_ms its time).  In deterministic mode every candidate returns the same
- * membership; d_membership (device, n entries) receives the last run's.  Costs 8 x reps runs. */
+ * membership; d_membership (device, n entries) receives the last run's.  Costs 8 x (reps + 1) runs. */
 louvain_status louvain_autotune(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
                                 const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
                                 const louvain_params* p, void* stream, int32_t* d_membership, int32_t reps,

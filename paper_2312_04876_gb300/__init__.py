@@ -168,7 +168,8 @@ def _stats_list(st, n) -> list:
     return [dict(pass_=s.pass_, iterations=s.iterations, moves=s.moves, n_vertices=s.n_vertices, n_arcs=s.n_arcs,
                  n_communities=s.n_communities, modularity=s.modularity, ms_colour=s.ms_colour, ms_move=s.ms_move,
                  ms_aggregate=s.ms_aggregate, ms_other=s.ms_other, colours=s.colours,
-                 colour_rounds=s.colour_rounds) for s in st[:n]]
+                 colour_rounds=s.colour_rounds, ms_graph=s.ms_graph,
+                 graphs_instantiated=s.graphs_instantiated) for s in st[:n]]
 
 
 class Louvain:

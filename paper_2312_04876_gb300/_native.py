@@ -28,7 +28,8 @@ class PassStats(ctypes.Structure):
                 ("n_vertices", ctypes.c_int64), ("n_arcs", ctypes.c_int64), ("n_communities", ctypes.c_int64),
                 ("modularity", ctypes.c_double), ("ms_colour", ctypes.c_float), ("ms_move", ctypes.c_float),
                 ("ms_aggregate", ctypes.c_float), ("ms_other", ctypes.c_float), ("colours", ctypes.c_int32),
-                ("colour_rounds", ctypes.c_int32)]
+                ("colour_rounds", ctypes.c_int32), ("ms_graph", ctypes.c_float),
+                ("graphs_instantiated", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):

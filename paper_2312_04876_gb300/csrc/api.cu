@@ -7,6 +7,7 @@
 // reused (the paper's preallocated CSRs, Section 4.1.7-8): two arc buffers (a holey merge target
 // and a dense compaction target), two sets of row descriptors, and per-vertex state.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -61,6 +62,9 @@ struct Workspace {
   unsigned* gt_bits = nullptr;
   GlobalTable gt;
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
+  DevAlloc desc_alloc;        // step records and the pass GraphView of captured iterations
+  int64_t* desc = nullptr;
+  int64_t desc_cap = 0;       // int64 words
   int32_t* glist = nullptr;   // [gcap] giant vertices of a pass, class by class
   int32_t* csz = nullptr;     // [n] table size of each giant community
   GiantPlan gp, gpv;          // plans of giant vertices / communities and of giant members
@@ -127,24 +131,30 @@ struct louvain_handle_s {
   cudaStream_t cap = nullptr;  // capture origin (the caller's stream may be the legacy one)
   std::vector<cudaEvent_t> fork_ev, join_ev;
   bool use_graphs = true;
-  // Executable graphs of earlier phases, updated in place (cudaGraphExecUpdate, ~0.1 ms for a
-  // 16-class iteration) when a new capture has the same topology, instead of instantiated anew
-  // (~2.6 ms); least recently used evicted beyond kExecCache.
+  // Executable graphs of earlier phases, keyed by everything their launches depend on: an
+  // iteration with the same key replays one with no capture at all; a full cache updates one of the
+  // same topology in place (cudaGraphExecUpdate, ~0.1 ms for a 16-class iteration) instead of
+  // instantiating anew (~2.6 ms); least recently used evicted beyond kExecCache.
   struct CachedExec {
     cudaGraphExec_t e = nullptr;
     size_t nodes = 0;
     uint64_t used = 0;
+    int64_t launches = 0;          // kernels per replay
+    std::vector<int64_t> key;      // everything the captured launches depend on (see iteration_key)
   };
   std::vector<CachedExec> execs;
   uint64_t exec_clock = 0;
+  int64_t* dpin = nullptr;         // pinned staging of the step records
+  int64_t dpin_cap = 0;
 };
 
-constexpr size_t kExecCache = 8;
+constexpr size_t kExecCache = 16;
 
 namespace {
 
 size_t total_bytes(const Workspace& ws) {
-  return ws.core.bytes + ws.keys_alloc.bytes + ws.gt_alloc.bytes + ws.in_alloc.bytes + ws.batch_alloc.bytes;
+  return ws.core.bytes + ws.keys_alloc.bytes + ws.gt_alloc.bytes + ws.in_alloc.bytes + ws.batch_alloc.bytes +
+         ws.desc_alloc.bytes;
 }
 
 void free_all(DevAlloc& a) {
@@ -289,6 +299,32 @@ louvain_status ensure_pool(louvain_handle h, Ctx& c, int64_t slots) {
     gp->vals = ws.gt.vals;
     gp->bits = ws.gt_bits;
     gp->pool_slots = ws.gt_slots_total;
+  }
+  return LOUVAIN_OK;
+}
+
+// Device and pinned buffers for the step records of captured iterations (`words` int64).
+louvain_status ensure_desc(louvain_handle h, int64_t words) {
+  Workspace& ws = h->ws;
+  if (words > ws.desc_cap) {
+    const int64_t cap = words < 4096 ? 4096 : 2 * words;
+    free_all(ws.desc_alloc);
+    ws.desc = nullptr;
+    ws.desc_cap = 0;
+    if (!dalloc(h, ws.desc_alloc, &ws.desc, cap)) return set_err(h, LOUVAIN_ERR_OOM, "step-record allocation failed");
+    ws.desc_cap = cap;
+  }
+  if (words > h->dpin_cap) {
+    // the previous records' copy has completed: the host synchronised since it was enqueued
+    if (h->dpin) cudaFreeHost(h->dpin);
+    h->dpin = nullptr;
+    h->dpin_cap = 0;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h->dpin), (size_t)ws.desc_cap * sizeof(int64_t),
+                      cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(h, LOUVAIN_ERR_OOM, "pinned host allocation failed");
+    }
+    h->dpin_cap = ws.desc_cap;
   }
   return LOUVAIN_OK;
 }
@@ -461,13 +497,21 @@ struct ClassStep {
 // Launches one iteration (every step; the convergence test at the end).  With `streams` the
 // degree buckets of a step fork to one side stream each and join before the next step (used
 // while capturing a CUDA graph); otherwise they run in order on c.s with per-launch profiling.
+// With `recs` (the device step records of `steps`) every launch reads its vertex range from device
+// memory, so the captured graph serves any pass over the same arrays whose steps launch the same
+// kernels; list bases are then ws.perm and gbase (the giant list), and the graph goes in with n = 0
+// (the captured kernels do not read it), so that only its arrays tie a graph to a pass.
 template <class M>
 void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st,
                        const std::vector<ClassStep>& steps, const int32_t* glist, bool det, bool pruning,
-                       GraphCtl* gc, int32_t n_graphs, bool streams) {
+                       GraphCtl* gc, int32_t n_graphs, bool streams, const int64_t* recs = nullptr,
+                       const int32_t* gbase = nullptr) {
   Workspace& ws = h->ws;
+  GraphView<typename M::w_t> gk = g;
+  if (recs) gk.n = 0;
   for (size_t k = 0; k < steps.size(); k++) {
     const ClassStep& cs = steps[k];
+    const int64_t* rk = recs ? recs + k * kStepWords : nullptr;
     if (streams) cudaEventRecord(h->fork_ev[k], c.s);
     for (int b = 0; b < kNumBuckets; b++) {
       const bool giant = b == kNumBuckets - 1;
@@ -478,8 +522,12 @@ void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t
         cb.s = h->side[b];
         cb.launches = 0;
         cudaStreamWaitEvent(cb.s, h->fork_ev[k], 0);
-        if (!giant) move_bucket<M>(cb, b, g, st, ws.perm + cs.start[b], cnt, ws.gt, !det, pruning);
-        else giant_move<M>(cb, g, st, glist, cs.g0, cs.g1, ws.gp, !det, pruning);
+        if (!giant)
+          move_bucket<M>(cb, b, gk, st, rk ? ws.perm : ws.perm + cs.start[b], cnt, ws.gt, !det, pruning,
+                         rk ? rk + 2 * b : nullptr);
+        else
+          giant_move<M>(cb, gk, st, rk ? gbase : glist, cs.g0, cs.g1, ws.gp, !det, pruning,
+                        rk ? rk + kStepGiant : nullptr);
         c.launches += cb.launches;
         cudaEventRecord(h->join_ev[k * kNumBuckets + b], cb.s);
         cudaStreamWaitEvent(c.s, h->join_ev[k * kNumBuckets + b], 0);
@@ -492,12 +540,70 @@ void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t
     }
     if (det && cs.apply_count > 0) {
       const int pm = streams ? -1 : prof_begin(h, c);
-      move_apply<M>(c, st, ws.perm + cs.apply_start, cs.apply_count);
+      move_apply<M>(c, st, rk ? ws.perm : ws.perm + cs.apply_start, cs.apply_count, rk ? rk + kStepApply : nullptr);
       if (!streams) prof_end(h, c, kApply, pm);
     }
   }
   if (gc) batch_finish<M>(c, ws.ctrl, gc, n_graphs);
   else move_finish<M>(c, ws.ctrl);
+}
+
+// Everything a captured iteration's launches depend on besides its device step records: the
+// kernel instances (mode, schedule, which buckets / giant chains / applies each step launches),
+// grid sizes, and every pointer and scalar passed by value.  Equal keys mean equal launches.
+template <class M>
+std::vector<int64_t> iteration_key(louvain_handle h, const Ctx& c, const GraphView<typename M::w_t>& g,
+                                   const PassState<M>& st, const std::vector<ClassStep>& steps, const int64_t* recs,
+                                   const int32_t* gbase, bool det, bool pruning, GraphCtl* gc, int32_t n_graphs) {
+  static_assert(sizeof(PassState<M>) % 8 == 0 && sizeof(GiantPlan) % 8 == 0, "pointer-only records");
+  const Workspace& ws = h->ws;
+  std::vector<int64_t> k = {M::is_fp ? 1 : 0, det ? 1 : 0, pruning ? 1 : 0, n_graphs, (int64_t)(intptr_t)gc,
+                            c.num_sms, c.lm_blocks_per_sm, c.giant_min, (int64_t)(intptr_t)ws.perm,
+                            (int64_t)(intptr_t)gbase, (int64_t)(intptr_t)recs, (int64_t)(intptr_t)ws.desc,
+                            (int64_t)(intptr_t)ws.gt.keys, (int64_t)(intptr_t)ws.gt.vals, ws.gt.slots_per_block,
+                            (int64_t)(intptr_t)g.rbeg, (int64_t)(intptr_t)g.rend, (int64_t)(intptr_t)g.tg,
+                            (int64_t)(intptr_t)g.w, (int64_t)steps.size()};
+  const size_t n0 = k.size();
+  k.resize(n0 + sizeof(PassState<M>) / 8 + sizeof(GiantPlan) / 8);
+  std::memcpy(&k[n0], &st, sizeof(PassState<M>));
+  std::memcpy(&k[n0 + sizeof(PassState<M>) / 8], &ws.gp, sizeof(GiantPlan));
+  for (const ClassStep& cs : steps) {
+    int64_t mask = 0;
+    for (int b = 0; b < kNumBuckets - 1; b++)
+      if (cs.count[b] > 0) mask |= 1 << b;
+    if (cs.g1 > cs.g0) mask |= 1 << (kNumBuckets - 1);
+    if (det && cs.apply_count > 0) mask |= 1 << kNumBuckets;
+    k.push_back(mask);
+  }
+  return k;
+}
+
+// Host image of the step records of `steps` (kStepWords each; the giant list offset from its base).
+void write_step_records(const std::vector<ClassStep>& steps, int64_t goff, int64_t* out) {
+  for (size_t k = 0; k < steps.size(); k++) {
+    int64_t* r = out + k * kStepWords;
+    std::memset(r, 0, sizeof(int64_t) * kStepWords);
+    const ClassStep& cs = steps[k];
+    for (int b = 0; b < kNumBuckets - 1; b++) {
+      r[2 * b] = cs.start[b];
+      r[2 * b + 1] = cs.count[b];
+    }
+    r[kStepGiant] = goff;
+    r[kStepGiant + 1] = cs.g0;
+    r[kStepGiant + 2] = cs.g1;
+    r[kStepApply] = cs.apply_start;
+    r[kStepApply + 1] = cs.apply_count;
+  }
+}
+
+// The cached executable with exactly this key, or null.
+louvain_handle_s::CachedExec* find_exec(louvain_handle h, const std::vector<int64_t>& key) {
+  for (auto& x : h->execs)
+    if (x.key == key) {
+      x.used = ++h->exec_clock;
+      return &x;
+    }
+  return nullptr;
 }
 
 // Captures one iteration into an executable CUDA graph owned by the handle's cache (launches
@@ -506,7 +612,8 @@ template <class M>
 louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<typename M::w_t>& g, const PassState<M>& st,
                                  const std::vector<ClassStep>& steps, const int32_t* glist, bool det, bool pruning,
                                  GraphCtl* gc, int32_t n_graphs, cudaGraphExec_t exclude, cudaGraphExec_t* exec,
-                                 int64_t* launches) {
+                                 int64_t* launches, int32_t* instantiated, const int64_t* recs,
+                                 const int32_t* gbase, const std::vector<int64_t>& key) {
   *exec = nullptr;
   if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cuda_err(h, cudaGetLastError(), "capture stream creation");
@@ -531,7 +638,7 @@ louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<type
   move_prepare();
   cudaError_t e = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_err(h, e, "graph capture begin");
-  enqueue_iteration<M>(h, c, g, st, steps, glist, det, pruning, gc, n_graphs, true);
+  enqueue_iteration<M>(h, c, g, st, steps, glist, det, pruning, gc, n_graphs, true, recs, gbase);
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(c.s, &graph);
   *launches = c.launches;
@@ -539,19 +646,23 @@ louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<type
     if (graph) cudaGraphDestroy(graph);
     return cuda_err(h, e, "graph capture end");
   }
-  // an executable of the same shape from an earlier phase (not `exclude`, the other graph of this
-  // phase), most recently used first; all work launched from it has completed (the host synchronised
-  // on the class offsets before this capture)
+  // While the cache has room the graph gets an executable of its own (its key then hits from the
+  // next run on).  A full cache updates, in place, an executable of the same node count that is not
+  // `exclude` (the other graph of this phase), least recently used first; all work launched from it
+  // has completed (the host synchronised on the class offsets before this capture).
   size_t nodes = 0;
   cudaGraphGetNodes(graph, nullptr, &nodes);
   std::vector<size_t> cand;
-  for (size_t k = 0; k < h->execs.size(); k++)
-    if (h->execs[k].nodes == nodes && h->execs[k].e != exclude) cand.push_back(k);
-  std::sort(cand.begin(), cand.end(), [&](size_t a, size_t b) { return h->execs[a].used > h->execs[b].used; });
+  if (h->execs.size() >= kExecCache)
+    for (size_t k = 0; k < h->execs.size(); k++)
+      if (h->execs[k].nodes == nodes && h->execs[k].e != exclude) cand.push_back(k);
+  std::sort(cand.begin(), cand.end(), [&](size_t a, size_t b) { return h->execs[a].used < h->execs[b].used; });
   for (size_t k : cand) {
     cudaGraphExecUpdateResultInfo info;
     if (cudaGraphExecUpdate(h->execs[k].e, graph, &info) == cudaSuccess) {
       h->execs[k].used = ++h->exec_clock;
+      h->execs[k].launches = *launches;
+      h->execs[k].key = key;
       *exec = h->execs[k].e;
       cudaGraphDestroy(graph);
       return LOUVAIN_OK;
@@ -564,6 +675,7 @@ louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<type
     *exec = nullptr;
     return cuda_err(h, e, "graph instantiation");
   }
+  ++*instantiated;
   if (h->execs.size() >= kExecCache) {
     size_t lru = h->execs.size();
     for (size_t k = 0; k < h->execs.size(); k++)
@@ -571,7 +683,7 @@ louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<type
     cudaGraphExecDestroy(h->execs[lru].e);
     h->execs.erase(h->execs.begin() + (std::ptrdiff_t)lru);
   }
-  h->execs.push_back({*exec, nodes, ++h->exec_clock});
+  h->execs.push_back({*exec, nodes, ++h->exec_clock, *launches, key});
   return LOUVAIN_OK;
 }
 
@@ -582,7 +694,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
                                 int64_t giant_slots, const louvain_params& p, int32_t pass, double tau, int32_t* li,
                                 int64_t* moves, size_t ev_colour_done, GraphCtl* gc = nullptr,
                                 const int32_t* vg = nullptr, int32_t n_graphs = 0, int32_t* colours = nullptr,
-                                int32_t* colour_rounds = nullptr) {
+                                int32_t* colour_rounds = nullptr, float* ms_graph = nullptr,
+                                int32_t* graphs_new = nullptr) {
   Workspace& ws = h->ws;
   PassState<M> st{reinterpret_cast<typename M::a_t*>(ws.K), reinterpret_cast<typename M::a_t*>(ws.Sig), ws.Cp,
                   ws.flags, ws.csize, ws.mv_from, ws.mv_to, ws.ctrl};
@@ -698,21 +811,58 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   const bool pruning = p.pruning != 0;
   int enq = 0;
   const int batch = det ? 2 : 4;
-  // Without per-launch profiling, an iteration is captured once per pass as a CUDA graph -- per
-  // step a fork to one stream per degree bucket and a join -- and replayed for every iteration.
+  // Without per-launch profiling an iteration runs as a CUDA graph -- per step a fork to one stream
+  // per degree bucket and a join -- whose launches read their vertex ranges from the step records
+  // copied here; a cached executable with the same key serves again with no capture.
   cudaGraphExec_t g_first = nullptr, g_rest = nullptr;
   int64_t l_first = 0, l_rest = 0;
   const bool graphs = !h->prof.on && h->use_graphs;
-  if (graphs && (s = capture_iteration<M>(h, c, g, st, first, glist, det, pruning, gc, n_graphs, nullptr, &g_first,
-                                          &l_first)) != LOUVAIN_OK)
-    return s;
+  int32_t n_new = 0;
+  double host_ms = 0.0;
+  auto now = [] { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count(); };
+  double t0 = now();
+  const int32_t* gbase = det ? ws.glist : ws.perm;  // giant lists: ws.glist (deterministic) or inside perm
+  const int64_t* recs_first = nullptr;
+  const int64_t* recs_rest = nullptr;
+  std::vector<int64_t> key_rest;
+  if (graphs) {
+    const int64_t words = (int64_t)(first.size() + rest.size()) * kStepWords;
+    if ((s = ensure_desc(h, words)) != LOUVAIN_OK) return s;
+    int64_t* hp = h->dpin;
+    const int64_t goff = glist - gbase;
+    write_step_records(first, goff, hp);
+    write_step_records(rest, goff, hp + first.size() * kStepWords);
+    cudaMemcpyAsync(ws.desc, hp, (size_t)words * sizeof(int64_t), cudaMemcpyHostToDevice, c.s);
+    recs_first = ws.desc;
+    recs_rest = ws.desc + first.size() * kStepWords;
+    const std::vector<int64_t> key =
+        iteration_key<M>(h, c, g, st, first, recs_first, gbase, det, pruning, gc, n_graphs);
+    if (auto* x = find_exec(h, key)) {
+      g_first = x->e;
+      l_first = x->launches;
+    } else {
+      if ((s = capture_iteration<M>(h, c, g, st, first, glist, det, pruning, gc, n_graphs, nullptr, &g_first, &l_first,
+                                    &n_new, recs_first, gbase, key)) != LOUVAIN_OK)
+        return s;
+    }
+    if (rest.size() != first.size())
+      key_rest = iteration_key<M>(h, c, g, st, rest, recs_rest, gbase, det, pruning, gc, n_graphs);
+  }
+  host_ms += now() - t0;
   while (true) {
     for (int k = 0; k < batch && enq < p.max_iterations; k++, enq++) {
       const bool is_first = enq == 0 || rest.size() == first.size();
-      if (graphs && !is_first && !g_rest &&
-          (s = capture_iteration<M>(h, c, g, st, rest, glist, det, pruning, gc, n_graphs, g_first, &g_rest,
-                                    &l_rest)) != LOUVAIN_OK)
-        return s;  // captured while the first iteration runs
+      if (graphs && !is_first && !g_rest) {  // found or captured while the first iteration runs
+        t0 = now();
+        if (auto* x = find_exec(h, key_rest)) {
+          g_rest = x->e;
+          l_rest = x->launches;
+        } else if ((s = capture_iteration<M>(h, c, g, st, rest, glist, det, pruning, gc, n_graphs, g_first, &g_rest,
+                                             &l_rest, &n_new, recs_rest, gbase, key_rest)) != LOUVAIN_OK) {
+          return s;
+        }
+        host_ms += now() - t0;
+      }
       const cudaGraphExec_t ex = is_first ? g_first : g_rest;
       if (ex) {
         cudaGraphLaunch(ex, c.s);
@@ -727,6 +877,8 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     if (hc->done || enq >= p.max_iterations) {
       *li = hc->iterations;
       *moves = (int64_t)hc->moves_pass;
+      if (ms_graph) *ms_graph = (float)host_ms;
+      if (graphs_new) *graphs_new = n_new;
       return LOUVAIN_OK;
     }
   }
@@ -816,9 +968,10 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
     // (a2-a5) local-moving phase
     int32_t li = 0;
     int64_t moves = 0;
-    int32_t ncolours = 0, nrounds = 0;
+    int32_t ncolours = 0, nrounds = 0, ngraphs = 0;
+    float gms = 0.f;
     if ((s = local_move_phase<M>(h, c, g, hb, gslots, p, lp, tau, &li, &moves, e0 + 2, nullptr, nullptr, 0, &ncolours,
-                                 &nrounds)) != LOUVAIN_OK)
+                                 &nrounds, &gms, &ngraphs)) != LOUVAIN_OK)
       return s;
     cudaEventRecord(h->events[e0 + 3], c.s);
     pending = true;
@@ -842,6 +995,7 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
       ps->pass = lp; ps->iterations = li; ps->moves = moves; ps->n_vertices = n_cur; ps->n_arcs = g_arcs;
       ps->n_communities = nc; ps->modularity = pass_q;
       ps->colours = ncolours; ps->colour_rounds = nrounds;
+      ps->ms_graph = gms; ps->graphs_instantiated = ngraphs;
       if (n_stats) *n_stats = lp + 1;
     }
     const bool stop = li <= 1 || (double)nc / (double)n_cur > p.aggregation_tolerance;
@@ -1041,7 +1195,8 @@ louvain_status check_graph_args(louvain_handle h, int64_t n, int64_t n_arcs, con
 // ------------------------------------------------------------------ autotuning
 // Candidates of the performance knobs that leave the arithmetic unchanged: the giant-row
 // threshold (which kernel takes rows of 2049..4096 arcs), the local-move grid cap and super-graph
-// compaction.  Each is timed by full runs (device time, best of `reps`); the fastest wins.
+// compaction.  Each is timed by full runs (device time, best of `reps`) after one untimed run that
+// builds its iteration graphs and buffers, as a run in steady use finds them; the fastest wins.
 template <class RunFn>
 static louvain_status autotune_impl(louvain_handle h, const louvain_params* p, int32_t reps, RunFn run,
                                     louvain_params* tuned, float* best_ms) {
@@ -1059,6 +1214,9 @@ static louvain_status autotune_impl(louvain_handle h, const louvain_params* p, i
         q.compact = cp;
         q.profile = 0;
         float t = -1.f;
+        float warm = 0.f;
+        louvain_status s0 = run(q, &warm);
+        if (s0 != LOUVAIN_OK) return s0;
         for (int32_t r = 0; r < (reps > 0 ? reps : 1); r++) {
           float ms = 0.f;
           louvain_status s = run(q, &ms);
@@ -1089,6 +1247,9 @@ void handle_trim(louvain_handle h) {
   free_all(ws.gt_alloc);
   free_all(ws.in_alloc);
   free_all(ws.batch_alloc);
+  free_all(ws.desc_alloc);
+  ws.desc = nullptr;
+  ws.desc_cap = 0;
   ws.n_cap = ws.a_cap = -1;
   ws.key_cap = 0;
   ws.gt_slots_total = 0;
@@ -1175,6 +1336,7 @@ void louvain_destroy(louvain_handle h) {
   for (auto& x : h->execs) cudaGraphExecDestroy(x.e);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->pin) cudaFreeHost(h->pin);
+  if (h->dpin) cudaFreeHost(h->dpin);
   delete h;
 }
 

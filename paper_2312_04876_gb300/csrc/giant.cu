@@ -210,14 +210,26 @@ __device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* tk, H* tv,
   return ok;
 }
 
+// A captured iteration passes its giant range (list offset, k0, k1) in device memory; eager
+// launches pass it as arguments (krng null).
+__device__ __forceinline__ void giant_range(const int64_t* krng, const int32_t*& list, int64_t& k0, int64_t& k1) {
+  if (krng) {
+    list += krng[0];
+    k0 = krng[1];
+    k1 = krng[2];
+  }
+}
+
 // ---------------------------------------------------------------- local move: activation
 // Giants [k0, k1) of the class: active iff their graph has not converged and (pruning) their flag
 // is set, which is then cleared (processed).  Also resets K_i->d and the moved marks, and counts
 // list entries / processed vertices / arcs.
 template <class W>
 __global__ void k_glm_activate(GraphView<W> g, const int32_t* list, int64_t k0, int64_t k1, uint8_t* flags,
-                               int pruning, const GraphCtl* gc, const int32_t* vg, GiantPlan p, Ctrl* ctrl) {
+                               int pruning, const GraphCtl* gc, const int32_t* vg, GiantPlan p, Ctrl* ctrl,
+                               const int64_t* krng) {
   if (*(volatile int32_t*)&ctrl->done) return;
+  giant_range(krng, list, k0, k1);
   unsigned long long act = 0, arcs = 0;
   for (int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < k1; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = list[k];
@@ -249,11 +261,13 @@ __global__ void k_glm_activate(GraphView<W> g, const int32_t* list, int64_t k0, 
 // and table updates (U memory requests in flight per thread).
 template <class M>
 __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t> g, const int32_t* list, int64_t k0,
-                                                       int64_t k1, const int32_t* Cp, GiantPlan p, Ctrl* ctrl) {
+                                                       int64_t k1, const int32_t* Cp, GiantPlan p, Ctrl* ctrl,
+                                                       const int64_t* krng) {
   typedef typename M::h_t H;
   constexpr int U = kLmChunk / kBlock;  // 2
   __shared__ H red[32];
   if (*(volatile int32_t*)&ctrl->done) return;
+  giant_range(krng, list, k0, k1);
   const int64_t q0 = p.chunk_off[k0], q1 = p.chunk_off[k1];
   bool ok = true;
   for (int64_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
@@ -299,11 +313,13 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
 template <class M>
 __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_t k0, int64_t k1, const int32_t* Cp,
                                                      const typename M::a_t* K, const typename M::a_t* Sig,
-                                                     GiantPlan p, Ctrl* ctrl, const GraphCtl* gc, const int32_t* vg) {
+                                                     GiantPlan p, Ctrl* ctrl, const GraphCtl* gc, const int32_t* vg,
+                                                     const int64_t* krng) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
   if (*(volatile int32_t*)&ctrl->done) return;
+  giant_range(krng, list, k0, k1);
   const int64_t r0 = p.slice_off[k0], r1 = p.slice_off[k1];
   const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
   const int lane = threadIdx.x & 31;
@@ -378,11 +394,12 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
 // ---------------------------------------------------------------- local move: decide (+ apply)
 template <class M>
 __global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int64_t k0, int64_t k1, PassState<M> st,
-                                                       GiantPlan p, int fast) {
+                                                       GiantPlan p, int fast, const int64_t* krng) {
   typedef typename M::a_t A;
   typedef typename M::s_t S;
   Ctrl* ctrl = st.ctrl;
   if (*(volatile int32_t*)&ctrl->done) return;
+  giant_range(krng, list, k0, k1);
   unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
   double acc_f = 0.0;
   const int lane = threadIdx.x & 31;
@@ -448,9 +465,10 @@ __global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int6
 // ---------------------------------------------------------------- local move: mark neighbours
 template <class W>
 __global__ void __launch_bounds__(kBlock) k_glm_mark(GraphView<W> g, const int32_t* list, int64_t k0, int64_t k1,
-                                                     uint8_t* flags, GiantPlan p, Ctrl* ctrl) {
+                                                     uint8_t* flags, GiantPlan p, Ctrl* ctrl, const int64_t* krng) {
   constexpr int U = kLmChunk / kBlock;
   if (*(volatile int32_t*)&ctrl->done) return;
+  giant_range(krng, list, k0, k1);
   const int64_t q0 = p.chunk_off[k0], q1 = p.chunk_off[k1];
   unsigned long long marks = 0;
   for (int64_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
@@ -483,17 +501,20 @@ void giant_move_plan(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t*
 
 template <class M>
 void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t k0,
-                int64_t k1, const GiantPlan& p, bool fast, bool pruning) {
-  if (k1 <= k0) return;
+                int64_t k1, const GiantPlan& p, bool fast, bool pruning, const int64_t* krng) {
+  if (k1 <= k0 && !krng) return;
   const int grid = c.num_sms * (c.lm_blocks_per_sm < 8 ? c.lm_blocks_per_sm : 8);
-  k_glm_activate<typename M::w_t><<<grid_for(k1 - k0, kBlock, c.num_sms * 2), kBlock, 0, c.s>>>(
-      g, list, k0, k1, st.flags, pruning ? 1 : 0, st.gc, st.vg, p, st.ctrl);
-  k_glm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.Cp, p, st.ctrl);
-  k_glm_scan<M><<<grid, kBlock, 0, c.s>>>(list, k0, k1, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg);
-  k_glm_decide<M><<<grid_for(k1 - k0, kBlock / 32, c.num_sms * 2), kBlock, 0, c.s>>>(list, k0, k1, st, p, fast ? 1 : 0);
+  // a device-resident range has no host count: the per-giant kernels take their cap
+  const int ga = krng ? c.num_sms * 2 : grid_for(k1 - k0, kBlock, c.num_sms * 2);
+  const int gd = krng ? c.num_sms * 2 : grid_for(k1 - k0, kBlock / 32, c.num_sms * 2);
+  k_glm_activate<typename M::w_t><<<ga, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, pruning ? 1 : 0, st.gc, st.vg, p,
+                                                          st.ctrl, krng);
+  k_glm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.Cp, p, st.ctrl, krng);
+  k_glm_scan<M><<<grid, kBlock, 0, c.s>>>(list, k0, k1, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg, krng);
+  k_glm_decide<M><<<gd, kBlock, 0, c.s>>>(list, k0, k1, st, p, fast ? 1 : 0, krng);
   c.launches += 4;
   if (pruning) {
-    k_glm_mark<typename M::w_t><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, p, st.ctrl);
+    k_glm_mark<typename M::w_t><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, p, st.ctrl, krng);
     c.launches++;
   }
 }
@@ -780,9 +801,9 @@ template void giant_compact<int32_t>(Ctx&, const int32_t*, int64_t, const int64_
 template void giant_compact<float>(Ctx&, const int32_t*, int64_t, const int64_t*, const int64_t*, const int64_t*,
                                    const int32_t*, const float*, int32_t*, float*, const GiantPlan&, Ctrl*);
 template void giant_move<IntMode>(Ctx&, const GraphView<int32_t>&, const PassState<IntMode>&, const int32_t*, int64_t,
-                                  int64_t, const GiantPlan&, bool, bool);
+                                  int64_t, const GiantPlan&, bool, bool, const int64_t*);
 template void giant_move<FpMode>(Ctx&, const GraphView<float>&, const PassState<FpMode>&, const int32_t*, int64_t,
-                                 int64_t, const GiantPlan&, bool, bool);
+                                 int64_t, const GiantPlan&, bool, bool, const int64_t*);
 template void giant_move_plan<IntMode>(Ctx&, const GraphView<int32_t>&, const int32_t*, int64_t, const GiantPlan&,
                                        Ctrl*);
 template void giant_move_plan<FpMode>(Ctx&, const GraphView<float>&, const int32_t*, int64_t, const GiantPlan&, Ctrl*);

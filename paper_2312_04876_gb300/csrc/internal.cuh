@@ -35,6 +35,16 @@ struct GraphView {
   const W* w = nullptr;
 };
 
+// Device-resident ranges of a captured local-moving iteration: one record of kStepWords int64 per
+// class step, written by the host before the iteration graph is launched, so one executable graph
+// serves every pass over the same arrays (the kernels read their vertex ranges here):
+//   [2b], [2b + 1]   start and count of degree bucket b < kNumBuckets - 1 in the perm list;
+//   [kStepGiant]     offset of the class-ordered giant list, then the giant range k0, k1 (plan indices);
+//   [kStepApply]     start and count of the deterministic Sigma apply.
+constexpr int kStepWords = 20;
+constexpr int kStepGiant = 12;
+constexpr int kStepApply = 16;
+
 // ---------------------------------------------------------------- prims.cu
 // Exclusive scan of in[0, n) into out[0, n) and out[n] = total; tile_tmp needs
 // scan_tmp_elems(n) int64 entries.  in == out allowed for int64 input.
@@ -115,14 +125,18 @@ struct GlobalTable {
 };
 
 // One bucket's decide (+ apply in fast mode) over list[0, count).
+// With `rng` (a step record's {start, count} of this bucket) the kernel reads its range there and
+// list is the base it is offset from; the grid is then the cap (blocks past the range return at
+// once).
 template <class M>
 void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
-                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning);
+                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning,
+                 const int64_t* rng = nullptr);
 // Shared-memory opt-ins of the local-move kernels (call before capturing launches into a graph).
 void move_prepare();
 // Deterministic mode: Sigma updates of the moves decided in list[0, count).
 template <class M>
-void move_apply(Ctx& c, const PassState<M>& st, const int32_t* list, int64_t count);
+void move_apply(Ctx& c, const PassState<M>& st, const int32_t* list, int64_t count, const int64_t* rng = nullptr);
 template <class M>
 void move_finish(Ctx& c, Ctrl* ctrl);
 
@@ -211,9 +225,10 @@ template <class M>
 void giant_move_plan(Ctx& c, const GraphView<typename M::w_t>& g, const int32_t* list, int64_t m, const GiantPlan& p,
                      Ctrl* ctrl);
 // Local moving of the giants list[k0, k1) of one colour / random class under that plan.
+// With `krng` (a step record's {list offset, k0, k1}) the range is read there.
 template <class M>
 void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>& st, const int32_t* list, int64_t k0,
-                int64_t k1, const GiantPlan& p, bool fast, bool pruning);
+                int64_t k1, const GiantPlan& p, bool fast, bool pruning, const int64_t* krng = nullptr);
 // Plan kernels (kind: see giant.cu); slices of 2^slice_log table slots.
 void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
                 const int64_t* cdeg, int64_t n_bound, const int32_t* Cp, int32_t* gix, int slice_log,

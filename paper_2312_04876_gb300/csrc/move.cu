@@ -31,6 +31,7 @@ struct LmArgs {
   int fast;
   int pruning;
   int bucket;
+  const int64_t* rng;  // device {start, count} of the list (a captured iteration), or null
 };
 
 // Block-wide reduction of the per-thread move accumulators into the control block.
@@ -79,7 +80,7 @@ __host__ __device__ constexpr int lm_block() {
 }
 
 template <class M, int G, int LOG, bool GLOBAL>
-__global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M> a) {
+__global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M> a) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
@@ -87,6 +88,15 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
   if (*(volatile int32_t*)&ctrl->done) return;
   constexpr int BS = lm_block<G, LOG>();
   constexpr int GPB = G <= 32 ? BS / G : 1;
+  // a captured iteration reads its list range from device memory (32-bit: counts and offsets are
+  // below 2^31); the graph's arrays stay kernel parameters
+  int32_t lo = 0, hi = (int32_t)a.count;  // list[lo, hi)
+  if (a.rng) {
+    lo = (int32_t)a.rng[0];
+    hi = lo + (int32_t)a.rng[1];
+  }
+  if (lo + (int)blockIdx.x * GPB >= hi) return;  // a fixed grid larger than this range
+  const GraphView<typename M::w_t>& g = a.g;
   constexpr int SL = GLOBAL ? 1 : (1 << LOG);
   constexpr int U = G >= 32 ? 4 : 2;  // arcs (and table slots) per lane per step
   extern __shared__ __align__(16) unsigned char lm_dyn[];  // GPB tables of SL (key, value) slots
@@ -114,13 +124,13 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
   }
   const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
   GraphCtl* const gcs = a.st.gc;
-  const int64_t n_cur = a.g.n;
+  const int64_t n_cur = g.n;
   unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
   double acc_f = 0.0;
   unsigned long long ctr[6] = {0, 0, 0, 0, 0, 0};  // list, processed, arcs, candidates, moves, marks
 
   const int64_t ngroups = (int64_t)gridDim.x * GPB;
-  for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < a.count; idx += ngroups) {
+  for (int32_t idx = lo + (int32_t)blockIdx.x * GPB + gib; idx < hi; idx += (int32_t)ngroups) {
     const int32_t i = a.list[idx];
     if (lane == 0) ctr[0]++;
     // batched run: the graph of i, skipped once its local-moving phase has converged
@@ -131,7 +141,7 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
     }
     const A two_m = gcv ? (M::is_fp ? (A)gcv->two_m_f : (A)gcv->two_m_i) : two_m_all;
     // row bounds, C'[i] and the flag are loaded together (the loads overlap)
-    const int64_t beg = a.g.rbeg[i], end = a.g.rend[i];
+    const int64_t beg = g.rbeg[i], end = g.rend[i];
     const int32_t d = a.st.Cp[i];
     if (a.pruning) {
       // every lane reads the flag and the group takes the OR, so the decision is uniform even if a
@@ -163,8 +173,8 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int64_t e = e0 + (int64_t)u * G;
-        jj[u] = e < end ? a.g.tg[e] : i;
-        ww[u] = e < end ? (H)a.g.w[e] : H(0);
+        jj[u] = e < end ? g.tg[e] : i;
+        ww[u] = e < end ? (H)g.w[e] : H(0);
       }
       int32_t cc[U];
 #pragma unroll
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 1)) lm_kernel(LmArgs<M>
 #pragma unroll
           for (int u = 0; u < U; u++) {
             const int64_t e = e0 + (int64_t)u * G;
-            jj[u] = e < end ? a.g.tg[e] : i;
+            jj[u] = e < end ? g.tg[e] : i;
           }
 #pragma unroll
           for (int u = 0; u < U; u++)
@@ -329,17 +339,20 @@ static void launch_lm(Ctx& c, const LmArgs<M>& a, int max_blocks) {
   constexpr int GPB = G <= 32 ? BS / G : 1;
   constexpr size_t smem = lm_smem<M, G, LOG, GLOBAL>();
   lm_attr<M, G, LOG, GLOBAL>();
-  int grid = grid_for(a.count, GPB, max_blocks * (kBlock / BS));
+  // device-resident range: the count is not known here, so the grid is the cap
+  int grid = a.rng ? max_blocks * (kBlock / BS) : grid_for(a.count, GPB, max_blocks * (kBlock / BS));
   lm_kernel<M, G, LOG, GLOBAL><<<grid, BS, smem, c.s>>>(a);
   c.launches++;
 }
 
 template <class M>
 void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
-                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning) {
-  if (count <= 0) return;
+                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning,
+                 const int64_t* rng) {
+  if (count <= 0 && !rng) return;
   LmArgs<M> a;
   a.g = g; a.st = st; a.list = list; a.count = count;
+  a.rng = rng;
   a.gkeys = gt.keys; a.gvals = reinterpret_cast<typename M::h_t*>(gt.vals); a.gslots = gt.slots_per_block;
   a.glog = 0;
   while (((int64_t)1 << a.glog) < gt.slots_per_block) a.glog++;
@@ -360,8 +373,12 @@ void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const 
 
 // ---------------------------------------------------------------- deterministic apply
 template <class M>
-__global__ void lm_apply(PassState<M> st, const int32_t* list, int64_t count) {
+__global__ void lm_apply(PassState<M> st, const int32_t* list, int64_t count, const int64_t* rng) {
   if (*(volatile int32_t*)&st.ctrl->done) return;
+  if (rng) {
+    list += rng[0];
+    count = rng[1];
+  }
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t i = list[k];
     const int32_t t = st.mv_to[i];
@@ -374,9 +391,10 @@ __global__ void lm_apply(PassState<M> st, const int32_t* list, int64_t count) {
   }
 }
 template <class M>
-void move_apply(Ctx& c, const PassState<M>& st, const int32_t* list, int64_t count) {
-  if (count <= 0) return;
-  lm_apply<M><<<grid_for(count, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(st, list, count);
+void move_apply(Ctx& c, const PassState<M>& st, const int32_t* list, int64_t count, const int64_t* rng) {
+  if (count <= 0 && !rng) return;
+  const int grid = rng ? c.num_sms * 8 : grid_for(count, kBlock, c.num_sms * 8);
+  lm_apply<M><<<grid, kBlock, 0, c.s>>>(st, list, count, rng);
   c.launches++;
 }
 
@@ -510,8 +528,8 @@ void total_weight(Ctx& c, const typename M::a_t* K, int64_t n, Ctrl* ctrl) {
                             M::a_t*);                                                                            \
   template void total_weight<M>(Ctx&, const M::a_t*, int64_t, Ctrl*);                                            \
   template void move_bucket<M>(Ctx&, int, const GraphView<M::w_t>&, const PassState<M>&, const int32_t*, int64_t, \
-                               const GlobalTable&, bool, bool);                                                  \
-  template void move_apply<M>(Ctx&, const PassState<M>&, const int32_t*, int64_t);                               \
+                               const GlobalTable&, bool, bool, const int64_t*);                                  \
+  template void move_apply<M>(Ctx&, const PassState<M>&, const int32_t*, int64_t, const int64_t*);               \
   template void move_finish<M>(Ctx&, Ctrl*);
 LV_MOVE_INST(IntMode)
 LV_MOVE_INST(FpMode)

@@ -60,6 +60,7 @@ struct Workspace {
   DevAlloc gt_alloc;
   int64_t gt_slots_total = 0;
   unsigned* gt_bits = nullptr;
+  int32_t* pool = nullptr;    // giant-row table pool: gt_slots_total {key, value} pairs
   GlobalTable gt;
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
   DevAlloc desc_alloc;        // step records and the pass GraphView of captured iterations
@@ -278,25 +279,20 @@ louvain_status ensure_pool(louvain_handle h, Ctx& c, int64_t slots) {
     free_all(ws.gt_alloc);
     ws.gt_slots_total = 0;
     const int64_t total = (slots + slots / 4 + 4096 + 63) / 64 * 64;
-    int32_t* k = nullptr;
-    int32_t* v = nullptr;
+    int32_t* kv = nullptr;
     unsigned* bits = nullptr;
-    if (!dalloc(h, ws.gt_alloc, &k, total) || !dalloc(h, ws.gt_alloc, &v, total) ||
-        !dalloc(h, ws.gt_alloc, &bits, total / 32)) {
+    if (!dalloc(h, ws.gt_alloc, &kv, 2 * total) || !dalloc(h, ws.gt_alloc, &bits, total / 32)) {
       free_all(ws.gt_alloc);
       return set_err(h, LOUVAIN_ERR_OOM, "giant hash-table pool allocation failed");
     }
-    cudaMemsetAsync(k, 0xFF, (size_t)total * 4, c.s);
-    cudaMemsetAsync(v, 0, (size_t)total * 4, c.s);
+    pool_init(c, kv, total);
     cudaMemsetAsync(bits, 0, (size_t)(total / 32) * 4, c.s);
-    ws.gt.keys = k;
-    ws.gt.vals = v;
+    ws.pool = kv;
     ws.gt_bits = bits;
     ws.gt_slots_total = total;
   }
   for (GiantPlan* gp : {&ws.gp, &ws.gpv}) {
-    gp->keys = ws.gt.keys;
-    gp->vals = ws.gt.vals;
+    gp->slots = ws.pool;
     gp->bits = ws.gt_bits;
     gp->pool_slots = ws.gt_slots_total;
   }

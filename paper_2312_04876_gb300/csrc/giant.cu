@@ -131,23 +131,48 @@ void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t*
   c.launches += 3;
 }
 
-// tbl_add for a giant's table at pool offset `base` that also sets the slot's bit in the pool's
-// occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
+// Pool slots: slot s of a table at pool offset `base` is the pair {key, value} at kv[2s], kv[2s + 1]
+// (kv = pool + 2 base), so a probe, its claim and its add touch one 32-byte sector.
+__global__ void k_pool_init(int2* kv, int64_t n) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    kv[s] = make_int2(kEmpty, 0);  // value 0 is 0u and 0.0f
+}
+void pool_init(Ctx& c, int32_t* slots, int64_t n) {
+  if (n <= 0) return;
+  k_pool_init<<<grid_for(n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(reinterpret_cast<int2*>(slots), n);
+  c.launches++;
+}
+
+// The value word of a pool slot as h_t (uint32_t or float).
+template <class H>
+__device__ __forceinline__ H int_as_h(int32_t x);
+template <>
+__device__ __forceinline__ uint32_t int_as_h<uint32_t>(int32_t x) { return (uint32_t)x; }
+template <>
+__device__ __forceinline__ float int_as_h<float>(int32_t x) { return __int_as_float(x); }
+
+template <class V>
+__device__ __forceinline__ V* slot_val(int32_t* kv, unsigned s) {
+  return reinterpret_cast<V*>(&kv[2 * (size_t)s + 1]);
+}
+
+// tbl_add for a giant's table (kv, at pool offset `base`) that also sets the slot's bit in the
+// pool's occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
 // Probing starts at slot s (the key's home) whose key was already read as k0.
 template <class V>
-__device__ __forceinline__ bool tbl_add_mark_at(int32_t* keys, V* vals, unsigned size, int32_t key, V w,
-                                                unsigned* bits, int64_t base, unsigned s, int32_t k0) {
+__device__ __forceinline__ bool tbl_add_mark_at(int32_t* kv, unsigned size, int32_t key, V w, unsigned* bits,
+                                                int64_t base, unsigned s, int32_t k0) {
   for (unsigned p = 0; p < size; p++) {
-    const int32_t k = p == 0 ? k0 : *((volatile int32_t*)&keys[s]);
-    if (k == key) { atomicAdd(&vals[s], w); return true; }
+    const int32_t k = p == 0 ? k0 : *((volatile int32_t*)&kv[2 * (size_t)s]);
+    if (k == key) { atomicAdd(slot_val<V>(kv, s), w); return true; }
     if (k == kEmpty) {
-      const int32_t old = atomicCAS(&keys[s], kEmpty, key);
+      const int32_t old = atomicCAS(&kv[2 * (size_t)s], kEmpty, key);
       if (old == kEmpty) {
         atomicOr(&bits[(base + s) >> 5], 1u << ((base + s) & 31));
-        atomicAdd(&vals[s], w);
+        atomicAdd(slot_val<V>(kv, s), w);
         return true;
       }
-      if (old == key) { atomicAdd(&vals[s], w); return true; }
+      if (old == key) { atomicAdd(slot_val<V>(kv, s), w); return true; }
     }
     s = (s + 1) & (size - 1);
   }
@@ -155,15 +180,15 @@ __device__ __forceinline__ bool tbl_add_mark_at(int32_t* keys, V* vals, unsigned
 }
 
 template <class V>
-__device__ __forceinline__ bool tbl_add_mark(int32_t* keys, V* vals, unsigned size, int shift, int32_t key, V w,
-                                             unsigned* bits, int64_t base) {
+__device__ __forceinline__ bool tbl_add_mark(int32_t* kv, unsigned size, int shift, int32_t key, V w, unsigned* bits,
+                                             int64_t base) {
   const unsigned s = tbl_home(key, shift);
-  return tbl_add_mark_at(keys, vals, size, key, w, bits, base, s, *((volatile int32_t*)&keys[s]));
+  return tbl_add_mark_at(kv, size, key, w, bits, base, s, *((volatile int32_t*)&kv[2 * (size_t)s]));
 }
 
 // ---------------------------------------------------------------- shared pre-aggregation
 // Sums a chunk's (key, weight) pairs in the block's shared table, then flushes each distinct key
-// once into the global table (tk, tv, size 2^lg).  Every thread of the block must call both.
+// once into the global table (kv, size 2^lg).  Every thread of the block must call both.
 template <class H>
 struct LocalAgg {
   int32_t keys[1 << kLocLog];
@@ -176,7 +201,7 @@ __device__ __forceinline__ void local_clear(LocalAgg<H>& la) {
 }
 
 template <class H>
-__device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* tk, H* tv, unsigned size, int lg, unsigned* bits,
+__device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* kv, unsigned size, int lg, unsigned* bits,
                                             int64_t base) {
   bool ok = true;
   __syncthreads();
@@ -200,11 +225,11 @@ __device__ __forceinline__ bool local_flush(LocalAgg<H>& la, int32_t* tk, H* tv,
     for (int v = 0; v < V; v++) {
       home[v] = tbl_home(key[v], 32 - lg);
       seen[v] = key[v];
-      if (key[v] != kEmpty) seen[v] = *((volatile int32_t*)&tk[home[v]]);
+      if (key[v] != kEmpty) seen[v] = *((volatile int32_t*)&kv[2 * (size_t)home[v]]);
     }
 #pragma unroll
     for (int v = 0; v < V; v++)
-      if (key[v] != kEmpty) ok &= tbl_add_mark_at(tk, tv, size, key[v], val[v], bits, base, home[v], seen[v]);
+      if (key[v] != kEmpty) ok &= tbl_add_mark_at(kv, size, key[v], val[v], bits, base, home[v], seen[v]);
   }
   __syncthreads();
   return ok;
@@ -278,8 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
     const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
     int lg = 0;
     while (((int64_t)1 << lg) < ts) lg++;
-    int32_t* tk = p.keys + off;
-    H* tv = reinterpret_cast<H*>(p.vals) + off;
+    int32_t* kv = p.slots + 2 * off;
     const int64_t e0 = g.rbeg[i] + (q - p.chunk_off[k]) * kLmChunk;
     const int64_t e1 = e0 + kLmChunk < g.rend[i] ? e0 + kLmChunk : g.rend[i];
     int32_t jj[U];
@@ -298,7 +322,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
     for (int u = 0; u < U; u++) {
       if (jj[u] == i) continue;
       if (cc[u] == d) kid += ww[u];
-      else ok &= tbl_add_mark(tk, tv, (unsigned)ts, 32 - lg, cc[u], ww[u], p.bits, off);
+      else ok &= tbl_add_mark(kv, (unsigned)ts, 32 - lg, cc[u], ww[u], p.bits, off);
     }
     kid = group_sum<kBlock>(kid, red);
     if (threadIdx.x == 0 && kid != H(0)) atomicAdd(reinterpret_cast<H*>(p.kid) + k, kid);
@@ -334,8 +358,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
     const H kid = reinterpret_cast<const H*>(p.kid)[k];
     const A ki = K[i], sd = Sig[d];
     const A two_m = gc ? (M::is_fp ? (A)gc[vg[i]].two_m_f : (A)gc[vg[i]].two_m_i) : two_m_all;
-    int32_t* tk = p.keys + off;
-    H* tv = reinterpret_cast<H*>(p.vals) + off;
+    int2* kv = reinterpret_cast<int2*>(p.slots) + off;
     // the range's bitmap words, one per lane (tables are >= 64 slots and 64-slot aligned)
     const int64_t sb = (q - p.slice_off[k]) << kRangeLog;
     const int64_t se = sb + (1 << kRangeLog) < ts ? sb + (1 << kRangeLog) : ts;
@@ -363,8 +386,9 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
       H vv[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        ks[u] = ss[u] >= 0 ? tk[ss[u]] : kEmpty;
-        vv[u] = ss[u] >= 0 ? tv[ss[u]] : H(0);
+        const int2 e = ss[u] >= 0 ? kv[ss[u]] : make_int2(kEmpty, 0);  // key and value: one 8-byte load
+        ks[u] = e.x;
+        vv[u] = int_as_h<H>(e.y);
       }
       A sg[4];
 #pragma unroll
@@ -372,8 +396,7 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         if (ss[u] < 0) continue;
-        tk[ss[u]] = kEmpty;
-        tv[ss[u]] = H(0);
+        kv[ss[u]] = make_int2(kEmpty, 0);
         cand++;
         const S sc = M::score(vv[u], kid, ki, sg[u], sd, two_m);
         if (better(sc, ks[u], best, bc)) { best = sc; bc = ks[u]; }
@@ -630,7 +653,7 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_comm_chunks(GraphView<typen
     const unsigned ts = (unsigned)(p.tab_off[k + 1] - off);
     int lg = 0;
     while ((1u << lg) < ts) lg++;
-    ok &= local_flush(la, p.keys + off, reinterpret_cast<H*>(p.vals) + off, ts, lg, p.bits, off);
+    ok &= local_flush(la, p.slots + 2 * off, ts, lg, p.bits, off);
   }
   if (!ok) atomicOr(&ctrl->error, kErrTableFull);
   if (threadIdx.x == 0 && n_arcs) {
@@ -656,8 +679,7 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_emit(const int32_t* list, i
     const int64_t k = p.sowner[q];
     const int32_t c = list[k];
     const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
-    int32_t* tk = p.keys + off;
-    H* tv = reinterpret_cast<H*>(p.vals) + off;
+    int2* kv = reinterpret_cast<int2*>(p.slots) + off;
     const int64_t sb = (q - p.slice_off[k]) << kSliceLog;
     const int64_t se = sb + (1 << kSliceLog) < ts ? sb + (1 << kSliceLog) : ts;
     const int nwords = (int)((se - sb) >> 5);
@@ -681,10 +703,10 @@ __global__ void __launch_bounds__(kBlock) k_giant_mg_emit(const int32_t* list, i
     while (word) {
       const int64_t s = s0 + (__ffs(word) - 1);
       word &= word - 1;
-      otg[pos] = tk[s];
-      ow[pos] = (typename M::w_t)tv[s];
-      tk[s] = kEmpty;
-      tv[s] = H(0);
+      const int2 e = kv[s];
+      otg[pos] = e.x;
+      ow[pos] = (typename M::w_t)int_as_h<H>(e.y);
+      kv[s] = make_int2(kEmpty, 0);
       pos++;
     }
     written += (unsigned long long)cnt;

@@ -200,8 +200,10 @@ void compact_rows(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, c
 void row_lengths(Ctx& c, int64_t n, const int64_t* hbeg, const int64_t* hend, int64_t* len);
 
 // ---------------------------------------------------------------- giant.cu
-// Plan of the multi-block path for bucket-4 rows: per giant k, ranges [off[k], off[k+1]) of arc
-// chunks, table slots (in the shared pool keys/vals) and table slices.
+// Sets n pool slots to {kEmpty, 0}.
+void pool_init(Ctx& c, int32_t* slots, int64_t n);
+// Plan of the multi-block path for giant rows: per giant k, ranges [off[k], off[k+1]) of arc
+// chunks, table slots (in the shared pool) and table slices.
 struct GiantPlan {
   int64_t* chunk_off = nullptr;  // [cap + 1]
   int64_t* tab_off = nullptr;    // [cap + 1]
@@ -214,8 +216,9 @@ struct GiantPlan {
   int32_t* cowner = nullptr;     // [chunk_cap] giant of each chunk
   int32_t* sowner = nullptr;     // [slice_cap] giant of each slice
   int64_t chunk_cap = 0, slice_cap = 0;
-  int32_t* keys = nullptr;       // shared table pool, all kEmpty between uses
-  void* vals = nullptr;          // (h_t), all zero between uses
+  int32_t* slots = nullptr;      // shared table pool, slot s = {key, value (h_t)} at slots[2s], [2s + 1]
+                                 // (one 8-byte pair: a probe touches one sector); all {kEmpty, 0}
+                                 // between uses
   unsigned* bits = nullptr;      // occupancy bitmap of the pool (local move), all zero between uses
   int64_t pool_slots = 0;
 };

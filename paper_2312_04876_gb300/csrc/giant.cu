@@ -160,19 +160,30 @@ __device__ __forceinline__ V* slot_val(int32_t* kv, unsigned s) {
 // pool's occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
 // Probing starts at slot s (the key's home) whose key was already read as k0.
 template <class V>
+__device__ __forceinline__ uint32_t val_bits(V w);
+template <>
+__device__ __forceinline__ uint32_t val_bits<uint32_t>(uint32_t w) { return w; }
+template <>
+__device__ __forceinline__ uint32_t val_bits<float>(float w) { return __float_as_uint(w); }
+
+// An empty slot is claimed together with its first value by one 64-bit compare-and-swap of the
+// pair ({kEmpty, 0} -> {key, w}); a slot that holds the key gets an add.
+template <class V>
 __device__ __forceinline__ bool tbl_add_mark_at(int32_t* kv, unsigned size, int32_t key, V w, unsigned* bits,
                                                 int64_t base, unsigned s, int32_t k0) {
+  constexpr unsigned long long kEmptyPair = 0xFFFFFFFFull;  // {key kEmpty, value 0}, little-endian
+  const unsigned long long mine = ((unsigned long long)val_bits<V>(w) << 32) | (uint32_t)key;
   for (unsigned p = 0; p < size; p++) {
     const int32_t k = p == 0 ? k0 : *((volatile int32_t*)&kv[2 * (size_t)s]);
     if (k == key) { atomicAdd(slot_val<V>(kv, s), w); return true; }
     if (k == kEmpty) {
-      const int32_t old = atomicCAS(&kv[2 * (size_t)s], kEmpty, key);
-      if (old == kEmpty) {
+      const unsigned long long old =
+          atomicCAS(reinterpret_cast<unsigned long long*>(&kv[2 * (size_t)s]), kEmptyPair, mine);
+      if (old == kEmptyPair) {
         atomicOr(&bits[(base + s) >> 5], 1u << ((base + s) & 31));
-        atomicAdd(slot_val<V>(kv, s), w);
         return true;
       }
-      if (old == key) { atomicAdd(slot_val<V>(kv, s), w); return true; }
+      if ((int32_t)(uint32_t)old == key) { atomicAdd(slot_val<V>(kv, s), w); return true; }
     }
     s = (s + 1) & (size - 1);
   }

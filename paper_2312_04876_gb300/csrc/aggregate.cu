@@ -182,13 +182,11 @@ __device__ __forceinline__ bool merge_members_block(const MergeArgs<M>& a, int64
   return ok;
 }
 
-template <class M, int G, int LOG, bool GLOBAL>
-__global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int32_t* list, int64_t count,
-                                                       int32_t* gkeys, typename M::h_t* gvals, int64_t gslots,
-                                                       int glog) {
+template <class M, int G, int LOG>
+__global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int32_t* list, int64_t count) {
   typedef typename M::h_t H;
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
-  constexpr int SL = GLOBAL ? 1 : (1 << LOG);
+  constexpr int SL = 1 << LOG;
   extern __shared__ __align__(16) unsigned char mg_dyn[];  // GPB tables of SL (key, value) slots
   int32_t* skeys = reinterpret_cast<int32_t*>(mg_dyn);
   H* svals = reinterpret_cast<H*>(mg_dyn + sizeof(int32_t) * GPB * SL);
@@ -196,24 +194,17 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
   __shared__ int64_t s_incl[G > 32 ? kBlock : 1], s_base[G > 32 ? kBlock : 1], s_wsum[kBlock / 32];
   const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
   const unsigned lane = Grp<G>::lane();
-  int32_t* tk;
-  H* tv;
-  if (GLOBAL) {
-    tk = gkeys + (int64_t)blockIdx.x * gslots;
-    tv = gvals + (int64_t)blockIdx.x * gslots;
-  } else {
-    for (int t = threadIdx.x; t < GPB * SL; t += kBlock) { skeys[t] = kEmpty; svals[t] = H(0); }
-    __syncthreads();
-    tk = skeys + gib * SL;
-    tv = svals + gib * SL;
-  }
+  for (int t = threadIdx.x; t < GPB * SL; t += kBlock) { skeys[t] = kEmpty; svals[t] = H(0); }
+  __syncthreads();
+  int32_t* tk = skeys + gib * SL;
+  H* tv = svals + gib * SL;
   unsigned long long ctr[4] = {0, 0, 0, 0};  // communities, members, arcs scanned, arcs written
   for (int64_t idx = (int64_t)blockIdx.x * GPB + gib; idx < count; idx += (int64_t)gridDim.x * GPB) {
     const int32_t c = list[idx];
     const int64_t m0 = a.coff[c], m1 = a.coff[c + 1];
     if (lane == 0) { ctr[0]++; ctr[1] += (unsigned long long)(m1 - m0); }
     const int64_t D = a.cdeg[c];
-    const int lg = GLOBAL ? tbl_log2(D < a.nc ? D : a.nc, 6, glog) : tbl_log2(D, 1, LOG);
+    const int lg = tbl_log2(D, 1, LOG);
     const unsigned size = 1u << lg;
     const int shift = 32 - lg;
     bool ok;
@@ -276,34 +267,29 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
   block_add_counters<4>(a.ctrl->mg_stat[a.bucket], ctr);
 }
 
-template <class M, int G, int LOG, bool GLOBAL>
-static void launch_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt,
-                         int max_blocks) {
+template <class M, int G, int LOG>
+static void launch_merge(Ctx& c, const MergeArgs<M>& a, const int32_t* list, int64_t count, int max_blocks) {
   constexpr int GPB = G <= 32 ? kBlock / G : 1;
-  constexpr size_t smem = (size_t)GPB * (GLOBAL ? 1 : (1 << LOG)) * (sizeof(int32_t) + sizeof(typename M::h_t));
+  constexpr size_t smem = (size_t)GPB * (1 << LOG) * (sizeof(int32_t) + sizeof(typename M::h_t));
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(merge_kernel<M, G, LOG, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int glog = 0;
-  while (((int64_t)1 << glog) < gt.slots_per_block) glog++;
-  merge_kernel<M, G, LOG, GLOBAL><<<grid_for(count, GPB, max_blocks), kBlock, smem, c.s>>>(
-      a, list, count, gt.keys, reinterpret_cast<typename M::h_t*>(gt.vals), gt.slots_per_block, glog);
+    cudaFuncSetAttribute(merge_kernel<M, G, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  merge_kernel<M, G, LOG><<<grid_for(count, GPB, max_blocks), kBlock, smem, c.s>>>(a, list, count);
   c.launches++;
 }
 
 template <class M>
-void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& args, const int32_t* list, int64_t count,
-                  const GlobalTable& gt) {
+void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& args, const int32_t* list, int64_t count) {
   if (count <= 0) return;
   MergeArgs<M> a = args;
   a.bucket = bucket < kNumBuckets ? bucket : kNumBuckets - 1;
   const int cap = c.num_sms * 16;
   switch (bucket) {
-    case 0: launch_merge<M, 4, 3, false>(c, a, list, count, gt, cap); break;
-    case 1: launch_merge<M, 8, 5, false>(c, a, list, count, gt, cap); break;
-    case 2: launch_merge<M, 32, 8, false>(c, a, list, count, gt, cap); break;
-    case 3: launch_merge<M, 32, 10, false>(c, a, list, count, gt, cap); break;
-    case 4: launch_merge<M, 256, 12, false>(c, a, list, count, gt, cap); break;
-    case 5: launch_merge<M, 256, 13, false>(c, a, list, count, gt, cap); break;
+    case 0: launch_merge<M, 4, 3>(c, a, list, count, cap); break;
+    case 1: launch_merge<M, 8, 5>(c, a, list, count, cap); break;
+    case 2: launch_merge<M, 32, 8>(c, a, list, count, cap); break;
+    case 3: launch_merge<M, 32, 10>(c, a, list, count, cap); break;
+    case 4: launch_merge<M, 256, 12>(c, a, list, count, cap); break;
+    case 5: launch_merge<M, 256, 13>(c, a, list, count, cap); break;
     default: break;  // giant communities go through giant_merge
   }
 }
@@ -413,8 +399,8 @@ template void compact_bucketed<float>(Ctx&, const int32_t*, const int64_t*, cons
                                       const int64_t*, const int32_t*, const float*, int32_t*, float*,
                                       const GiantPlan&, Ctrl*);
 
-template void merge_bucket<IntMode>(Ctx&, int, const MergeArgs<IntMode>&, const int32_t*, int64_t, const GlobalTable&);
-template void merge_bucket<FpMode>(Ctx&, int, const MergeArgs<FpMode>&, const int32_t*, int64_t, const GlobalTable&);
+template void merge_bucket<IntMode>(Ctx&, int, const MergeArgs<IntMode>&, const int32_t*, int64_t);
+template void merge_bucket<FpMode>(Ctx&, int, const MergeArgs<FpMode>&, const int32_t*, int64_t);
 template void compact_rows<int32_t>(Ctx&, int64_t, const int64_t*, const int64_t*, const int64_t*, const int32_t*,
                                     const int32_t*, int32_t*, int32_t*);
 template void compact_rows<float>(Ctx&, int64_t, const int64_t*, const int64_t*, const int64_t*, const int32_t*,

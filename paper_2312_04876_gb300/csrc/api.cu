@@ -61,7 +61,6 @@ struct Workspace {
   int64_t gt_slots_total = 0;
   unsigned* gt_bits = nullptr;
   int32_t* pool = nullptr;    // giant-row table pool: gt_slots_total {key, value} pairs
-  GlobalTable gt;
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
   DevAlloc desc_alloc;        // step records and the pass GraphView of captured iterations
   int64_t* desc = nullptr;
@@ -252,6 +251,13 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   if (!ok) {
     free_all(ws.core);
     return set_err(h, LOUVAIN_ERR_OOM, "workspace allocation failed or exceeds the HBM budget");
+  }
+  // fresh device memory holds whatever its last owner left: the control block starts zeroed (error
+  // bits, counters), complete before any stream of the caller's touches it
+  if (cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), cudaStreamLegacy) != cudaSuccess ||
+      cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+    free_all(ws.core);
+    return cuda_err(h, cudaGetLastError(), "control block initialisation");
   }
   ws.n_cap = nc;
   ws.a_cap = ac;
@@ -519,7 +525,7 @@ void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t
         cb.launches = 0;
         cudaStreamWaitEvent(cb.s, h->fork_ev[k], 0);
         if (!giant)
-          move_bucket<M>(cb, b, gk, st, rk ? ws.perm : ws.perm + cs.start[b], cnt, ws.gt, !det, pruning,
+          move_bucket<M>(cb, b, gk, st, rk ? ws.perm : ws.perm + cs.start[b], cnt, !det, pruning,
                          rk ? rk + 2 * b : nullptr);
         else
           giant_move<M>(cb, gk, st, rk ? gbase : glist, cs.g0, cs.g1, ws.gp, !det, pruning,
@@ -529,7 +535,7 @@ void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t
         cudaStreamWaitEvent(c.s, h->join_ev[k * kNumBuckets + b], 0);
       } else {
         const int pm = prof_begin(h, c);
-        if (!giant) move_bucket<M>(c, b, g, st, ws.perm + cs.start[b], cnt, ws.gt, !det, pruning);
+        if (!giant) move_bucket<M>(c, b, g, st, ws.perm + cs.start[b], cnt, !det, pruning);
         else giant_move<M>(c, g, st, glist, cs.g0, cs.g1, ws.gp, !det, pruning);
         prof_end(h, c, kLm0 + b, pm);
       }
@@ -556,7 +562,6 @@ std::vector<int64_t> iteration_key(louvain_handle h, const Ctx& c, const GraphVi
   std::vector<int64_t> k = {M::is_fp ? 1 : 0, det ? 1 : 0, pruning ? 1 : 0, n_graphs, (int64_t)(intptr_t)gc,
                             c.num_sms, c.lm_blocks_per_sm, c.giant_min, (int64_t)(intptr_t)ws.perm,
                             (int64_t)(intptr_t)gbase, (int64_t)(intptr_t)recs, (int64_t)(intptr_t)ws.desc,
-                            (int64_t)(intptr_t)ws.gt.keys, (int64_t)(intptr_t)ws.gt.vals, ws.gt.slots_per_block,
                             (int64_t)(intptr_t)g.rbeg, (int64_t)(intptr_t)g.rend, (int64_t)(intptr_t)g.tg,
                             (int64_t)(intptr_t)g.w, (int64_t)steps.size()};
   const size_t n0 = k.size();
@@ -915,7 +920,7 @@ louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typenam
   for (int b = 0; b < kNumBuckets; b++) {
     if (cb[b + 1] - cb[b] <= 0) continue;
     const int pm = prof_begin(h, c);
-    if (b < kNumBuckets - 1) merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.gt);
+    if (b < kNumBuckets - 1) merge_bucket<M>(c, b, a, ws.cperm + cb[b], cb[b + 1] - cb[b]);
     else giant_merge<M>(c, a, ws.cperm + cb[b], cb[b + 1] - cb[b], ws.csz, ws.gp, reinterpret_cast<int64_t*>(ws.tot),
                         ws.len, ws.tile_tmp);
     prof_end(h, c, kMg0 + b, pm);
@@ -1585,11 +1590,12 @@ louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const
   Ctx c;
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
-  if ((s = ensure_workspace(h, n, 0)) != LOUVAIN_OK) return s;
+  // the colour bitmaps and push chunks are sized from the arcs (ceil((deg + 1) / 32) words a vertex)
+  if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
   *n_colours = 0;
   if (n == 0) return LOUVAIN_OK;
   Ctrl* ctrl = h->ws.ctrl;
-  validate_reset(c, ctrl);
+  cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), c.s);  // error bits of an earlier call must not stop this one
   validate_offsets(c, n, n_arcs, d_offsets, ctrl);
   const Ctrl* hc = read_ctrl(h, c, &s, "validate offsets");
   if (!hc) return s;

@@ -304,6 +304,23 @@ __device__ __forceinline__ bool tbl_add(int32_t* keys, V* vals, unsigned size, i
   return false;
 }
 
+// Tables of {key, value} pairs (the giant-row pool): slot s is kv[2s] (key) and kv[2s + 1] (value
+// bits of an h_t, a uint32_t or float), so one 8-byte access reads or clears a slot; empty =
+// {kEmpty, 0}.
+template <class V>
+__device__ __forceinline__ uint32_t val_bits(V w);
+template <>
+__device__ __forceinline__ uint32_t val_bits<uint32_t>(uint32_t w) { return w; }
+template <>
+__device__ __forceinline__ uint32_t val_bits<float>(float w) { return __float_as_uint(w); }
+template <class H>
+__device__ __forceinline__ H int_as_h(int32_t x);
+template <>
+__device__ __forceinline__ uint32_t int_as_h<uint32_t>(int32_t x) { return (uint32_t)x; }
+template <>
+__device__ __forceinline__ float int_as_h<float>(int32_t x) { return __int_as_float(x); }
+constexpr unsigned long long kEmptyPair = 0xFFFFFFFFull;  // {kEmpty, 0} as one little-endian word
+
 // log2 of the table size for `distinct_bound` keys: the smallest power of two >= 2*bound, at
 // least `min_size`, at most `max_size` (callers guarantee 2*bound <= max_size).
 __host__ __device__ __forceinline__ int tbl_log2(int64_t distinct_bound, int min_log2, int max_log2) {

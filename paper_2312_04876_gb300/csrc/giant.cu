@@ -143,14 +143,6 @@ void pool_init(Ctx& c, int32_t* slots, int64_t n) {
   c.launches++;
 }
 
-// The value word of a pool slot as h_t (uint32_t or float).
-template <class H>
-__device__ __forceinline__ H int_as_h(int32_t x);
-template <>
-__device__ __forceinline__ uint32_t int_as_h<uint32_t>(int32_t x) { return (uint32_t)x; }
-template <>
-__device__ __forceinline__ float int_as_h<float>(int32_t x) { return __int_as_float(x); }
-
 template <class V>
 __device__ __forceinline__ V* slot_val(int32_t* kv, unsigned s) {
   return reinterpret_cast<V*>(&kv[2 * (size_t)s + 1]);
@@ -159,19 +151,11 @@ __device__ __forceinline__ V* slot_val(int32_t* kv, unsigned s) {
 // tbl_add for a giant's table (kv, at pool offset `base`) that also sets the slot's bit in the
 // pool's occupancy bitmap when it claims the slot, so the scan visits only occupied slots.
 // Probing starts at slot s (the key's home) whose key was already read as k0.
-template <class V>
-__device__ __forceinline__ uint32_t val_bits(V w);
-template <>
-__device__ __forceinline__ uint32_t val_bits<uint32_t>(uint32_t w) { return w; }
-template <>
-__device__ __forceinline__ uint32_t val_bits<float>(float w) { return __float_as_uint(w); }
-
 // An empty slot is claimed together with its first value by one 64-bit compare-and-swap of the
 // pair ({kEmpty, 0} -> {key, w}); a slot that holds the key gets an add.
 template <class V>
 __device__ __forceinline__ bool tbl_add_mark_at(int32_t* kv, unsigned size, int32_t key, V w, unsigned* bits,
                                                 int64_t base, unsigned s, int32_t k0) {
-  constexpr unsigned long long kEmptyPair = 0xFFFFFFFFull;  // {key kEmpty, value 0}, little-endian
   const unsigned long long mine = ((unsigned long long)val_bits<V>(w) << 32) | (uint32_t)key;
   for (unsigned p = 0; p < size; p++) {
     const int32_t k = p == 0 ? k0 : *((volatile int32_t*)&kv[2 * (size_t)s]);

@@ -117,12 +117,6 @@ void total_weight(Ctx& c, const typename M::a_t* K, int64_t n, Ctrl* ctrl);
 // Reset the iteration state of a local-moving phase.
 void move_setup(Ctx& c, Ctrl* ctrl, double tau, int max_iterations);
 
-struct GlobalTable {
-  int32_t* keys = nullptr;
-  void* vals = nullptr;
-  int64_t slots_per_block = 0;  // power of two
-  int blocks = 0;
-};
 
 // One bucket's decide (+ apply in fast mode) over list[0, count).
 // With `rng` (a step record's {start, count} of this bucket) the kernel reads its range there and
@@ -130,8 +124,7 @@ struct GlobalTable {
 // once).
 template <class M>
 void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
-                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning,
-                 const int64_t* rng = nullptr);
+                 const int32_t* list, int64_t count, bool fast, bool pruning, const int64_t* rng = nullptr);
 // Shared-memory opt-ins of the local-move kernels (call before capturing launches into a graph).
 void move_prepare();
 // Deterministic mode: Sigma updates of the moves decided in list[0, count).
@@ -190,7 +183,7 @@ struct MergeArgs {
   int bucket = 0;  // set by merge_bucket (selects the traffic counters)
 };
 template <class M>
-void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& a, const int32_t* list, int64_t count, const GlobalTable& gt);
+void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& a, const int32_t* list, int64_t count);
 
 // Dense copy of holey rows: out arcs at doff[r] for rows [0, n).
 template <class W>

@@ -1,9 +1,10 @@
 // move.cu -- the local-moving phase of Algorithm 2 on the GPU.
 //
 // One group of G threads handles one vertex i (G by degree bucket: 4, 8, 32 lanes or a whole
-// block).  The group streams i's arcs (scanCommunities with self = false), accumulates
-// K_i->c for every neighbouring community c != C'[i] in an open-addressing table (shared
-// memory, or a per-block slice of global memory for hubs) and K_i->d in registers, then scores
+// block; rows above 4096 arcs take the multi-block path of giant.cu, whose tables live in global
+// memory).  The group streams i's arcs (scanCommunities with self = false), accumulates
+// K_i->c for every neighbouring community c != C'[i] in an open-addressing table in shared
+// memory and K_i->d in registers, then scores
 // every candidate with the Eq. 2 numerator
 //     N(c) = 2m (K_i->c - K_i->d) - K_i (Sigma_c - Sigma_d + K_i)
 // (exact int64 for int32 weights), takes the best with ties to the smallest id and moves iff
@@ -24,10 +25,6 @@ struct LmArgs {
   PassState<M> st;
   const int32_t* list;
   int64_t count;
-  int32_t* gkeys;
-  typename M::h_t* gvals;
-  int64_t gslots;
-  int glog;
   int fast;
   int pruning;
   int bucket;
@@ -79,7 +76,7 @@ __host__ __device__ constexpr int lm_block() {
   return (G == 32 && LOG >= 10) ? 64 : kBlock;
 }
 
-template <class M, int G, int LOG, bool GLOBAL>
+template <class M, int G, int LOG>
 __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M> a) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
@@ -97,7 +94,7 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
   }
   if (lo + (int)blockIdx.x * GPB >= hi) return;  // a fixed grid larger than this range
   const GraphView<typename M::w_t>& g = a.g;
-  constexpr int SL = GLOBAL ? 1 : (1 << LOG);
+  constexpr int SL = 1 << LOG;
   constexpr int U = G >= 32 ? 4 : 2;  // arcs (and table slots) per lane per step
   extern __shared__ __align__(16) unsigned char lm_dyn[];  // GPB tables of SL (key, value) slots
   int32_t* skeys = reinterpret_cast<int32_t*>(lm_dyn);
@@ -111,20 +108,12 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
 
   const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
   const unsigned lane = Grp<G>::lane();
-  int32_t* tk;
-  H* tv;
-  if (GLOBAL) {
-    tk = a.gkeys + (int64_t)blockIdx.x * a.gslots;
-    tv = a.gvals + (int64_t)blockIdx.x * a.gslots;
-  } else {
-    for (int t = threadIdx.x; t < GPB * SL; t += BS) { skeys[t] = kEmpty; svals[t] = H(0); }
-    __syncthreads();
-    tk = skeys + gib * SL;
-    tv = svals + gib * SL;
-  }
+  for (int t = threadIdx.x; t < GPB * SL; t += BS) { skeys[t] = kEmpty; svals[t] = H(0); }
+  __syncthreads();
+  int32_t* tk = skeys + gib * SL;  // this group's table
+  H* tv = svals + gib * SL;
   const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
   GraphCtl* const gcs = a.st.gc;
-  const int64_t n_cur = g.n;
   unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
   double acc_f = 0.0;
   unsigned long long ctr[6] = {0, 0, 0, 0, 0, 0};  // list, processed, arcs, candidates, moves, marks
@@ -156,9 +145,7 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
     // deterministic schedule Sigma does not change during a class; the fast schedule reads live values)
     const A ki = a.st.K[i];
     const A sd = a.st.Sig[d];
-    int lg;
-    if (GLOBAL) lg = tbl_log2(deg < n_cur ? deg : n_cur, 6, a.glog);
-    else lg = tbl_log2(deg, 1, LOG);
+    const int lg = tbl_log2(deg, 1, LOG);
     const unsigned size = 1u << lg;
     const int shift = 32 - lg;
 
@@ -306,67 +293,64 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
   block_add_counters<6>(ctrl->lm_stat[a.bucket], ctr);
 }
 
-template <class M, int G, int LOG, bool GLOBAL>
+template <class M, int G, int LOG>
 static constexpr size_t lm_smem() {
-  return (size_t)(G <= 32 ? lm_block<G, LOG>() / G : 1) * (GLOBAL ? 1 : (1 << LOG)) *
+  return (size_t)(G <= 32 ? lm_block<G, LOG>() / G : 1) * (1 << LOG) *
          (sizeof(int32_t) + sizeof(typename M::h_t));
 }
 
 // Opts a kernel into more than 48 KB of dynamic shared memory, once per device (outside any graph
 // capture: move_prepare runs it for every instantiation before an iteration is captured).
-template <class M, int G, int LOG, bool GLOBAL>
+template <class M, int G, int LOG>
 static void lm_attr() {
-  constexpr size_t smem = lm_smem<M, G, LOG, GLOBAL>();
+  constexpr size_t smem = lm_smem<M, G, LOG>();
   if (smem <= 48 * 1024) return;
   static std::atomic<unsigned long long> done{0};  // one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && (done.load() >> dev) & 1ULL) return;
-  cudaFuncSetAttribute(lm_kernel<M, G, LOG, GLOBAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(lm_kernel<M, G, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (dev < 64) done.fetch_or(1ULL << dev);
 }
 
 void move_prepare() {
-  lm_attr<IntMode, 32, 10, false>();
-  lm_attr<IntMode, 256, 13, false>();
-  lm_attr<FpMode, 32, 10, false>();
-  lm_attr<FpMode, 256, 13, false>();
+  lm_attr<IntMode, 32, 10>();
+  lm_attr<IntMode, 256, 13>();
+  lm_attr<FpMode, 32, 10>();
+  lm_attr<FpMode, 256, 13>();
 }
 
-template <class M, int G, int LOG, bool GLOBAL>
+template <class M, int G, int LOG>
 static void launch_lm(Ctx& c, const LmArgs<M>& a, int max_blocks) {
   constexpr int BS = lm_block<G, LOG>();
   constexpr int GPB = G <= 32 ? BS / G : 1;
-  constexpr size_t smem = lm_smem<M, G, LOG, GLOBAL>();
-  lm_attr<M, G, LOG, GLOBAL>();
+  constexpr size_t smem = lm_smem<M, G, LOG>();
+  lm_attr<M, G, LOG>();
   // device-resident range: the count is not known here, so the grid is the cap
   int grid = a.rng ? max_blocks * (kBlock / BS) : grid_for(a.count, GPB, max_blocks * (kBlock / BS));
-  lm_kernel<M, G, LOG, GLOBAL><<<grid, BS, smem, c.s>>>(a);
+  lm_kernel<M, G, LOG><<<grid, BS, smem, c.s>>>(a);
   c.launches++;
 }
 
 template <class M>
 void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
-                 const int32_t* list, int64_t count, const GlobalTable& gt, bool fast, bool pruning,
+                 const int32_t* list, int64_t count, bool fast, bool pruning,
                  const int64_t* rng) {
   if (count <= 0 && !rng) return;
   LmArgs<M> a;
   a.g = g; a.st = st; a.list = list; a.count = count;
   a.rng = rng;
-  a.gkeys = gt.keys; a.gvals = reinterpret_cast<typename M::h_t*>(gt.vals); a.gslots = gt.slots_per_block;
-  a.glog = 0;
-  while (((int64_t)1 << a.glog) < gt.slots_per_block) a.glog++;
   a.fast = fast ? 1 : 0;
   a.pruning = pruning ? 1 : 0;
   a.bucket = bucket < kNumBuckets ? bucket : kNumBuckets - 1;
   const int cap = c.num_sms * c.lm_blocks_per_sm;
   switch (bucket) {
-    case 0: launch_lm<M, 4, 3, false>(c, a, cap); break;
-    case 1: launch_lm<M, 8, 5, false>(c, a, cap); break;
-    case 2: launch_lm<M, 32, 8, false>(c, a, cap); break;
-    case 3: launch_lm<M, 32, 10, false>(c, a, cap); break;
-    case 4: launch_lm<M, 256, 12, false>(c, a, cap); break;
-    case 5: launch_lm<M, 256, 13, false>(c, a, cap); break;
+    case 0: launch_lm<M, 4, 3>(c, a, cap); break;
+    case 1: launch_lm<M, 8, 5>(c, a, cap); break;
+    case 2: launch_lm<M, 32, 8>(c, a, cap); break;
+    case 3: launch_lm<M, 32, 10>(c, a, cap); break;
+    case 4: launch_lm<M, 256, 12>(c, a, cap); break;
+    case 5: launch_lm<M, 256, 13>(c, a, cap); break;
     default: break;  // giants go through giant_move
   }
 }
@@ -528,7 +512,7 @@ void total_weight(Ctx& c, const typename M::a_t* K, int64_t n, Ctrl* ctrl) {
                             M::a_t*);                                                                            \
   template void total_weight<M>(Ctx&, const M::a_t*, int64_t, Ctrl*);                                            \
   template void move_bucket<M>(Ctx&, int, const GraphView<M::w_t>&, const PassState<M>&, const int32_t*, int64_t, \
-                               const GlobalTable&, bool, bool, const int64_t*);                                  \
+                               bool, bool, const int64_t*);                                                      \
   template void move_apply<M>(Ctx&, const PassState<M>&, const int32_t*, int64_t, const int64_t*);               \
   template void move_finish<M>(Ctx&, Ctrl*);
 LV_MOVE_INST(IntMode)

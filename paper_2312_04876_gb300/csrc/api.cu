@@ -141,11 +141,13 @@ struct louvain_handle_s {
     uint64_t used = 0;
     int64_t launches = 0;          // kernels per replay
     std::vector<int64_t> key;      // everything the captured launches depend on (see iteration_key)
+    uint64_t call = 0;             // API call that last used it
   };
   std::vector<CachedExec> execs;
   uint64_t exec_clock = 0;
   int64_t* dpin = nullptr;         // pinned staging of the step records
   int64_t dpin_cap = 0;
+  uint64_t call_seq = 0;           // API calls so far (begin_call)
 };
 
 constexpr size_t kExecCache = 16;
@@ -496,6 +498,17 @@ struct ClassStep {
   int64_t apply_start = 0, apply_count = 0;
 };
 
+// Upper bound of bucket b's count over the steps, rounded up to a power of two: it sizes the grid of
+// a captured launch that reads its count from the step records (the rounding lets later passes and
+// runs find the same executable).
+int64_t bucket_bound(const std::vector<ClassStep>& steps, int b) {
+  int64_t m = 0;
+  for (const ClassStep& cs : steps) m = cs.count[b] > m ? cs.count[b] : m;
+  int64_t p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+
 // Launches one iteration (every step; the convergence test at the end).  With `streams` the
 // degree buckets of a step fork to one side stream each and join before the next step (used
 // while capturing a CUDA graph); otherwise they run in order on c.s with per-launch profiling.
@@ -511,6 +524,9 @@ void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t
   Workspace& ws = h->ws;
   GraphView<typename M::w_t> gk = g;
   if (recs) gk.n = 0;
+  int64_t bound[kNumBuckets] = {};
+  if (recs)
+    for (int b = 0; b < kNumBuckets - 1; b++) bound[b] = bucket_bound(steps, b);
   for (size_t k = 0; k < steps.size(); k++) {
     const ClassStep& cs = steps[k];
     const int64_t* rk = recs ? recs + k * kStepWords : nullptr;
@@ -525,7 +541,7 @@ void enqueue_iteration(louvain_handle h, Ctx& c, const GraphView<typename M::w_t
         cb.launches = 0;
         cudaStreamWaitEvent(cb.s, h->fork_ev[k], 0);
         if (!giant)
-          move_bucket<M>(cb, b, gk, st, rk ? ws.perm : ws.perm + cs.start[b], cnt, !det, pruning,
+          move_bucket<M>(cb, b, gk, st, rk ? ws.perm : ws.perm + cs.start[b], rk ? bound[b] : cnt, !det, pruning,
                          rk ? rk + 2 * b : nullptr);
         else
           giant_move<M>(cb, gk, st, rk ? gbase : glist, cs.g0, cs.g1, ws.gp, !det, pruning,
@@ -568,6 +584,7 @@ std::vector<int64_t> iteration_key(louvain_handle h, const Ctx& c, const GraphVi
   k.resize(n0 + sizeof(PassState<M>) / 8 + sizeof(GiantPlan) / 8);
   std::memcpy(&k[n0], &st, sizeof(PassState<M>));
   std::memcpy(&k[n0 + sizeof(PassState<M>) / 8], &ws.gp, sizeof(GiantPlan));
+  for (int b = 0; b < kNumBuckets - 1; b++) k.push_back(bucket_bound(steps, b));  // grid sizes
   for (const ClassStep& cs : steps) {
     int64_t mask = 0;
     for (int b = 0; b < kNumBuckets - 1; b++)
@@ -602,6 +619,7 @@ louvain_handle_s::CachedExec* find_exec(louvain_handle h, const std::vector<int6
   for (auto& x : h->execs)
     if (x.key == key) {
       x.used = ++h->exec_clock;
+      x.call = h->call_seq;
       return &x;
     }
   return nullptr;
@@ -647,21 +665,34 @@ louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<type
     if (graph) cudaGraphDestroy(graph);
     return cuda_err(h, e, "graph capture end");
   }
-  // While the cache has room the graph gets an executable of its own (its key then hits from the
-  // next run on).  A full cache updates, in place, an executable of the same node count that is not
-  // `exclude` (the other graph of this phase), least recently used first; all work launched from it
-  // has completed (the host synchronised on the class offsets before this capture).
+  // A miss updates, in place, an executable of the same node count that no phase of this API call
+  // has used (one from an earlier graph: a new graph's keys never repeat, and an update costs ~0.1
+  // ms against ~2.6 ms for an instantiation), least recently used first.  Executables of this call
+  // are kept, so the passes of a graph that is run again all hit; when every candidate belongs to
+  // this call the graph gets an executable of its own while the cache has room, and a full cache
+  // updates its least recently used one of the same node count.  `exclude` (the other graph of
+  // this phase) is never touched; all work launched from the others has completed (the host
+  // synchronised on the class offsets before this capture).
   size_t nodes = 0;
   cudaGraphGetNodes(graph, nullptr, &nodes);
-  std::vector<size_t> cand;
-  if (h->execs.size() >= kExecCache)
-    for (size_t k = 0; k < h->execs.size(); k++)
-      if (h->execs[k].nodes == nodes && h->execs[k].e != exclude) cand.push_back(k);
-  std::sort(cand.begin(), cand.end(), [&](size_t a, size_t b) { return h->execs[a].used < h->execs[b].used; });
+  auto lru_first = [&](std::vector<size_t>& v) {
+    std::sort(v.begin(), v.end(), [&](size_t a, size_t b) { return h->execs[a].used < h->execs[b].used; });
+  };
+  std::vector<size_t> stale, any;
+  for (size_t k = 0; k < h->execs.size(); k++)
+    if (h->execs[k].nodes == nodes && h->execs[k].e != exclude) {
+      any.push_back(k);
+      if (h->execs[k].call != h->call_seq) stale.push_back(k);
+    }
+  lru_first(stale);
+  lru_first(any);
+  std::vector<size_t> cand = stale;
+  if (cand.empty() && h->execs.size() >= kExecCache) cand = any;
   for (size_t k : cand) {
     cudaGraphExecUpdateResultInfo info;
     if (cudaGraphExecUpdate(h->execs[k].e, graph, &info) == cudaSuccess) {
       h->execs[k].used = ++h->exec_clock;
+      h->execs[k].call = h->call_seq;
       h->execs[k].launches = *launches;
       h->execs[k].key = key;
       *exec = h->execs[k].e;
@@ -684,7 +715,7 @@ louvain_status capture_iteration(louvain_handle h, Ctx& c0, const GraphView<type
     cudaGraphExecDestroy(h->execs[lru].e);
     h->execs.erase(h->execs.begin() + (std::ptrdiff_t)lru);
   }
-  h->execs.push_back({*exec, nodes, ++h->exec_clock, *launches, key});
+  h->execs.push_back({*exec, nodes, ++h->exec_clock, *launches, key, h->call_seq});
   return LOUVAIN_OK;
 }
 
@@ -1176,6 +1207,7 @@ louvain_status run_batch_impl(louvain_handle h, Ctx& c, int32_t G, int64_t n, in
 louvain_status begin_call(louvain_handle h) {
   if (!h) return LOUVAIN_ERR_INVALID;
   h->err.clear();
+  h->call_seq++;
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_err(h, e, "cudaSetDevice");
   return LOUVAIN_OK;

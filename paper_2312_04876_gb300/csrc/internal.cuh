@@ -119,9 +119,9 @@ void move_setup(Ctx& c, Ctrl* ctrl, double tau, int max_iterations);
 
 
 // One bucket's decide (+ apply in fast mode) over list[0, count).
-// With `rng` (a step record's {start, count} of this bucket) the kernel reads its range there and
-// list is the base it is offset from; the grid is then the cap (blocks past the range return at
-// once).
+// With `rng` (a step record's {start, count} of this bucket) the kernel reads its range there, list
+// is the base it is offset from and count is an upper bound of the range that sizes the grid
+// (blocks past the range return at once).
 template <class M>
 void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const PassState<M>& st,
                  const int32_t* list, int64_t count, bool fast, bool pruning, const int64_t* rng = nullptr);

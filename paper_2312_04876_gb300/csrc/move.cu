@@ -326,8 +326,8 @@ static void launch_lm(Ctx& c, const LmArgs<M>& a, int max_blocks) {
   constexpr int GPB = G <= 32 ? BS / G : 1;
   constexpr size_t smem = lm_smem<M, G, LOG>();
   lm_attr<M, G, LOG>();
-  // device-resident range: the count is not known here, so the grid is the cap
-  int grid = a.rng ? max_blocks * (kBlock / BS) : grid_for(a.count, GPB, max_blocks * (kBlock / BS));
+  // device-resident range: a.count is then an upper bound of the range (a power of two)
+  const int grid = grid_for(a.count, GPB, max_blocks * (kBlock / BS));
   lm_kernel<M, G, LOG><<<grid, BS, smem, c.s>>>(a);
   c.launches++;
 }

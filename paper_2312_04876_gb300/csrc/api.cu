@@ -975,7 +975,7 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
                   ws.mv_to, ws.ctrl};
   cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), c.s);
   double tau = p.tolerance;
-  bool pending = false;
+  bool pending = false, q_done = false;
   int64_t g_arcs = n_arcs;
   for (int32_t lp = 0; lp < p.max_passes; lp++) {
     const size_t e0 = (size_t)lp * 6 + 1;
@@ -1031,6 +1031,17 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
       if (n_stats) *n_stats = lp + 1;
     }
     const bool stop = li <= 1 || (double)nc / (double)n_cur > p.aggregation_tolerance;
+    if (!M::is_fp && (stop || lp + 1 == p.max_passes)) {
+      // (a10) Eq. 1 of the returned membership, evaluated on this pass's graph and communities: the
+      // aggregation keeps every community's internal weight and total (R1), so with integer weights
+      // (exact super-arc sums) Q(G', C') has the same int64 numerator and denominator as Q on the
+      // input graph of the membership C' maps to, and this pass's degree-bucket lists serve as they
+      // are.  fp32 super-arc weights are rounded sums, so fp32 graphs are evaluated on the input.
+      const int pm = prof_begin(h, c);
+      modularity_bucketed<M>(c, g, ws.Cp, reinterpret_cast<A*>(ws.tot), ws.ctrl, ws.dperm, hb, ws.gpv);
+      prof_end(h, c, kModularity, pm);
+      q_done = true;
+    }
     if (!stop) {
       // (a6) renumber C', dendrogram lookup, K of the next pass = Sigma by new id
       relabel(c, ws.Cp, n_cur, ws.newid);
@@ -1077,12 +1088,14 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
   mark_occupied(c, C, n, ws.occ, g.n);
   scan_exclusive_i32(c, ws.occ, ws.newid, g.n, ws.tile_tmp);
   relabel(c, C, n, ws.newid);
-  // (a10) Eq. 1 on the input graph
-  const int pm = prof_begin(h, c);
-  int64_t hb0[kNumBuckets + 1], gs0 = 0;
-  if ((s = degree_buckets(h, c, g0, hb0, &gs0)) != LOUVAIN_OK) return s;
-  modularity_bucketed<M>(c, g0, C, reinterpret_cast<A*>(ws.tot), ws.ctrl, ws.dperm, hb0, ws.gpv);
-  prof_end(h, c, kModularity, pm);
+  if (!q_done) {
+    // (a10) fp32 weights, or no pass ran: Eq. 1 on the input graph
+    const int pm = prof_begin(h, c);
+    int64_t hb0[kNumBuckets + 1], gs0 = 0;
+    if ((s = degree_buckets(h, c, g0, hb0, &gs0)) != LOUVAIN_OK) return s;
+    modularity_bucketed<M>(c, g0, C, reinterpret_cast<A*>(ws.tot), ws.ctrl, ws.dperm, hb0, ws.gpv);
+    prof_end(h, c, kModularity, pm);
+  }
   const Ctrl* hc = read_ctrl(h, c, &s, "final modularity");
   if (!hc) return s;
   if (hc->error) return set_err(h, LOUVAIN_ERR_CUDA, "internal: hash table overflow");

@@ -1,4 +1,4 @@
-// giant.cu -- the multi-block path for giant rows (degree bucket 5, > 4096 arcs).
+// giant.cu -- the multi-block path for giant rows (the last degree bucket: rows longer than the giant threshold, 4096 arcs by default).
 //
 // A hub vertex (R-MAT hubs reach 10^5 arcs) or a giant community (10^6-10^7 member arcs after a
 // pass) handled by one block serialises a whole launch on one SM.  Here the work of a giant is cut

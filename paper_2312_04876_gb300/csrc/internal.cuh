@@ -72,7 +72,7 @@ struct KeyDesc {
 // left out.  hist must hold nkeys + 1 int64; cursor nkeys int32.  Writes perm and offsets[nkeys+1]
 // (device).
 // max_deg (device, optional) receives the largest row length / deg64 value seen (atomicMax);
-// giant_slots (device, optional) the summed table size of the bucket-4 items, each
+// giant_slots (device, optional) the summed table size of the giant-bucket items, each
 // 2^tbl_log2(min(deg, n_bound), 6, 40).
 void bucket_sort(Ctx& c, KeyDesc key_kind, int64_t n, const int64_t* rbeg, const int64_t* rend, const int32_t* colour,
                  const int64_t* deg64, int64_t nkeys, int32_t* perm, int64_t* offsets, int32_t* cursor,

@@ -56,10 +56,11 @@ struct Ctrl {
 };
 
 // Adds K per-thread counters of a whole block to dst[0..K) (one atomic per counter per block).
-// Every thread of the block must call it.
-template <int K>
+// Every thread of the block must call it; the block has at most W warps (the merge kernels keep
+// W = 32: their smaller footprint let more blocks share an SM's L1 and measured slower).
+template <int K, int W = 32>
 __device__ __forceinline__ void block_add_counters(unsigned long long* dst, unsigned long long (&v)[K]) {
-  __shared__ unsigned long long part[K][32];
+  __shared__ unsigned long long part[K][W];
 #pragma unroll
   for (int k = 0; k < K; k++) {
 #pragma unroll
@@ -205,7 +206,7 @@ struct Grp {
   }
 };
 
-// Sum over a group.  Block groups use `scratch` (>= 32 elements of T) in shared memory.
+// Sum over a group.  Block groups use `scratch` (>= G / 32 elements of T) in shared memory.
 template <int G, class T>
 __device__ __forceinline__ T group_sum(T v, T* scratch) {
   if (G <= 32) {

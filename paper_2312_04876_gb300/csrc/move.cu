@@ -99,12 +99,16 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
   extern __shared__ __align__(16) unsigned char lm_dyn[];  // GPB tables of SL (key, value) slots
   int32_t* skeys = reinterpret_cast<int32_t*>(lm_dyn);
   H* svals = reinterpret_cast<H*>(lm_dyn + sizeof(int32_t) * GPB * SL);
-  __shared__ S red_s[32];
-  __shared__ int32_t red_c[32];
-  __shared__ H red_h[32];
-  __shared__ int32_t red_i[32];
-  __shared__ unsigned long long r_lo[32], r_hi[32], r_mv[32];
-  __shared__ double r_f[32];
+  // per-warp reduction scratch, sized by the block's warps: static shared memory counts against
+  // the blocks an SM holds (13 instead of 11 two-warp blocks of 1024-slot tables)
+  constexpr int NW = BS / 32;
+  static_assert(BS % 32 == 0 && BS <= kBlock, "whole warps, at most kBlock threads");
+  __shared__ S red_s[NW];
+  __shared__ int32_t red_c[NW];
+  __shared__ H red_h[NW];
+  __shared__ int32_t red_i[NW];
+  __shared__ unsigned long long r_lo[NW], r_hi[NW], r_mv[NW];
+  __shared__ double r_f[NW];
 
   const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
   const unsigned lane = Grp<G>::lane();
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
     }
   }
   flush_move_acc<M::is_fp>(ctrl, acc_lo, acc_hi, acc_mv, acc_f, r_lo, r_hi, r_mv, r_f);
-  block_add_counters<6>(ctrl->lm_stat[a.bucket], ctr);
+  block_add_counters<6, NW>(ctrl->lm_stat[a.bucket], ctr);
 }
 
 template <class M, int G, int LOG>

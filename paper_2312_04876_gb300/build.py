@@ -1,7 +1,7 @@
 """Builds liblouvain.so (the CUDA library behind include/louvain.h) in-tree for sm_103a.
 
-Each .cu file is compiled to an object in parallel (one -gencode, so a build takes about a
-minute), then linked with the static CUDA runtime into paper_2312_04876_gb300/_build/.
+Each .cu file is compiled to an object in parallel (one -gencode, so a build takes seconds with
+a core per file), then linked with the static CUDA runtime into paper_2312_04876_gb300/_build/.
 """
 from __future__ import annotations
 

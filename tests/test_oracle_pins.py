@@ -239,6 +239,28 @@ def test_ring_of_cliques_recovered(schedule):
     assert q == float(Fraction(s * (s - 1), s * (s - 1) + 2) - Fraction(1, k))
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_karate_club_below_published_optimum(schedule):
+    """Zachary's karate club (networkx's copy, unweighted): the maximum modularity over all
+    partitions is 0.4197896, proved optimal by integer linear programming (Brandes et al., "On
+    Modularity Clustering", IEEE TKDE 2008).  Louvain may not exceed it and lands close to it; its
+    Q is a rational with denominator (2m)^2 in integer mode and equals networkx's Eq. 1."""
+    nx = pytest.importorskip("networkx")
+    kc = nx.karate_club_graph()
+    edges = sorted((min(u, v), max(u, v)) for u, v in kc.edges())
+    assert kc.number_of_nodes() == 34 and len(edges) == 78
+    g = gg.from_edges(34, edges)
+    mem, q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params(schedule=schedule))
+    assert 0.41 <= q <= 0.4197896 + 1e-7
+    two_m = 2 * len(edges)
+    assert abs(q * two_m * two_m - round(q * two_m * two_m)) < 1e-6
+    h = nx.Graph()
+    h.add_nodes_from(range(34))
+    h.add_edges_from(edges)
+    parts = [set(np.flatnonzero(mem == c).tolist()) for c in np.unique(mem)]
+    assert q == pytest.approx(nx.community.modularity(h, parts), abs=1e-12)
+
+
 def test_planted_partition_sbm_10k():
     g = gg.sbm(10000, 100, 0.1, 0.0005, 1)
     planted = gg.planted_blocks(10000, 100)

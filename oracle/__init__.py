@@ -11,7 +11,8 @@ Parity status of each function (what pins it lives in tests/test_oracle_pins.py)
   colour ............ pinned (properness; complete graphs; brute-force greedy on tiny graphs)
   aggregate ......... pinned (numpy scatter-add of community pairs; Q invariance; 2m invariance)
   local_move/louvain  pinned (brute-force optimum on <= 9 vertices; clique rings; planted SBM;
-                      hand-traced two-vertex/triangle cases)
+                      hand-traced two-vertex/triangle cases; the karate club's published optimum;
+                      tolerance limits and the single-move optimum at tolerance 0)
 """
 from __future__ import annotations
 

@@ -120,6 +120,63 @@ def test_move_score_equals_exact_delta_q(seed, loops):
                 assert Fraction(2 * nscore, two_m * two_m) == q_exact(a, m2) - q0
 
 
+# ---------------------------------------------------------------- convergence of the local-moving phase
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_local_move_tolerance_limits(schedule):
+    """Algorithm 2's per-iteration test: an infinite tolerance ends the phase after its first
+    iteration; MAX_ITERATIONS caps the count; every iteration but a converged one moves something."""
+    rng = np.random.default_rng(7)
+    g = random_graph(40, 0.15, rng)
+    _, it_inf, mv_inf = oracle.local_move(g.offsets, g.targets, g.weights,
+                                           oracle.default_params(schedule=schedule), tau=float("inf"))
+    assert it_inf == 1 and mv_inf > 0
+    for cap in (1, 2, 3):
+        _, it, _ = oracle.local_move(g.offsets, g.targets, g.weights,
+                                     oracle.default_params(schedule=schedule, max_iterations=cap), tau=0.0)
+        assert it <= cap
+    _, it0, mv0 = oracle.local_move(g.offsets, g.targets, g.weights,
+                                    oracle.default_params(schedule=schedule, max_iterations=1000), tau=0.0)
+    assert it0 >= 2 and mv0 >= it0 - 1  # the last iteration may move nothing; every earlier one moved
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_local_move_zero_tolerance_reaches_single_move_optimum(seed, schedule):
+    """With tolerance 0 and pruning off the phase stops only after an iteration with no move, so
+    no single vertex can then raise Q by changing to a neighbouring community: every such move has
+    exact Delta Q <= 0 (Eq. 1 evaluated before and after, in rationals).  The sequential schedule
+    raises Q with every move and must stop.  The colour-synchronous one need not: vertices of a
+    class that join one community together lose a cross term -2 K_u K_v / (2m)^2 that neither
+    score sees, and seed 0 settles into a two-iteration cycle (Q 0.19216 / 0.16723), which is what
+    the paper's positive tolerance and iteration cap bound."""
+    rng = np.random.default_rng(100 + seed)
+    g = random_graph(12, 0.35, rng, self_loops=seed % 2 == 1)
+    a = dense_adjacency(g)
+    cap = 1000
+
+    def run(max_it):
+        return oracle.local_move(g.offsets, g.targets, g.weights,
+                                 oracle.default_params(schedule=schedule, pruning=0, max_iterations=max_it),
+                                 tau=0.0)
+
+    cp, it, _ = run(cap)
+    if schedule == 0 and seed == 0:
+        assert it == cap
+        cp1, _, _ = run(cap + 1)
+        cp2, _, _ = run(cap + 2)
+        assert q_exact(a, cp1) < q_exact(a, cp) and same_partition(cp2, cp)
+        return
+    assert it < cap
+    q0 = q_exact(a, cp)
+    for i in range(g.n):
+        for c in {int(cp[j]) for j in np.flatnonzero(a[i]) if j != i}:
+            if c == cp[i]:
+                continue
+            m2 = cp.copy()
+            m2[i] = c
+            assert q_exact(a, m2) - q0 <= 0
+
+
 # ---------------------------------------------------------------- colouring (deterministic schedule)
 def _greedy_reference(g, seed, pass_index):
     order = sorted(range(g.n), key=lambda v: (gg.hash3(seed, pass_index, v), v), reverse=True)

@@ -62,7 +62,7 @@ struct Workspace {
   unsigned* gt_bits = nullptr;
   int32_t* pool = nullptr;    // giant-row table pool: gt_slots_total {key, value} pairs
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
-  DevAlloc desc_alloc;        // step records and the pass GraphView of captured iterations
+  DevAlloc desc_alloc;        // step records of captured iterations (kStepWords per class step)
   int64_t* desc = nullptr;
   int64_t desc_cap = 0;       // int64 words
   int32_t* glist = nullptr;   // [gcap] giant vertices of a pass, class by class

@@ -136,6 +136,23 @@ def test_local_move_deterministic_bit_exact(L, name, pruning):
     assert np.array_equal(cp.cpu().numpy(), ref_cp)
 
 
+@pytest.mark.parametrize("seed,cap", [(0, 100), (0, 101), (1, 1000), (3, 1000)])
+def test_local_move_zero_tolerance_bit_exact(L, seed, cap):
+    """Tolerance 0 without pruning: a phase ends only after an iteration with no move, or at
+    MAX_ITERATIONS where the colour-synchronous schedule cycles (seed 0 settles into a period-2
+    cycle; caps 100 and 101 stop it in either phase).  The GPU stops at the same iteration with the
+    same C' and move count."""
+    g = random_graph(12, 0.35, np.random.default_rng(100 + seed), self_loops=seed % 2 == 1)
+    o, t, w = dev(g)
+    cp, it, mv = L.local_move(o, t, w, tau=0.0, mode="deterministic", pruning=0, seed=0, max_iterations=cap)
+    ref_cp, ref_it, ref_mv = oracle.local_move(g.offsets, g.targets, g.weights,
+                                               oracle.default_params(pruning=0, seed=0, max_iterations=cap), 0,
+                                               tau=0.0)
+    assert (it, mv) == (ref_it, ref_mv)
+    assert np.array_equal(cp.cpu().numpy(), ref_cp)
+    assert (it == cap) == (seed == 0)
+
+
 # ---------------------------------------------------------------- whole method
 @pytest.mark.parametrize("name", ["sbm2k", "sbm10k_cfg1", "rmat12", "rmat14", "rmat16", "loops", "grid", "ring", "star",
                                   "star20k"])

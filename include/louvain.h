@@ -131,7 +131,8 @@ void louvain_destroy(louvain_handle h);
 
 /* Defaults from Section 4.1: max_iterations 20, tolerance 0.01, tolerance_drop 10,
  * aggregation_tolerance 0.8, pruning on; max_passes 10; deterministic mode; seed 0;
- * validate 1; compact 1; pass_modularity 0; profile 0; fast_classes 16. */
+ * validate 1; compact 1; pass_modularity 0; profile 0; fast_classes 16; fast_classes_later 1;
+ * fast_giant_class, lm_blocks_per_sm and giant_min_degree 0 (their built-in choices). */
 louvain_status louvain_default_params(louvain_params* p);
 
 /* Message of the last failure on this handle ("" if none).  Valid until the next call. */

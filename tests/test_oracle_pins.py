@@ -318,6 +318,24 @@ def test_karate_club_below_published_optimum(schedule):
     assert q == pytest.approx(nx.community.modularity(h, parts), abs=1e-12)
 
 
+@pytest.mark.parametrize("tau_agg,passes", [(0.8, 1), (0.96, 1), (101 / 105, 2), (0.97, 2)])
+def test_aggregation_tolerance_stops_the_pass_loop(tau_agg, passes):
+    """Algorithm 1 stops after a pass whose community count is more than tau_agg of its vertices.
+    A 5-clique plus 100 isolated vertices: pass 0 merges the clique, |Gamma| / |V'| = 101 / 105 =
+    0.9619; a larger ratio than tau_agg (strictly) ends the run, otherwise the aggregated graph gets
+    a second pass, which moves nothing and ends after one iteration.  Q = 1 - 1^2 = 0 (one
+    community holds every edge)."""
+    g = gg.from_edges(105, [(i, j) for i in range(5) for j in range(i + 1, 5)])
+    mem, q, n_passes, stats = oracle.louvain(g.offsets, g.targets, g.weights,
+                                             oracle.default_params(aggregation_tolerance=tau_agg))
+    assert n_passes == passes
+    assert (stats[0]["n_vertices"], stats[0]["n_communities"]) == (105, 101)
+    if passes == 2:
+        assert (stats[1]["n_vertices"], stats[1]["iterations"], stats[1]["moves"]) == (101, 1, 0)
+    assert same_partition(mem, [0] * 5 + list(range(1, 101)))
+    assert q == 0.0
+
+
 def test_planted_partition_sbm_10k():
     g = gg.sbm(10000, 100, 0.1, 0.0005, 1)
     planted = gg.planted_blocks(10000, 100)

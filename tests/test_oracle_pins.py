@@ -336,6 +336,39 @@ def test_aggregation_tolerance_stops_the_pass_loop(tau_agg, passes):
     assert q == 0.0
 
 
+def _replay_passes(g, p, next_tau):
+    """Algorithm 1's loop written out over the single steps (each pinned on its own): local moving
+    from singletons with the pass's tolerance, renumbering by rank, the two pass tests, aggregation,
+    then the next tolerance.  Returns (iterations, moves) per pass."""
+    offs, tg, w = g.offsets, g.targets, g.weights
+    tau, seq = p.tolerance, []
+    for k in range(p.max_passes):
+        cp, it, mv = oracle.local_move(offs, tg, w, p, k, tau=tau)
+        seq.append((it, mv))
+        ids = np.unique(cp)
+        if it <= 1 or len(ids) / len(cp) > p.aggregation_tolerance:
+            break
+        offs, tg, w = oracle.aggregate(offs, tg, w, np.searchsorted(ids, cp).astype(np.int32), len(ids))
+        tau = next_tau(tau, p.tolerance_drop)
+    return seq
+
+
+@pytest.mark.parametrize("name", ["sbm2k", "rmat12", "rmat14"])
+def test_threshold_scaling_between_passes(name):
+    """Threshold scaling (Section 4.1.3): pass p runs with tolerance tau_0 / drop^p.  The run's
+    per-pass iterations and moves equal the replay that divides, and differ from replays that
+    multiply or keep tau (so the check sees the drop's direction)."""
+    g = {"sbm2k": lambda: gg.sbm(2000, 20, 0.1, 0.002, 7),
+         "rmat12": lambda: gg.rmat(12, weights=gg.W_INT8, seed=3),
+         "rmat14": lambda: gg.rmat(14, weights=gg.W_INT8, seed=22)}[name]()
+    p = oracle.default_params()
+    _, _, passes, stats = oracle.louvain(g.offsets, g.targets, g.weights, p)
+    run = [(s["iterations"], s["moves"]) for s in stats]
+    assert passes >= 2 and run == _replay_passes(g, p, lambda t, d: t / d)
+    assert run != _replay_passes(g, p, lambda t, d: t * d)
+    assert run != _replay_passes(g, p, lambda t, d: t)
+
+
 def test_planted_partition_sbm_10k():
     g = gg.sbm(10000, 100, 0.1, 0.0005, 1)
     planted = gg.planted_blocks(10000, 100)

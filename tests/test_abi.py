@@ -67,3 +67,11 @@ def test_null_handle_is_rejected(lib):
     lib.louvain_run.restype = ctypes.c_int32
     rc = lib.louvain_run(None, 0, 0, None, None, None, 0, None, None, None, None, None, 0, None)
     assert rc == 1
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """The product path has no CPU fallback: without the built library every entry point raises."""
+    from paper_2312_04876_gb300 import _native
+    monkeypatch.setattr(_native, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _native.load(str(tmp_path / "liblouvain.so"))

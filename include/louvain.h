@@ -93,6 +93,11 @@ typedef struct {
                                     holds in flight (small graphs keep every class on its own).  The
                                     first iteration, where most vertices move, takes every class on
                                     its own */
+  int32_t wait_spins;            /* bound of the device-side waits (the colouring's grid barrier in
+                                    deterministic mode): polls of about 64 ns each before a waiting
+                                    block gives up (0 = built-in, about 0.3 s).  A wait that runs out
+                                    ends the kernel on every block and the call returns
+                                    LOUVAIN_ERR_TIMEOUT; the handle stays usable */
 } louvain_params;
 
 typedef struct {
@@ -132,8 +137,18 @@ void louvain_destroy(louvain_handle h);
 /* Defaults from Section 4.1: max_iterations 20, tolerance 0.01, tolerance_drop 10,
  * aggregation_tolerance 0.8, pruning on; max_passes 10; deterministic mode; seed 0;
  * validate 1; compact 1; pass_modularity 0; profile 0; fast_classes 16; fast_classes_later 1;
- * fast_giant_class, lm_blocks_per_sm and giant_min_degree 0 (their built-in choices). */
+ * fast_giant_class, lm_blocks_per_sm, giant_min_degree and wait_spins 0 (their built-in choices). */
 louvain_status louvain_default_params(louvain_params* p);
+
+/* Device bytes the handle holds now: every workspace buffer it allocated and has not freed
+ * (grown on demand, kept across calls, released by louvain_destroy).  *bytes (host). */
+louvain_status louvain_workspace_bytes(louvain_handle h, size_t* bytes);
+
+/* Fault injection for tests of the out-of-memory path (the paper has no counterpart): the k-th
+ * device allocation the handle makes from now on (k >= 1) fails once, as if cudaMalloc had run
+ * out of memory; k = 0 cancels.  The call that meets the failure returns LOUVAIN_ERR_OOM and the
+ * handle stays usable.  LOUVAIN_ERR_INVALID for k < 0. */
+louvain_status louvain_inject_alloc_failure(louvain_handle h, int32_t k);
 
 /* Message of the last failure on this handle ("" if none).  Valid until the next call. */
 const char* louvain_last_error(louvain_handle h);

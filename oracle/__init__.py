@@ -26,6 +26,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "louvain_oracle.cpp")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _SO = os.path.join(_OUT_DIR, "liboracle.so")
+# A test that plants a mistake in a copy of the oracle points this variable at the copy's build.
+_SO_OVERRIDE = os.environ.get("LOUVAIN_ORACLE_SO")
 
 SCHEDULE_COLOUR_SYNC = 0
 SCHEDULE_SEQUENTIAL = 1
@@ -73,7 +75,7 @@ _P = ctypes.c_void_p
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(_SO_OVERRIDE or build())
         lib.oracle_hash3.restype = ctypes.c_uint64
         lib.oracle_hash3.argtypes = [ctypes.c_uint64] * 3
         lib.oracle_modularity.restype = ctypes.c_double

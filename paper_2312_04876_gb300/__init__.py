@@ -6,7 +6,8 @@ and streams.  If the library is missing the calls raise -- there is no CPU fallb
 
     import torch, paper_2312_04876_gb300 as lv
     L = lv.Louvain(device=0)
-    membership, result, stats = L.run(offsets, targets, weights, mode="fast")
+    membership, result = L.run(offsets, targets, weights, mode="fast")
+    result.modularity, result.passes, result.stats   # per-pass statistics in result.stats
 """
 from __future__ import annotations
 
@@ -47,18 +48,36 @@ def default_params(**overrides) -> Params:
 STATIC_SCAN_MAX = 1 << 26
 
 
+def _check_scan_args(values, out):
+    """The scan kernels read values[0, n) and write out[0, n]: both must be contiguous int64 CUDA
+    tensors on one device, out holding at least n + 1 elements."""
+    import torch
+    if not isinstance(values, torch.Tensor) or values.dtype != torch.int64 or not values.is_cuda \
+            or not values.is_contiguous():
+        raise ValueError("values must be a contiguous int64 CUDA tensor")
+    if out is not None:
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.int64 or not out.is_cuda \
+                or not out.is_contiguous() or out.device != values.device:
+            raise ValueError("out must be a contiguous int64 CUDA tensor on the device of values")
+        if out.numel() < values.numel() + 1:
+            raise ValueError(f"out holds {out.numel()} elements; the scan writes {values.numel() + 1}")
+
+
 def exclusive_scan_static(values, out=None, stream=None):
     """Exclusive scan through louvain_exclusive_scan_static, the entry point that allocates
     nothing (scratch in a fixed device array; at most 2^26 elements; no handle).  For callers that
-    cannot call cudaMalloc.  Returns (out int64 tensor of numel + 1, total)."""
+    cannot call cudaMalloc.  Runs on the device of `values`.  Returns (out int64 tensor of at least
+    numel + 1 elements, total)."""
     import torch
+    _check_scan_args(values, out)
     lib = _native.load()
     n = values.numel()
-    if out is None:
-        out = torch.empty(n + 1, dtype=torch.int64, device=values.device)
-    tot = ctypes.c_int64()
-    st = lib.louvain_exclusive_scan_static(values.data_ptr(), out.data_ptr(), n, _stream_ptr(stream),
-                                           ctypes.byref(tot))
+    with torch.cuda.device(values.device):
+        if out is None:
+            out = torch.empty(n + 1, dtype=torch.int64, device=values.device)
+        tot = ctypes.c_int64()
+        st = lib.louvain_exclusive_scan_static(values.data_ptr(), out.data_ptr(), n, _stream_ptr(stream),
+                                               ctypes.byref(tot))
     if st != _native.OK:
         raise LouvainError(st, f"louvain_exclusive_scan_static(count={n}) failed")
     return out, int(tot.value)
@@ -193,6 +212,16 @@ class Louvain:
             self.close()
         except Exception:
             pass
+
+    def workspace_bytes(self) -> int:
+        """Device bytes the handle's workspace holds now (louvain_workspace_bytes)."""
+        b = ctypes.c_size_t()
+        self._check(self._lib.louvain_workspace_bytes(self._h, ctypes.byref(b)))
+        return int(b.value)
+
+    def inject_alloc_failure(self, k: int) -> None:
+        """Make the k-th device allocation from now fail once (testing the out-of-memory path)."""
+        self._check(self._lib.louvain_inject_alloc_failure(self._h, k))
 
     def _check(self, st: int):
         if st != _native.OK:
@@ -368,6 +397,9 @@ class Louvain:
 
     def exclusive_scan(self, values, stream=None):
         import torch
+        _check_scan_args(values, None)
+        if values.device != torch.device("cuda", self.device):
+            raise ValueError(f"values live on {values.device}; this handle runs on cuda:{self.device}")
         out = torch.empty(values.numel() + 1, dtype=torch.int64, device=values.device)
         tot = ctypes.c_int64()
         rc = self._lib.louvain_exclusive_scan(self._h, values.data_ptr(), out.data_ptr(), values.numel(),

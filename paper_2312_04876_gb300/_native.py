@@ -20,7 +20,7 @@ class Params(ctypes.Structure):
                 ("compact", ctypes.c_int32), ("pass_modularity", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("fast_classes", ctypes.c_int32), ("fast_giant_class", ctypes.c_int32),
                 ("lm_blocks_per_sm", ctypes.c_int32), ("giant_min_degree", ctypes.c_int32),
-                ("fast_classes_later", ctypes.c_int32)]
+                ("fast_classes_later", ctypes.c_int32), ("wait_spins", ctypes.c_int32)]
 
 
 class PassStats(ctypes.Structure):
@@ -64,6 +64,8 @@ SIGNATURES = {
     "louvain_default_params": (_I32, [ctypes.POINTER(Params)]),
     "louvain_last_error": (ctypes.c_char_p, [_V]),
     "louvain_status_string": (ctypes.c_char_p, [_I32]),
+    "louvain_workspace_bytes": (_I32, [_V, ctypes.POINTER(ctypes.c_size_t)]),
+    "louvain_inject_alloc_failure": (_I32, [_V, _I32]),
     "louvain_run": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V, _V, ctypes.POINTER(Result),
                            ctypes.POINTER(PassStats), _I32, ctypes.POINTER(_I32)]),
     "louvain_run_host": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V, _V,

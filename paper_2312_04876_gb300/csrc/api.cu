@@ -148,6 +148,7 @@ struct louvain_handle_s {
   int64_t* dpin = nullptr;         // pinned staging of the step records
   int64_t dpin_cap = 0;
   uint64_t call_seq = 0;           // API calls so far (begin_call)
+  int64_t fail_alloc_in = 0;       // > 0: the fail_alloc_in-th device allocation from now fails (injected)
 };
 
 constexpr size_t kExecCache = 16;
@@ -179,6 +180,7 @@ bool dalloc(louvain_handle h, DevAlloc& a, T** p, int64_t count) {
   size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
   bytes = (bytes + 255) & ~(size_t)255;
   if (h->budget && total_bytes(h->ws) + bytes > h->budget) return false;
+  if (h->fail_alloc_in > 0 && --h->fail_alloc_in == 0) return false;  // louvain_inject_alloc_failure
   void* q = nullptr;
   if (cudaMalloc(&q, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -425,6 +427,7 @@ bool valid_params(const louvain_params* p) {
          p->aggregation_tolerance >= 0.0 && p->fast_classes >= 0 && p->fast_classes <= 4096 &&
          p->lm_blocks_per_sm >= 0 && p->lm_blocks_per_sm <= 64 && p->fast_classes_later >= 0 &&
          (p->giant_min_degree == 0 || (p->giant_min_degree >= 2048 && p->giant_min_degree <= 4096)) &&
+         p->wait_spins >= 0 &&
          (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
 }
 
@@ -456,14 +459,21 @@ struct RunOut {
   int64_t n_communities = 0;
 };
 
-louvain_status colour_failure(louvain_handle h) {
+// A colouring that did not colour every listed vertex: a grid-barrier wait that ran out (the
+// kernel left on every block) is LOUVAIN_ERR_TIMEOUT, anything else an internal error.
+louvain_status colour_failure(louvain_handle h, Ctx& c) {
   const unsigned long long* q = h->pin;
   char buf[256];
   snprintf(buf, sizeof buf,
-           "internal: colouring did not finish (coloured %llu of %llu after %llu rounds, max colour %llu, "
-           "guard trips %llu)",
+           "colouring did not finish (coloured %llu of %llu after %llu rounds, max colour %llu, guard trips %llu)",
            q[3], q[5], q[6], q[4], q[7]);
-  return set_err(h, LOUVAIN_ERR_CUDA, buf);
+  const std::string what = buf;
+  louvain_status st;
+  const Ctrl* hc = read_ctrl(h, c, &st, "colouring end");
+  if (!hc) return st;
+  if (hc->error & kErrTimeout)
+    return set_err(h, LOUVAIN_ERR_TIMEOUT, "a bounded grid-barrier wait of the colouring ran out: " + what);
+  return set_err(h, LOUVAIN_ERR_CUDA, "internal: " + what);
 }
 
 // Per-pass degree buckets of graph g into ws.dperm with host offsets hb[kNumBuckets + 1];
@@ -752,7 +762,7 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
     ncol = jp_colour(c, gs, ws.dperm, hb, p.seed, pass, ws.colour, jb, ws.ctrl, h->pin, &ce, seg, &rounds);
     prof_end(h, c, kColour, pm);
     if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
-    if (ncol < 0) return colour_failure(h);
+    if (ncol < 0) return colour_failure(h, c);
     if (colours) *colours = ncol;
     if (colour_rounds) *colour_rounds = (int32_t)rounds;
     const int64_t nkeys = (int64_t)ncol * kNumBuckets;
@@ -1388,6 +1398,18 @@ void louvain_destroy(louvain_handle h) {
 
 const char* louvain_last_error(louvain_handle h) { return h ? h->err.c_str() : "invalid handle"; }
 
+louvain_status louvain_workspace_bytes(louvain_handle h, size_t* bytes) {
+  if (!h || !bytes) return LOUVAIN_ERR_INVALID;
+  *bytes = total_bytes(h->ws);
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_inject_alloc_failure(louvain_handle h, int32_t k) {
+  if (!h || k < 0) return LOUVAIN_ERR_INVALID;
+  h->fail_alloc_in = k;
+  return LOUVAIN_OK;
+}
+
 louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64_t* graph_vtx_offs, int64_t n_arcs,
                                  const int64_t* d_offsets, const int32_t* d_targets, const void* d_weights,
                                  louvain_wtype wtype, const louvain_params* p, void* stream, int32_t* d_membership,
@@ -1411,6 +1433,7 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
   if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
+  if (p) c.wait_spins = p->wait_spins;
   h->prof.on = p->profile != 0;
   h->prof.used = 0;
   h->prof.recs.clear();
@@ -1501,6 +1524,7 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
   if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
+  if (p) c.wait_spins = p->wait_spins;
   if (res) std::memset(res, 0, sizeof(*res));
   if (n_stats) *n_stats = 0;
   h->prof.on = p->profile != 0;
@@ -1658,7 +1682,7 @@ louvain_status louvain_colour(louvain_handle h, int64_t n, int64_t n_arcs, const
   cudaError_t ce;
   int32_t nc = jp_colour(c, g, h->ws.dperm, hb, seed, pass, d_colour, jb, ctrl, h->pin, &ce);
   if (ce != cudaSuccess) return cuda_err(h, ce, "colouring");
-  if (nc < 0) return colour_failure(h);
+  if (nc < 0) return colour_failure(h, c);
   *n_colours = nc;
   return sync(h, c, "colour end");
 }
@@ -1677,6 +1701,7 @@ louvain_status louvain_local_move(louvain_handle h, int64_t n, int64_t n_arcs, c
   c.s = reinterpret_cast<cudaStream_t>(stream);
   c.num_sms = h->num_sms;
   if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
+  if (p) c.wait_spins = p->wait_spins;
   if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
   if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
   const bool fp = wtype == LOUVAIN_W_FP32;

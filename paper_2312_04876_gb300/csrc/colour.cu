@@ -209,7 +209,7 @@ struct GridBar {
 };
 
 // Returns false (on every block, at this or the next barrier) once any block has timed out.
-__device__ __forceinline__ bool grid_barrier(const GridBar& b, Ctrl* ctrl) {
+__device__ __forceinline__ bool grid_barrier(const GridBar& b, Ctrl* ctrl, long long max_spins) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -223,7 +223,7 @@ __device__ __forceinline__ bool grid_barrier(const GridBar& b, Ctrl* ctrl) {
     } else {
       long long spins = 0;
       while (*(volatile unsigned*)b.gen == g) {
-        if (++spins > kBarrierSpins || (*(volatile int32_t*)&ctrl->error & kErrTimeout)) {
+        if (++spins > max_spins || (*(volatile int32_t*)&ctrl->error & kErrTimeout)) {
           atomicOr(&ctrl->error, kErrTimeout);
           ok = 0;
           break;
@@ -239,15 +239,16 @@ __device__ __forceinline__ bool grid_barrier(const GridBar& b, Ctrl* ctrl) {
   return ok_s != 0;
 }
 
-__global__ void __launch_bounds__(kBlock) jp_persistent(JpArgs a, GridBar bar, unsigned long long max_rounds) {
+__global__ void __launch_bounds__(kBlock) jp_persistent(JpArgs a, GridBar bar, unsigned long long max_rounds,
+                                                       long long max_spins) {
   __shared__ unsigned long long done_blk;
   __shared__ int32_t max_blk;
   for (unsigned long long r = 0; r < max_rounds; r++) {
     if (*(volatile unsigned long long*)&a.rcount[r] == 0) break;  // nothing ready: coloured (or stuck)
     jp_round_body(a, r, &done_blk, &max_blk);
-    if (!grid_barrier(bar, a.ctrl)) return;
+    if (!grid_barrier(bar, a.ctrl, max_spins)) return;
     jp_big_body(a, r);
-    if (!grid_barrier(bar, a.ctrl)) return;
+    if (!grid_barrier(bar, a.ctrl, max_spins)) return;
   }
 }
 
@@ -313,7 +314,8 @@ int32_t jp_colour(Ctx& c, const GraphView<int32_t>& g, const int32_t* perm, cons
       GridBar bar{reinterpret_cast<unsigned*>(jb.round + 1), reinterpret_cast<unsigned*>(jb.round + 2)};
       cudaMemsetAsync(jb.round + 1, 0, 2 * sizeof(unsigned long long), c.s);
       unsigned long long mr = (unsigned long long)max_rounds;
-      void* args[] = {(void*)&a, (void*)&bar, (void*)&mr};
+      long long spins = c.wait_spins > 0 ? c.wait_spins : kBarrierSpins;
+      void* args[] = {(void*)&a, (void*)&bar, (void*)&mr, (void*)&spins};
       const int blocks = c.num_sms * (per_sm < 2 ? per_sm : 2);
       if (cudaLaunchCooperativeKernel((const void*)jp_persistent, blocks, kBlock, args, 0, c.s) == cudaSuccess) {
         c.launches++;

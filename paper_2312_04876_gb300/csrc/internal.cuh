@@ -15,6 +15,7 @@ struct Ctx {
   int num_sms = 152;
   int lm_blocks_per_sm = 16;  // grid cap of the local-moving kernels (blocks per SM)
   int64_t giant_min = 4096;   // rows longer than this take the giant path (2048..4096)
+  long long wait_spins = 0;   // polls of a bounded device wait before it gives up (0 = built-in)
 };
 
 inline int grid_for(int64_t work_items, int items_per_block, int cap) {

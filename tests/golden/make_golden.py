@@ -27,6 +27,8 @@ WORKLOADS = {
     "sbm10k": lambda: gg.sbm(10000, 100, 0.1, 0.0005, 1),
     # road-like: 4899 x 4899 lattice (~24.0M vertices), 10% of the edges deleted, 1% long links
     "grid24m": lambda: gg.grid(4899, 4899, 0.10, 0.01, 3),
+    # fp32 weights in (0, 1]; 172 rows over 4096 arcs (the giant-row path), maximum degree 25,238
+    "rmat18_fp32": lambda: gg.rmat(18, 16, 0.57, 0.19, 0.19, 18, gg.W_FP32),
 }
 
 

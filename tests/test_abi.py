@@ -75,3 +75,20 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_native, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _native.load(str(tmp_path / "liblouvain.so"))
+
+
+def test_scan_wrappers_refuse_bad_tensors_before_any_library_call(monkeypatch):
+    """The scan kernels read values[0, n) and write out[0, n] through raw pointers: a CPU tensor,
+    another dtype or a strided view is refused by the binding before the library is touched."""
+    import torch
+    import paper_2312_04876_gb300 as lv
+    from paper_2312_04876_gb300 import _native
+
+    def no_library(*a, **k):
+        raise AssertionError("library called")
+
+    monkeypatch.setattr(_native, "load", no_library)
+    for bad in (torch.arange(10, dtype=torch.int64), torch.arange(10, dtype=torch.int32),
+                torch.arange(20, dtype=torch.int64)[::2], [1, 2, 3]):
+        with pytest.raises(ValueError):
+            lv.exclusive_scan_static(bad)

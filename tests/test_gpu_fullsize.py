@@ -1,5 +1,6 @@
 """Full-size parity: the 10k SBM, R-MAT scale 20 and 22 and the 24M-vertex road-like grid against the
-CPU oracle's stored results, and R-MAT scale 27 with fp32 weights by invariants.
+CPU oracle's stored results, R-MAT scale 18 with fp32 weights (hub rows over 4096 arcs) against the
+stored fp64 oracle result, and R-MAT scale 27 with fp32 weights by invariants.
 
 tests/golden/<workload>_oracle.json is written by tests/golden/make_golden.py, which calls only
 the seeded generators and the CPU oracle.  The graph is regenerated here and checked against the
@@ -78,6 +79,44 @@ def test_fast_within_tolerance(L, workload):
     assert len(np.unique(m)) == r.n_communities
     # its modularity, re-evaluated by the library's Eq. 1 kernel, is the one reported
     assert abs(L.modularity(o, t, w, mem) - r.modularity) <= 1e-12
+    assert r.modularity >= gold["modularity"] - 0.005
+
+
+@pytest.fixture(scope="module")
+def rmat18_fp32(cuda_ok):
+    with open(os.path.join(GOLDEN, "rmat18_fp32_oracle.json")) as f:
+        gold = json.load(f)
+    g = gg.rmat(18, 16, 0.57, 0.19, 0.19, 18, gg.W_FP32)
+    assert _sha(g.offsets, g.targets, g.weights) == gold["csr_sha256"], "generator output drifted"
+    assert int(np.diff(g.offsets).max()) > 4096  # hub rows take the giant-row kernels
+    d = torch.device("cuda:0")
+    yield g, tuple(torch.from_numpy(a).to(d) for a in (g.offsets, g.targets, g.weights)), gold
+
+
+@pytest.mark.parametrize("giant_min_degree", [4096, 2048])
+def test_rmat18_fp32_deterministic_vs_fp64_oracle(L, rmat18_fp32, giant_min_degree):
+    """fp32 weights with 172 rows over 4096 arcs: the giant local-move and giant merge kernels sum
+    K_i->c in fp32 while the oracle works in fp64.  Final Q within 1e-4 of the stored fp64 oracle
+    result (two-sided), and Eq. 1 of the returned membership, evaluated by the oracle in fp64,
+    within 1e-10 of the library's.  Two runs in a row: the fp32 table sums use atomics in
+    arbitrary order, so near-ties may resolve differently from run to run; both runs must meet
+    the bound."""
+    import oracle
+    g, (o, t, w), gold = rmat18_fp32
+    for _ in range(2):
+        mem, r = L.run(o, t, w, mode="deterministic", validate=1, giant_min_degree=giant_min_degree)
+        m = mem.cpu().numpy()
+        assert m.min() == 0 and m.max() == r.n_communities - 1 and len(np.unique(m)) == r.n_communities
+        assert abs(r.modularity - gold["modularity"]) <= 1e-4
+        assert abs(oracle.modularity(g.offsets, g.targets, g.weights, m) - r.modularity) <= 1e-10
+
+
+def test_rmat18_fp32_fast_vs_fp64_oracle(L, rmat18_fp32):
+    import oracle
+    g, (o, t, w), gold = rmat18_fp32
+    mem, r = L.run(o, t, w, mode="fast", validate=0)
+    m = mem.cpu().numpy()
+    assert abs(oracle.modularity(g.offsets, g.targets, g.weights, m) - r.modularity) <= 1e-10
     assert r.modularity >= gold["modularity"] - 0.005
 
 

@@ -2,12 +2,14 @@
 
 Each result must be the same alone (louvain_run on the graph by itself) and in the mix (served
 together with other requests, in whatever batches the lanes formed): identical memberships and
-modularity in deterministic mode; in fast mode valid partitions whose mean modularity is within
+modularity in deterministic mode, both equal to the CPU oracle's; in fast mode valid partitions whose mean modularity is within
 0.005 of the oracle's (each graph within 0.03: the asynchronous schedule's noise on small graphs).
 The admission budget is respected: a request larger than the budget is refused, and a budget that
 holds only one request at a time still completes every request with the same results.
 """
 from __future__ import annotations
+
+import functools
 
 import numpy as np
 import pytest
@@ -31,6 +33,13 @@ def request_mix():
     return gs
 
 
+@functools.lru_cache(maxsize=None)
+def oracle_result(k):
+    g = request_mix()[k]
+    mem, q, passes, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params())
+    return mem, q, passes
+
+
 def alone(g, **kw):
     import paper_2312_04876_gb300 as lv
     L = lv.Louvain(0)
@@ -49,11 +58,16 @@ def test_same_alone_and_in_the_mix(cuda_ok, lanes, max_graphs):
     tickets = [srv.submit(g.offsets, g.targets, g.weights) for g in graphs]
     got = [srv.result(t) for t in tickets]
     srv.close()
-    for g, (m, info) in zip(graphs, got):
+    for k, (g, (m, info)) in enumerate(zip(graphs, got)):
         m1, q1 = alone(g, mode="deterministic")
         assert np.array_equal(m, m1)
         assert info["modularity"] == q1
         assert info["latency_ms"] >= info["queue_ms"] >= 0.0
+        # and each served result is the CPU oracle's, bit for bit
+        ref_mem, ref_q, ref_passes = oracle_result(k)
+        assert np.array_equal(m, ref_mem), f"request {k}"
+        assert info["modularity"] == ref_q, f"request {k}"
+        assert info["passes"] == ref_passes, f"request {k}"
     if max_graphs > 1 and lanes == 1:
         # requests that queued behind the first batch ran together
         assert max(info["batch_graphs"] for _, info in got) > 1

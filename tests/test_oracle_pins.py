@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import hand_traced
 import oracle
 from helpers import (brute_force_max_q, canonical, cliques, dense_adjacency, q_exact, q_pairsum, random_graph,
                      same_partition)
@@ -399,3 +400,71 @@ def test_overflow_rejected():
     g = gg.from_edges(2, [(0, 1)], [2**30])
     with pytest.raises(OverflowError):
         oracle.louvain(g.offsets, g.targets, g.weights)
+
+
+# ---------------------------------------------------------------- hand-traced readings of Algorithm 2
+@pytest.mark.parametrize("case", hand_traced.CASES, ids=lambda c: c.name)
+def test_hand_traced_local_move(case):
+    """R2 (ties to the smallest id, strict N > 0) and R3 (marks of a class make later classes of
+    the same iteration eligible) on graphs traced by hand; the trace is in tests/hand_traced.py."""
+    if case.colours is not None:
+        col, _ = oracle.colour(case.offsets, case.targets, case.seed, 0)
+        assert tuple(col.tolist()) == case.colours
+    cp, it, mv = oracle.local_move(case.offsets, case.targets, case.weights,
+                                   oracle.default_params(seed=case.seed), 0, tau=case.tau)
+    assert tuple(cp.tolist()) == case.cp
+    assert (it, mv) == (case.iterations, case.moves)
+
+
+def test_hand_traced_zero_gain_is_zero_by_eq1():
+    """The zero-gain moves of the strict-rule cases change Eq. 1 by exactly 0 (exact rationals)."""
+    c = hand_traced.ZERO_LOOPS
+    a = dense_adjacency(gg.Graph(n=2, offsets=c.offsets, targets=c.targets, weights=c.weights))
+    assert q_exact(a, [0, 1]) == q_exact(a, [1, 1]) == 0
+    t = hand_traced.ZERO_TRIANGLE
+    a = dense_adjacency(gg.Graph(n=3, offsets=t.offsets, targets=t.targets, weights=t.weights))
+    # vertex 0 leaving {0, 1} for {2}, the state after class {1} of the trace
+    assert q_exact(a, [0, 0, 2]) == q_exact(a, [2, 0, 2])
+
+
+# Each entry plants one plausible mistake in a copy of the oracle's source: (old text, new text)
+# replacements that must each match exactly once.
+_MUTANTS = {
+    "tie_to_largest_id": [("(nscore == best && c < bc)", "(nscore == best && c > bc)")],
+    "tie_to_first_seen": [(" || (nscore == best && c < bc)", "")],
+    "tie_to_last_seen": [("nscore > best || (nscore == best && c < bc)", "nscore >= best")],
+    "move_on_zero_gain": [("return found && best > W(0);", "return found && best >= W(0);")],
+    "marks_wait_for_next_iteration": [
+        ("int64_t moves = 0;", "int64_t moves = 0;\n  std::vector<int32_t> later;"),
+        ("if (g.tg[e] != i) flag[g.tg[e]] = 1;", "if (g.tg[e] != i) later.push_back(g.tg[e]);"),
+        ("li = it + 1;", "for (int32_t v : later) flag[v] = 1;\n      later.clear();\n      li = it + 1;"),
+    ],
+}
+
+
+def test_hand_traced_pins_catch_planted_mistakes(tmp_path):
+    """Every planted mistake in R2 / R3 fails at least one hand-traced pin, run in a child process
+    against the mutated copy of the oracle (LOUVAIN_ORACLE_SO)."""
+    import os
+    import subprocess
+    import sys
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "louvain_oracle.cpp")).read()
+    builds = {}
+    for name, edits in _MUTANTS.items():
+        text = src
+        for old, new in edits:
+            assert text.count(old) == 1, (name, old)
+            text = text.replace(old, new)
+        cpp = tmp_path / f"{name}.cpp"
+        cpp.write_text(text)
+        so = tmp_path / f"{name}.so"
+        builds[name] = (so, subprocess.Popen(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-o", str(so), str(cpp)]))
+    here = os.path.dirname(os.path.abspath(__file__))
+    for name, (so, proc) in builds.items():
+        assert proc.wait() == 0, name
+        env = dict(os.environ, LOUVAIN_ORACLE_SO=str(so))
+        r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                            os.path.join(here, "test_oracle_pins.py"), "-k", "test_hand_traced_local_move"],
+                           env=env, capture_output=True, text=True, cwd=os.path.dirname(here))
+        assert r.returncode == 1, (name, r.stdout[-2000:])
+        assert "failed" in r.stdout, name

@@ -5,7 +5,14 @@ final modularity) on the device-resident CSR.  value = arcs / step time (arcs co
 directions, as the paper's Table 2 does).  e2e = the same through louvain_run_host from pinned
 host buffers (CSR upload and membership download inside the timed region).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fast|deterministic]
+Beside the headline the same JSON line carries a `suite` of the other workloads, each timed on
+its own with CUDA events and its own clock samples: R-MAT 22 in deterministic mode (membership
+against the oracle's), R-MAT 22 without its isolated vertices, the road-like grid of 24M vertices
+(fast and deterministic), R-MAT 27 with fp32 weights, 4,096 batched planted-partition graphs
+against one at a time, and a Poisson stream of mixed requests through the serving runtime.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fast|deterministic] [--no-suite]
+    python bench.py --workload batch|serve|grid24m|rmat27_fp32|...   # one workload on its own
     python bench.py --impl reference      # the CPU oracle on a bounded sample (reference arm)
 """
 from __future__ import annotations
@@ -29,6 +36,12 @@ WORKLOADS = {
     "rmat20": (dict(kind="rmat", scale=20), "R-MAT scale 20, edge factor 16, int32 weights 1..8, seed 22"),
     "rmat18": (dict(kind="rmat", scale=18), "R-MAT scale 18, edge factor 16, int32 weights 1..8, seed 22"),
     "sbm10k": (dict(kind="sbm"), "planted-partition SBM, 10k vertices, 100 blocks, p_in 0.1, p_out 0.0005"),
+    "rmat22_noiso": (dict(kind="rmat"), "R-MAT scale 22 as above with its isolated vertices dropped "
+                                        "(the others renumbered in order)"),
+    "grid24m": (dict(kind="grid"), "road-like grid: 4899 x 4899 lattice (24.0M vertices), 10% of edges deleted, "
+                                   "1% random long links, unit int32 weights, seed 3"),
+    "rmat27_fp32": (dict(kind="rmat"), "R-MAT scale 27, edge factor 16, (0.57,0.19,0.19,0.05), fp32 weights in "
+                                       "(0, 1], seed 22, drawn on the GPU"),
 }
 CPU_SAMPLE = "rmat20"   # cpu_baseline of the bench line: one oracle run, ~10-30 s
 REF_SAMPLE = "rmat18"   # one step of --impl reference: a few seconds each
@@ -38,6 +51,10 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 def make_graph(name):
     import graphgen as gg
+    if name == "rmat22_noiso":
+        return gg.drop_isolated(make_graph("rmat22"))
+    if name == "grid24m":
+        return gg.grid(4899, 4899, 0.10, 0.01, 3)
     if name.startswith("rmat"):
         return gg.rmat(int(name[4:]), 16, 0.57, 0.19, 0.19, 22, gg.W_INT8)
     if name == "sbm10k":
@@ -137,7 +154,7 @@ def stored_traffic(workload: str, mode: str, kernel: str):
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    from paper_2312_04876_gb300.profiling import source_sha256
+    from paper_2312_04876_gb300.sources import source_sha256
     if t.get("source_sha256") != source_sha256():
         return None
     c = t.get("classes", {}).get(kernel)
@@ -206,172 +223,358 @@ def run_reference(args):
     return 0
 
 
-def batch_graphs(count: int, n_hi: float, threads: int):
-    """Members 0..count-1 of the batched planted-partition family (n log-uniform in [1e3, n_hi],
-    2-64 blocks, average degree log-uniform in [4, 64], p_out = 0.02 p_in, seed hash3(4, g, 0)),
-    generated on `threads` host threads (the C generator releases the GIL)."""
-    import graphgen as gg
-    from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(max_workers=threads) as ex:
-        return list(ex.map(lambda k: gg.batch_sbm(4, k, n_hi=n_hi), range(count)))
-
-
-def run_batch_bench(args):
-    """Batched workload: G independent graphs in one louvain_run_batch call (graphs/s), beside the
-    one-graph-at-a-time path (louvain_run per graph on the same device-resident graphs)."""
-    import numpy as np
+# ---------------------------------------------------------------- single-graph measurement
+def timed_runs(L, offs, tg, w, params, mem, steps: int, warmup: int, gpu: int, barrier=None):
+    """W untimed runs, then K runs between CUDA events on the launching stream (with nvidia-smi
+    clock samples).  Returns (ms per step, the K run results, clock summary)."""
     import torch
-    import graphgen as gg
-    import paper_2312_04876_gb300 as lv
-
-    ws, rank, local = dist_env()
-    if rank != 0:
-        return 0  # a one-GPU measurement: under torchrun the other ranks leave at once
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    t0 = time.perf_counter()
-    graphs = batch_graphs(args.batch_graphs, args.batch_n_hi, min(32, os.cpu_count() or 1))
-    gen_s = time.perf_counter() - t0
-    vo, offs, tg, w = gg.concat(graphs)
-    n_arcs = int(offs[-1])
-    o_d, t_d, w_d = (torch.from_numpy(a).to(dev) for a in (offs, tg, w))
-    del offs, tg, w
-    L = lv.Louvain(local)
-    params = lv.default_params(mode=args.mode, validate=0)
-    mem = torch.empty(int(vo[-1]), dtype=torch.int32, device=dev)
-    for _ in range(max(args.warmup, 3)):
-        L.run_batch(vo, o_d, t_d, w_d, params, membership=mem)
+    for _ in range(warmup):
+        L.run(offs, tg, w, params, membership=mem)
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    results = []
+    with ClockSampler(gpu) as clk:
+        if barrier:
+            barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        for _ in range(args.steps):
-            _, per, res = L.run_batch(vo, o_d, t_d, w_d, params, membership=mem)
+        for _ in range(steps):
+            _, r = L.run(offs, tg, w, params, membership=mem)
+            results.append(r)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    G = len(graphs)
-    batch_gps = G / (ms / 1e3)
-    # one graph at a time on the same GPU: every graph alone through louvain_run (device-resident)
-    single_q = []
-    idx = range(G) if args.single_sample <= 0 else range(min(G, args.single_sample))
-    singles = [(torch.from_numpy(graphs[k].offsets).to(dev), torch.from_numpy(graphs[k].targets).to(dev),
-                torch.from_numpy(graphs[k].weights).to(dev)) for k in idx]
-    m1 = torch.empty(max(g.n for g in graphs), dtype=torch.int32, device=dev)
-    for so, st_, sw in singles[:3]:
-        L.run(so, st_, sw, params, membership=m1[:so.numel() - 1])
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for so, st_, sw in singles:
-        _, r = L.run(so, st_, sw, params, membership=m1[:so.numel() - 1])
-        single_q.append(r.modularity)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    single_ms = ev0.elapsed_time(ev1)
-    single_gps = len(singles) / (single_ms / 1e3)
-    dq = [per[k]["modularity"] - single_q[j] for j, k in enumerate(idx)]
-    line = {
-        "metric": "louvain_batched_graphs_per_second", "value": batch_gps, "unit": "graphs/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"{G} planted-partition SBM graphs, n log-uniform [1e3, {args.batch_n_hi:.0f}], "
-                               "2-64 blocks, degree log-uniform [4, 64], p_out/p_in 0.02, unit int32 weights",
-                   "graphs": G, "vertices": int(vo[-1]), "arcs": n_arcs, "mode": args.mode,
-                   "l2": f"inputs larger than L2 (CSR {(8 * (int(vo[-1]) + 1) + 8 * n_arcs) / 1e9:.2f} GB)"},
-        "edges_per_second": n_arcs / (ms / 1e3), "gpu_launches_per_step": res.kernel_launches,
-        "one_at_a_time": {"graphs_per_second": single_gps, "graphs_timed": len(singles), "ms": single_ms,
-                          "max_abs_dq_vs_batch": max(abs(x) for x in dq) if dq else None,
-                          "mean_dq_batch_minus_single": float(np.mean(dq)) if dq else None,
-                          "graphs_abs_dq_over_0.005": int(sum(abs(x) > 0.005 for x in dq)),
-                          "worst_graph": (lambda j: {"index": j, "n": graphs[j].n, "arcs": graphs[j].n_arcs,
-                                                     "q_batch": per[j]["modularity"], "q_single": single_q[j]})(
-                              int(np.argmax(np.abs(dq)))) if dq else None},
-        "speedup_vs_one_at_a_time": batch_gps / single_gps,
-        "passes_max": res.passes, "generate_s": gen_s, "clocks": clk.summary(),
-    }
-    print(json.dumps(line))
-    return 0
+        if barrier:
+            barrier()
+    return ev0.elapsed_time(ev1), results, clk.summary()
 
 
-def run_serve_bench(args):
-    """Serving workload: a Poisson stream of mixed graphs (half SBM, half R-MAT, 1e4-2e7 edges)
-    against the continuous-batching server and against the one-at-a-time server (one lane, one
-    graph per batch), at arrival rates that are multiples of the one-at-a-time capacity."""
+def kernel_roofline(L, offs, tg, w, params, mem, steps: int, workload: str, mode: str, top: int = 0):
+    """Per-kernel-class device time (CUDA events around every launch on the run's stream) and
+    algorithmic bytes (device counters) from `steps` profiled repeats; the roofline of the class
+    that takes the most time among those with a byte count."""
+    import paper_2312_04876_gb300 as lv
+    pparams = lv.default_params()
+    for f, _ in pparams._fields_:
+        setattr(pparams, f, getattr(params, f))
+    pparams.profile = 1
+    agg = {}
+    for _ in range(steps):
+        L.run(offs, tg, w, pparams, membership=mem)
+        for k in L.kernel_profile():
+            a = agg.setdefault(k["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            a["launches"] += k["launches"]
+            a["ms"] += k["ms"]
+            a["bytes"] += k["bytes"]
+    peak, peak_kind = peaks()
+    kernels = []
+    for name, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"]):
+        gbs = a["bytes"] / (a["ms"] * 1e6) if a["ms"] > 0 and a["bytes"] > 0 else None
+        kernels.append({"name": name, "launches_per_step": a["launches"] / steps, "ms_per_step": a["ms"] / steps,
+                        "gbs": gbs, "frac": gbs / peak if gbs else None})
+    dom = next((k for k in kernels if k["gbs"] is not None), None)
+    roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
+            "peak_kind": peak_kind}
+    if dom:
+        a = agg[dom["name"]]
+        roof["traffic"] = stored_traffic(workload, mode, dom["name"])
+        roof.update({"kernel": dom["name"], "achieved": dom["gbs"], "frac": dom["gbs"] / peak,
+                     "algorithmic_bytes_per_launch": a["bytes"] / max(1, a["launches"]),
+                     "avg_launch_ms": a["ms"] / max(1, a["launches"])})
+    return roof, (kernels[:top] if top else kernels)
+
+
+def graph_block(L, name: str, desc: str, offs, tg, w, n: int, n_arcs: int, mode: str, steps: int, warmup: int,
+                gpu: int, golden: str | None = None, knobs=None):
+    """One single-graph workload of the suite: edges/s, modularity against the oracle's stored
+    result, roofline of its dominant kernel class, clocks."""
+    import hashlib
+    import torch
+    import paper_2312_04876_gb300 as lv
+    params = lv.default_params(mode=mode, validate=0, **(knobs or {}))
+    mem = torch.empty(max(n, 1), dtype=torch.int32, device=offs.device)[:n]
+    ms, results, clocks = timed_runs(L, offs, tg, w, params, mem, steps, warmup, gpu)
+    last = results[-1]
+    msha = hashlib.sha256(mem.cpu().numpy().astype("<i4").tobytes()).hexdigest() if mode == "deterministic" else None
+    nc = last.n_communities
+    valid = bool(n == 0 or (int(mem.min()) == 0 and int(mem.max()) == nc - 1))
+    roof, kernels = kernel_roofline(L, offs, tg, w, params, mem, 1, name.split(":")[0], mode, top=6)
+    out = {"workload": desc, "n": n, "arcs": n_arcs, "mode": mode, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms / steps, "edges_per_second": n_arcs / (ms / steps / 1e3),
+           "modularity": last.modularity, "passes": last.passes, "iterations": last.total_iterations,
+           "communities": nc, "valid_partition": valid, "gpu_launches_per_step": last.kernel_launches,
+           "roofline": roof, "kernels": kernels, "clocks": clocks}
+    if golden:
+        out["oracle_match"] = oracle_match(golden, mode, last.modularity, msha)
+    return out
+
+
+# ---------------------------------------------------------------- suite blocks
+def block_rmat22_deterministic(ctx):
+    return graph_block(ctx["L"], "rmat22", WORKLOADS["rmat22"][1], *ctx["rmat22"], "deterministic", 3, 3,
+                       ctx["gpu"], golden="rmat22")
+
+
+def _device_graph(g, dev):
+    import torch
+    return (torch.from_numpy(g.offsets).to(dev), torch.from_numpy(g.targets).to(dev),
+            torch.from_numpy(g.weights).to(dev), g.n, g.n_arcs)
+
+
+def block_rmat22_noiso(ctx):
+    import graphgen as gg
+    g = gg.drop_isolated(ctx["g"])
+    d = _device_graph(g, ctx["dev"])
+    out = graph_block(ctx["L"], "rmat22_noiso", WORKLOADS["rmat22_noiso"][1], *d, "fast", 5, 3, ctx["gpu"],
+                      golden="rmat22_noiso")
+    out["isolated_vertices_dropped"] = ctx["g"].n - g.n
+    return out
+
+
+def block_grid(ctx):
+    g = make_graph("grid24m")
+    d = _device_graph(g, ctx["dev"])
+    del g
+    out = {}
+    for mode, steps in (("fast", 5), ("deterministic", 3)):
+        out[mode] = graph_block(ctx["L"], "grid24m", WORKLOADS["grid24m"][1], *d, mode, steps, 3, ctx["gpu"],
+                                golden="grid24m")
+    return out
+
+
+def block_rmat27_fp32(ctx):
+    """R-MAT 27 with fp32 weights (134M vertices, > 2^31 arcs), drawn on the GPU.  No stored oracle
+    result (one oracle run takes hours on one core): a valid canonical partition and its Eq. 1
+    evaluated again by the library's modularity kernel."""
+    import torch
+    import paper_2312_04876_gb300 as lv
+    from graphgen import device as gd
+    t0 = time.perf_counter()
+    o, t, w = gd.rmat(27, 16, 0.57, 0.19, 0.19, 22, fp_weights=True, device=ctx["dev"])
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    L = lv.Louvain(ctx["gpu"])
+    try:
+        n, a = o.numel() - 1, t.numel()
+        out = graph_block(L, "rmat27_fp32", WORKLOADS["rmat27_fp32"][1], o, t, w, n, a, "fast", 3, 2, ctx["gpu"])
+        mem = torch.empty(n, dtype=torch.int32, device=ctx["dev"])
+        _, r = L.run(o, t, w, lv.default_params(mode="fast", validate=0), membership=mem)
+        out["eq1_recomputed_delta"] = abs(L.modularity(o, t, w, mem) - r.modularity)
+        out["communities_distinct"] = int(torch.unique(mem).numel()) == r.n_communities
+        out["generate_s"] = gen_s
+        out["workspace_gb"] = L.workspace_bytes() / 1e9
+        return out
+    finally:
+        L.close()
+        del o, t, w
+        torch.cuda.empty_cache()
+
+
+def _oracle_q(arrays):
+    import oracle
+    o, t, w = arrays
+    _, q, _, _ = oracle.louvain(o, t, w, oracle.default_params())
+    return q
+
+
+def oracle_qs(graphs, workers: int):
+    """Oracle modularity of each graph, in a pool of fresh (spawned) processes."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_oracle_q, [(g.offsets, g.targets, g.weights) for g in graphs])
+
+
+def block_batched(ctx, count: int = 4096, n_hi: float = 2e5, single_sample: int = 512, oracle_sample: int = 48,
+                  steps: int = 3, warmup: int = 3, mode: str = "fast"):
+    """4,096 independent planted-partition graphs in one louvain_run_batch call (graphs/s), beside
+    the one-graph-at-a-time path (louvain_run per graph on the same device-resident graphs, timed
+    on the first `single_sample` of them); modularity of a sample against the CPU oracle."""
     import numpy as np
     import torch
     import graphgen as gg
     import paper_2312_04876_gb300 as lv
     from concurrent.futures import ThreadPoolExecutor
+    dev, gpu = ctx["dev"], ctx["gpu"]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        graphs = list(ex.map(lambda k: gg.batch_sbm(4, k, n_hi=n_hi), range(count)))
+    gen_s = time.perf_counter() - t0
+    G = len(graphs)
+    vo = np.zeros(G + 1, dtype=np.int64)
+    ao = np.zeros(G + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        vo[k + 1] = vo[k] + g.n
+        ao[k + 1] = ao[k] + g.n_arcs
+    n, n_arcs = int(vo[-1]), int(ao[-1])
+    # segmented CSR built on the device graph by graph (no host-side union copy)
+    o_d = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    t_d = torch.empty(n_arcs, dtype=torch.int32, device=dev)
+    w_d = torch.empty(n_arcs, dtype=torch.int32, device=dev)
+    o_d[n] = n_arcs
+    for k in range(G):
+        g = graphs[k]
+        o_d[vo[k]:vo[k + 1]] = torch.from_numpy(g.offsets[:-1] + ao[k]).to(dev)
+        t_d[ao[k]:ao[k + 1]] = torch.from_numpy(g.targets).to(dev)
+        w_d[ao[k]:ao[k + 1]] = torch.from_numpy(g.weights).to(dev)
+        if k >= oracle_sample:
+            graphs[k] = None
+    sample = graphs[:oracle_sample]
+    del graphs
+    L = lv.Louvain(gpu)
+    try:
+        params = lv.default_params(mode=mode, validate=0)
+        mem = torch.empty(n, dtype=torch.int32, device=dev)
+        for _ in range(warmup):
+            L.run_batch(vo, o_d, t_d, w_d, params, membership=mem)
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(gpu) as clk:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps):
+                _, per, res = L.run_batch(vo, o_d, t_d, w_d, params, membership=mem)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        batch_gps = G / (ms / 1e3)
+        # one graph at a time: each graph alone through louvain_run, sliced from the union arrays
+        S = min(G, single_sample)
+        singles = [(o_d[int(vo[k]):int(vo[k + 1]) + 1] - int(ao[k]), t_d[int(ao[k]):int(ao[k + 1])], w_d[int(ao[k]):int(ao[k + 1])])
+                   for k in range(S)]
+        m1 = torch.empty(int(max(vo[k + 1] - vo[k] for k in range(G))), dtype=torch.int32, device=dev)
+        for so, st_, sw in singles[:3]:
+            L.run(so, st_, sw, params, membership=m1[:so.numel() - 1])
+        single_q = []
+        with ClockSampler(gpu) as clk1:
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for so, st_, sw in singles:
+                _, r = L.run(so, st_, sw, params, membership=m1[:so.numel() - 1])
+                single_q.append(r.modularity)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        single_ms = ev0.elapsed_time(ev1)
+        single_gps = S / (single_ms / 1e3)
+        dq_single = [per[k]["modularity"] - single_q[k] for k in range(S)]
+        launches = res.kernel_launches
+    finally:
+        L.close()
+        del o_d, t_d, w_d
+        torch.cuda.empty_cache()
+    t1 = time.perf_counter()
+    ref_q = oracle_qs(sample, min(16, os.cpu_count() or 1))
+    oracle_s = time.perf_counter() - t1
+    dq = [per[k]["modularity"] - ref_q[k] for k in range(len(sample))]
+    return {
+        "workload": f"{G} planted-partition SBM graphs, n log-uniform [1e3, {n_hi:.0f}], 2-64 blocks, degree "
+                    "log-uniform [4, 64], p_out/p_in 0.02, unit int32 weights (segmented CSR)",
+        "graphs": G, "vertices": n, "arcs": n_arcs, "mode": mode, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms, "graphs_per_second": batch_gps, "edges_per_second": n_arcs / (ms / 1e3),
+        "gpu_launches_per_step": launches, "clocks": clk.summary(),
+        "one_at_a_time": {"graphs_per_second": single_gps, "graphs_timed": S, "ms": single_ms,
+                          "clocks": clk1.summary(),
+                          "mean_dq_batch_minus_single": float(np.mean(dq_single)),
+                          "max_abs_dq_batch_vs_single": float(np.max(np.abs(dq_single)))},
+        "speedup_vs_one_at_a_time": batch_gps / single_gps,
+        "vs_oracle": {"graphs": len(sample), "mean_dq": float(np.mean(dq)), "worst_dq": float(np.min(dq)),
+                      "graphs_below_minus_0.005": int(sum(x < -0.005 for x in dq)), "oracle_s": oracle_s},
+        "generate_s": gen_s,
+    }
 
-    ws, rank, local = dist_env()
-    if rank != 0:
-        return 0  # a one-GPU measurement: under torchrun the other ranks leave at once
-    torch.cuda.set_device(local)
-    R = args.serve_requests
+
+def block_serving(ctx, requests: int = 64, lanes: int = 4, budget_gb: float = 40.0, rates=(2.0, 4.0),
+                  mode: str = "fast"):
+    """A Poisson stream of mixed graphs (half SBM, half R-MAT, 1e4-2e7 edges) through the
+    continuous-batching server and through the one-at-a-time server (one lane, one graph per
+    batch), at arrival rates that are multiples of the one-at-a-time capacity."""
+    import numpy as np
+    import graphgen as gg
+    import paper_2312_04876_gb300 as lv
+    from concurrent.futures import ThreadPoolExecutor
+    gpu = ctx["gpu"]
+    R = requests
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
         reqs = list(ex.map(lambda r: gg.serving_request(5, r), range(R)))
     gen_s = time.perf_counter() - t0
-    budget = int(args.serve_budget_gb * (1 << 30))
-    kw = dict(mode=args.mode, validate=0)
+    budget = int(budget_gb * (1 << 30))
 
-    def run_stream(lanes, max_graphs, rate):
-        srv = lv.Server(local, hbm_budget_bytes=budget, lanes=lanes, max_batch_graphs=max_graphs, **kw)
-        # warm the lanes' workspaces with the largest requests
-        for t in [srv.submit(g.offsets, g.targets, g.weights) for g in sorted(reqs, key=lambda g: -g.n_arcs)[:lanes]]:
-            srv.result(t)
-        gaps = [-np.log(((gg.hash3(9, r, 0) >> 11) + 1) / 9007199254740992.0) / rate for r in range(R)]
-        tickets = []
-        start = time.perf_counter()
-        due = start
-        for g, gap in zip(reqs, gaps):
-            due += gap if rate > 0 else 0.0
-            now = time.perf_counter()
-            if due > now:
-                time.sleep(due - now)
-            tickets.append(srv.submit(g.offsets, g.targets, g.weights))
-        lat, qs, bs = [], [], []
-        for t in tickets:
-            _, info = srv.result(t)
-            lat.append(info["latency_ms"])
-            qs.append(info["modularity"])
-            bs.append(info["batch_graphs"])
-        span = time.perf_counter() - start
-        srv.close()
+    def run_stream(nl, max_graphs, rate):
+        srv = lv.Server(gpu, hbm_budget_bytes=budget, lanes=nl, max_batch_graphs=max_graphs, mode=mode, validate=0)
+        try:
+            # warm the lanes' workspaces with the largest requests
+            for t in [srv.submit(g.offsets, g.targets, g.weights) for g in sorted(reqs, key=lambda g: -g.n_arcs)[:nl]]:
+                srv.result(t)
+            gaps = [-np.log(((gg.hash3(9, r, 0) >> 11) + 1) / 9007199254740992.0) / rate if rate > 0 else 0.0
+                    for r in range(R)]
+            tickets = []
+            with ClockSampler(gpu) as clk:
+                start = time.perf_counter()
+                due = start
+                for g, gap in zip(reqs, gaps):
+                    due += gap
+                    now = time.perf_counter()
+                    if due > now:
+                        time.sleep(due - now)
+                    tickets.append(srv.submit(g.offsets, g.targets, g.weights))
+                lat, qs, bs = [], [], []
+                for t in tickets:
+                    _, info = srv.result(t)
+                    lat.append(info["latency_ms"])
+                    qs.append(info["modularity"])
+                    bs.append(info["batch_graphs"])
+                span = time.perf_counter() - start
+        finally:
+            srv.close()
         return {"rate": rate, "graphs_per_second": R / span, "p50_ms": float(np.percentile(lat, 50)),
-                "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(np.mean(bs)), "q": qs}
+                "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(np.mean(bs)), "q": qs,
+                "clocks": clk.summary()}
 
-    # one-at-a-time capacity: everything submitted at once to one lane with one graph per batch
-    cap1 = run_stream(1, 1, 0.0)
+    cap1 = run_stream(1, 1, 0.0)  # one-at-a-time capacity: everything at once, one lane, one graph a batch
     base = cap1["graphs_per_second"]
     rows = []
-    for mult in args.serve_rates:
-        rate = mult * base
-        b = run_stream(args.serve_lanes, 256, rate)
-        o = run_stream(1, 1, rate)
-        dq = max(abs(x - y) for x, y in zip(b["q"], o["q"]))
-        rows.append({"rate_x_one_at_a_time": mult, "rate_graphs_per_s": rate,
+    for mult in rates:
+        b = run_stream(lanes, 256, mult * base)
+        o = run_stream(1, 1, mult * base)
+        rows.append({"rate_x_one_at_a_time": mult, "rate_graphs_per_s": mult * base,
                      "batched": {k: v for k, v in b.items() if k != "q"},
-                     "one_at_a_time": {k: v for k, v in o.items() if k != "q"}, "max_abs_dq": dq})
-    satb = run_stream(args.serve_lanes, 256, 0.0)  # saturated: everything at once
+                     "one_at_a_time": {k: v for k, v in o.items() if k != "q"},
+                     "max_abs_dq": max(abs(x - y) for x, y in zip(b["q"], o["q"]))})
+    sat = run_stream(lanes, 256, 0.0)
     arcs = [g.n_arcs for g in reqs]
-    line = {
-        "metric": "louvain_serving_graphs_per_second", "value": satb["graphs_per_second"], "unit": "graphs/s",
-        "n_gpus": 1, "steps": R, "warmup": args.serve_lanes, "ms_per_step": 1e3 / satb["graphs_per_second"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"{R} requests, half planted-partition SBM, half R-MAT (0.57,0.19,0.19,0.05), "
-                               "edge counts log-uniform [1e4, 2e7], Poisson arrivals",
-                   "mode": args.mode, "budget_gb": args.serve_budget_gb, "lanes": args.serve_lanes,
-                   "arcs_total": int(sum(arcs)), "arcs_max": int(max(arcs))},
-        "saturated": {k: v for k, v in satb.items() if k != "q"},
-        "one_at_a_time_capacity": {k: v for k, v in cap1.items() if k != "q"},
-        "speedup_saturated": satb["graphs_per_second"] / base, "rates": rows, "generate_s": gen_s,
-    }
-    print(json.dumps(line))
-    return 0
+    return {"workload": f"{R} requests, half planted-partition SBM, half R-MAT (0.57,0.19,0.19,0.05), edge counts "
+                        "log-uniform [1e4, 2e7], int32 weights, Poisson arrivals",
+            "mode": mode, "budget_gb": budget_gb, "lanes": lanes, "arcs_total": int(sum(arcs)),
+            "arcs_max": int(max(arcs)), "graphs_per_second": sat["graphs_per_second"],
+            "saturated": {k: v for k, v in sat.items() if k != "q"},
+            "one_at_a_time_capacity": {k: v for k, v in cap1.items() if k != "q"},
+            "speedup_saturated": sat["graphs_per_second"] / base, "rates": rows, "generate_s": gen_s}
 
 
+SUITE = [("rmat22_deterministic", block_rmat22_deterministic), ("rmat22_noiso_fast", block_rmat22_noiso),
+         ("grid24m", block_grid), ("rmat27_fp32_fast", block_rmat27_fp32), ("batched", block_batched),
+         ("serving", block_serving)]
+
+
+def run_suite(ctx, names):
+    out = {}
+    for name, fn in SUITE:
+        if names and name not in names:
+            continue
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(ctx)
+        except Exception as e:  # one failing block must not lose the others or the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["block_wall_s"] = round(time.perf_counter() - t0, 1)
+        print(f"[suite] {name}: {out[name]['block_wall_s']} s", file=sys.stderr, flush=True)
+    return out
+
+
+# ---------------------------------------------------------------- entry
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,15 +583,10 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--mode", default="fast", choices=["fast", "deterministic"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS) + ["batch", "serve"])
-    ap.add_argument("--batch-graphs", type=int, default=4096, help="batch workload: number of graphs")
-    ap.add_argument("--batch-n-hi", type=float, default=2e5, help="batch workload: largest vertex count")
-    ap.add_argument("--serve-requests", type=int, default=64, help="serving workload: requests in the stream")
-    ap.add_argument("--serve-lanes", type=int, default=4)
-    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 1.0, 2.0, 4.0],
-                    help="serving workload: arrival rates as multiples of the one-at-a-time capacity")
-    ap.add_argument("--single-sample", type=int, default=0,
-                    help="batch workload: time the one-at-a-time path on the first K graphs only (0 = all)")
+    ap.add_argument("--suite", default=None,
+                    help="comma-separated suite blocks to add to the line (default: all, with the default "
+                         "workload on one GPU); 'none' for the headline alone")
+    ap.add_argument("--no-suite", action="store_true")
     ap.add_argument("--fast-classes", type=int, default=None, help="random vertex classes of the fast schedule")
     ap.add_argument("--fast-classes-later", type=int, default=None,
                     help="fast mode: class groups of the iterations after the first of a pass")
@@ -407,16 +605,19 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch":
-        return run_batch_bench(args)
-    if args.workload == "serve":
-        return run_serve_bench(args)
 
-    import numpy as np
     import torch
     import paper_2312_04876_gb300 as lv
 
     ws, rank, local = dist_env()
+    if args.workload in ("batch", "serve", "rmat27_fp32"):
+        if rank != 0:
+            return 0  # one-GPU measurements: under torchrun the other ranks leave at once
+        torch.cuda.set_device(local)
+        ctx = {"dev": torch.device("cuda", local), "gpu": local}
+        fn = {"batch": block_batched, "serve": block_serving, "rmat27_fp32": block_rmat27_fp32}[args.workload]
+        print(json.dumps({"workload": args.workload, **fn(ctx)}))
+        return 0
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -429,31 +630,21 @@ def main():
     w = torch.from_numpy(g.weights).to(dev)
     L = lv.Louvain(local)
     knobs = {}
-    if args.fast_classes is not None:
-        knobs["fast_classes"] = args.fast_classes
-    if args.fast_classes_later is not None:
-        knobs["fast_classes_later"] = args.fast_classes_later
-    if args.compact is not None:
-        knobs["compact"] = args.compact
-    if args.fast_giant_class is not None:
-        knobs["fast_giant_class"] = args.fast_giant_class
-    if args.lm_blocks_per_sm is not None:
-        knobs["lm_blocks_per_sm"] = args.lm_blocks_per_sm
-    if args.giant_min_degree is not None:
-        knobs["giant_min_degree"] = args.giant_min_degree
+    for k in ("fast_classes", "fast_classes_later", "compact", "fast_giant_class", "lm_blocks_per_sm",
+              "giant_min_degree"):
+        if getattr(args, k) is not None:
+            knobs[k] = getattr(args, k)
     params = lv.default_params(mode=args.mode, validate=0, **knobs)
     tuned_ms = None
     if args.autotune and not knobs:
         # untimed: the knobs it picks leave the arithmetic unchanged (see louvain_autotune)
         params, tuned_ms = L.autotune(offs, tg, w, params, reps=1)
     mem = torch.empty(g.n, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream()
-
-    for _ in range(max(args.warmup, 3) if args.warmup > 0 else 0):
-        L.run(offs, tg, w, params, membership=mem)
-    torch.cuda.synchronize()
 
     if args.ncu_window:
+        for _ in range(max(args.warmup, 1)):
+            L.run(offs, tg, w, params, membership=mem)
+        torch.cuda.synchronize()
         torch.cuda.profiler.start()
         _, r = L.run(offs, tg, w, params, membership=mem)
         torch.cuda.synchronize()
@@ -467,19 +658,9 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    results = []
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            _, r = L.run(offs, tg, w, params, membership=mem)
-            results.append(r)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    ms = replica_time(ev0.elapsed_time(ev1), ws, dev)
+    warm = max(args.warmup, 3) if args.warmup > 0 else 0
+    ms_local, results, clocks = timed_runs(L, offs, tg, w, params, mem, args.steps, warm, local, barrier)
+    ms = replica_time(ms_local, ws, dev)
     ms_step = ms / args.steps
     msha = None
     if args.mode == "deterministic":
@@ -506,36 +687,11 @@ def main():
         e2e = {"value": replica_value(g.n_arcs, k2, ws, dt), "unit": "edges/s",
                "h2d_bytes_per_step": int(g.offsets.nbytes + g.targets.nbytes + g.weights.nbytes),
                "d2h_bytes_per_step": int(4 * g.n), "steps": k2}
+        del ho, ht, hw, hm
 
-    # per-kernel device time (CUDA events around every launch on the run's stream) and algorithmic
-    # bytes (device counters), from a profiled repeat of the timed steps
-    pparams = lv.default_params(mode=args.mode, validate=0, profile=1, **knobs)
-    for f in ("giant_min_degree", "lm_blocks_per_sm", "compact"):
-        setattr(pparams, f, getattr(params, f))
-    agg = {}
-    for _ in range(args.steps):
-        L.run(offs, tg, w, pparams, membership=mem)
-        for k in L.kernel_profile():
-            a = agg.setdefault(k["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0})
-            a["launches"] += k["launches"]
-            a["ms"] += k["ms"]
-            a["bytes"] += k["bytes"]
+    roof, kernels = kernel_roofline(L, offs, tg, w, params, mem, args.steps, args.workload, args.mode)
     if rank != 0:
         return 0
-    peak, peak_kind = peaks()
-    kernels = []
-    for name, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"]):
-        gbs = a["bytes"] / (a["ms"] * 1e6) if a["ms"] > 0 and a["bytes"] > 0 else None
-        kernels.append({"name": name, "launches_per_step": a["launches"] / args.steps,
-                        "ms_per_step": a["ms"] / args.steps, "gbs": gbs})
-    dom = next((k for k in kernels if k["gbs"] is not None), None)
-    roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
-            "peak_kind": peak_kind}
-    if dom:
-        roof["traffic"] = stored_traffic(args.workload, args.mode, dom["name"])
-        roof.update({"kernel": dom["name"], "achieved": dom["gbs"], "frac": dom["gbs"] / peak,
-                     "algorithmic_bytes_per_launch": agg[dom["name"]]["bytes"] / max(1, agg[dom["name"]]["launches"]),
-                     "avg_launch_ms": agg[dom["name"]]["ms"] / max(1, agg[dom["name"]]["launches"])})
     line = {
         "metric": "louvain_edges_per_second", "value": value, "unit": "edges/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -551,10 +707,14 @@ def main():
         "passes": last.passes, "iterations": last.total_iterations,
         "communities": last.n_communities, "gpu_launches": launches,
         "pass_ms": [{k: round(v, 3) if isinstance(v, float) else v for k, v in s.items()} for s in last.stats],
-        "roofline": roof, "kernels": kernels, "clocks": clk.summary(), "e2e": e2e,
+        "roofline": roof, "kernels": kernels, "clocks": clocks, "e2e": e2e,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    want = None if args.suite in (None, "all") else ([] if args.suite == "none" else args.suite.split(","))
+    if ws == 1 and not args.no_suite and want != [] and (args.suite is not None or args.workload == "rmat22"):
+        ctx = {"dev": dev, "gpu": local, "L": L, "g": g, "rmat22": (offs, tg, w, g.n, g.n_arcs)}
+        line["suite"] = run_suite(ctx, want)
     print(json.dumps(line))
     return 0
 

@@ -205,6 +205,18 @@ def concat(graphs):
     return vo, offs, tg.astype(np.int32, copy=False), wt
 
 
+def drop_isolated(g: Graph) -> Graph:
+    """The same graph without its isolated vertices (rows with no arc): the others keep their
+    order and are renumbered 0..n'-1, so every remaining arc and weight is unchanged."""
+    deg = np.diff(g.offsets)
+    keep = deg > 0
+    newid = (np.cumsum(keep) - 1).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum(deg[keep])]).astype(np.int64)
+    tg = newid[g.targets].astype(np.int32)
+    return Graph(int(keep.sum()), offs, tg, g.weights.copy(), g.name + " (isolated vertices dropped)",
+                 g.edges_drawn)
+
+
 def serving_request(base_seed: int, r: int) -> Graph:
     """Request r of the mixed serving stream: target edge count E log-uniform in [1e4, 2e7]; even
     r: a planted-partition SBM (average degree log-uniform in [4, 64], 2-64 blocks, p_out/p_in =

@@ -1383,6 +1383,7 @@ void louvain_destroy(louvain_handle h) {
   free_all(h->ws.gt_alloc);
   free_all(h->ws.in_alloc);
   free_all(h->ws.batch_alloc);
+  free_all(h->ws.desc_alloc);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
   for (cudaEvent_t e : h->fork_ev) cudaEventDestroy(e);

@@ -27,6 +27,9 @@ WORKLOADS = {
     "sbm10k": lambda: gg.sbm(10000, 100, 0.1, 0.0005, 1),
     # road-like: 4899 x 4899 lattice (~24.0M vertices), 10% of the edges deleted, 1% long links
     "grid24m": lambda: gg.grid(4899, 4899, 0.10, 0.01, 3),
+    # R-MAT 22 without its 1,799,215 isolated vertices (which count toward |V'| in the pass loop's
+    # aggregation-tolerance test and stop it after two passes on the full graph)
+    "rmat22_noiso": lambda: gg.drop_isolated(gg.rmat(22, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8)),
     # fp32 weights in (0, 1]; 172 rows over 4096 arcs (the giant-row path), maximum degree 25,238
     "rmat18_fp32": lambda: gg.rmat(18, 16, 0.57, 0.19, 0.19, 18, gg.W_FP32),
 }

@@ -93,3 +93,15 @@ def test_tensor_hash3_equals_c_hash3():
     for a, b, c in [(0, 0, 0), (22, 12345, 3), (2**63 + 5, 2**40, 7)]:
         x = gd.hash3(torch.tensor(gd._s64(a)), gd._s64(b), gd._s64(c))
         assert int(x) & ((1 << 64) - 1) == gg.hash3(a, b, c)
+
+
+def test_drop_isolated_keeps_every_arc():
+    g = gg.from_edges(7, [(1, 3), (3, 5), (5, 1), (6, 6)], [2, 3, 4, 5])
+    h = gg.drop_isolated(g)
+    assert h.n == 4  # vertices 0, 2 and 4 had no arc
+    old = {1: 0, 3: 1, 5: 2, 6: 3}
+    arcs_g = sorted((old[u], old[int(v)], int(w)) for u in range(g.n)
+                    for v, w in zip(g.targets[g.offsets[u]:g.offsets[u + 1]], g.weights[g.offsets[u]:g.offsets[u + 1]]))
+    arcs_h = sorted((u, int(v), int(w)) for u in range(h.n)
+                    for v, w in zip(h.targets[h.offsets[u]:h.offsets[u + 1]], h.weights[h.offsets[u]:h.offsets[u + 1]]))
+    assert arcs_g == arcs_h

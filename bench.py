@@ -554,9 +554,92 @@ def block_serving(ctx, requests: int = 64, lanes: int = 4, budget_gb: float = 40
             "speedup_saturated": sat["graphs_per_second"] / base, "rates": rows, "generate_s": gen_s}
 
 
+def block_dynamic(ctx, frac: float = 0.005, steps: int = 5, warmup: int = 3):
+    """A dynamic graph: R-MAT 22, then a batch that deletes `frac` of its edges and inserts as many
+    uniform random ones (weights 1..8).  Times the batch update (louvain_update_graph) and the warm
+    start from the previous result (louvain_run_from) against a cold run on the updated graph, all
+    in fast mode."""
+    import numpy as np
+    import torch
+    import paper_2312_04876_gb300 as lv
+    L, dev, gpu, g = ctx["L"], ctx["dev"], ctx["gpu"], ctx["g"]
+    o, t, w, n, _ = ctx["rmat22"]
+    params = lv.default_params(mode="fast", validate=0)
+    prev, r0 = L.run(o, t, w, params)
+    rng = np.random.default_rng(42)
+    m = g.n_arcs // 2
+    k = int(frac * m)
+    src = np.repeat(np.arange(g.n, dtype=np.int32), np.diff(g.offsets))
+    e = rng.choice(g.n_arcs, size=4 * k, replace=False)
+    e = e[src[e] < g.targets[e]][:k]
+    dels = np.stack([src[e], g.targets[e]], axis=1).astype(np.int32)
+    ins = rng.integers(0, g.n, size=(k, 2)).astype(np.int32)
+    iw = rng.integers(1, 9, size=k).astype(np.int32)
+    del src
+    d_dels, d_ins, d_iw = (torch.from_numpy(a).to(dev) for a in (dels, ins, iw))
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        L.update_graph(o, t, w, n, d_dels, d_ins, d_iw)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        oo, ot, ow = L.update_graph(o, t, w, n, d_dels, d_ins, d_iw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    upd_ms = ev0.elapsed_time(ev1) / steps
+    a_new = ot.numel()
+    mem = torch.empty(n, dtype=torch.int32, device=dev)
+    out = {"workload": f"R-MAT scale 22 as the headline, then {k} edge deletions and {k} uniform random edge "
+                       f"insertions ({100 * frac:.1f}% of its {m} edges each), weights 1..8",
+           "deleted_edges": k, "inserted_edges": k, "arcs_after": a_new, "update_ms": upd_ms,
+           "update_arcs_per_second": a_new / (upd_ms / 1e3)}
+    for kind in ("warm", "cold"):
+        for _ in range(warmup):
+            if kind == "warm":
+                L.run_from(oo, ot, ow, prev, params, membership=mem)
+            else:
+                L.run(oo, ot, ow, params, membership=mem)
+        torch.cuda.synchronize()
+        res = []
+        with ClockSampler(gpu) as clk:
+            ev0.record(stream)
+            for _ in range(steps):
+                if kind == "warm":
+                    _, r = L.run_from(oo, ot, ow, prev, params, membership=mem)
+                else:
+                    _, r = L.run(oo, ot, ow, params, membership=mem)
+                res.append(r)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        out[kind] = {"ms_per_step": ms, "edges_per_second": a_new / (ms / 1e3),
+                     "modularity": float(np.mean([r.modularity for r in res])), "passes": res[-1].passes,
+                     "iterations": res[-1].total_iterations, "clocks": clk.summary()}
+    out["warm_speedup_vs_cold"] = out["cold"]["ms_per_step"] / out["warm"]["ms_per_step"]
+    out["warm_plus_update_speedup_vs_cold"] = out["cold"]["ms_per_step"] / (out["warm"]["ms_per_step"] + upd_ms)
+    out["previous_modularity"] = r0.modularity
+    return out
+
+
+def in_child(workload: str):
+    """A block run as `bench.py --workload <workload>` in a fresh process (its own CUDA context, host
+    heap and threads), so that what earlier blocks left behind does not colour its timing."""
+    def run(ctx):
+        env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES", str(ctx["gpu"])))
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", workload],
+                           capture_output=True, text=True, env=env, timeout=1200)
+        if r.returncode != 0:
+            raise RuntimeError(f"child exited {r.returncode}: {r.stderr[-500:]}")
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        d.pop("workload_key", None)
+        return d
+    return run
+
+
 SUITE = [("rmat22_deterministic", block_rmat22_deterministic), ("rmat22_noiso_fast", block_rmat22_noiso),
-         ("grid24m", block_grid), ("rmat27_fp32_fast", block_rmat27_fp32), ("batched", block_batched),
-         ("serving", block_serving)]
+         ("grid24m", block_grid), ("dynamic_rmat22", block_dynamic), ("rmat27_fp32_fast", in_child("rmat27_fp32")), ("batched", in_child("batch")),
+         ("serving", in_child("serve"))]
 
 
 def run_suite(ctx, names):
@@ -616,7 +699,7 @@ def main():
         torch.cuda.set_device(local)
         ctx = {"dev": torch.device("cuda", local), "gpu": local}
         fn = {"batch": block_batched, "serve": block_serving, "rmat27_fp32": block_rmat27_fp32}[args.workload]
-        print(json.dumps({"workload": args.workload, **fn(ctx)}))
+        print(json.dumps({"workload_key": args.workload, **fn(ctx)}))
         return 0
     if ws > 1:
         import torch.distributed as dist

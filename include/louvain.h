@@ -140,6 +140,41 @@ void louvain_destroy(louvain_handle h);
  * fast_giant_class, lm_blocks_per_sm, giant_min_degree and wait_spins 0 (their built-in choices). */
 louvain_status louvain_default_params(louvain_params* p);
 
+/* Algorithm 1 as louvain_run, but the first pass starts from the membership d_initial[n] (device,
+ * ids in [0, n)) instead of singleton communities: C' = d_initial, Sigma_c = the sum of K_i over
+ * c's members, every vertex flagged for processing; later passes are unchanged.  This is the warm
+ * start of a dynamic graph -- pass the membership of the graph before a batch update (extended
+ * with any new vertices, e.g. as singletons) and the updated graph (louvain_update_graph).  The
+ * paper keeps the first pass's graph in a format open to batch updates (Section 4.2), gives later
+ * passes an initial membership (Figure 2) and names dynamic graphs as its next step (Conclusion).
+ * d_membership gets the canonical result as in louvain_run.  LOUVAIN_ERR_INVALID for an id out of
+ * range.  A vertex can only join a neighbour's community, so a community of the initial membership
+ * never splits (it can only grow or empty). */
+louvain_status louvain_run_from(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                const louvain_params* p, void* stream, const int32_t* d_initial,
+                                int32_t* d_membership, louvain_result* res, louvain_pass_stats* stats,
+                                int32_t stats_cap, int32_t* n_stats);
+
+/* A batch update of a symmetric CSR (Section 4.2: the first pass's graph in a format open to batch
+ * updates) into caller buffers: rows grow from n_old to n_new (>= n_old; new rows start empty);
+ * every arc between u and v of a deleted edge {d_del_u[k], d_del_v[k]} is removed, in both
+ * directions and with all its duplicates (deleting a pair that is not an edge is a no-op); then
+ * each inserted edge (d_ins_u[k], d_ins_v[k]) with weight d_ins_w[k] (the graph's wtype) adds the
+ * arc u->v and, if u != v, the arc v->u (an edge that already exists gets a second arc, which the
+ * method sums).  Row r of the result holds its surviving arcs, then its inserted arcs, each group in
+ * unspecified order (no step of the method depends on the order of a row).  All arrays are device arrays; d_out_offsets [n_new + 1],
+ * d_out_targets / d_out_weights hold out_cap arcs and must not overlap the input.  *out_arcs (host)
+ * gets the updated arc count, also when it exceeds out_cap (then LOUVAIN_ERR_INVALID and only the
+ * offsets are written).  LOUVAIN_ERR_INVALID for an id outside [0, n_new). */
+louvain_status louvain_update_graph(louvain_handle h, int64_t n_old, int64_t n_arcs, const int64_t* d_offsets,
+                                    const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                    int64_t n_new, int64_t n_del, const int32_t* d_del_u, const int32_t* d_del_v,
+                                    int64_t n_ins, const int32_t* d_ins_u, const int32_t* d_ins_v,
+                                    const void* d_ins_w, void* stream, int64_t* d_out_offsets,
+                                    int32_t* d_out_targets, void* d_out_weights, int64_t out_cap,
+                                    int64_t* out_arcs);
+
 /* Device bytes the handle holds now: every workspace buffer it allocated and has not freed
  * (grown on demand, kept across calls, released by louvain_destroy).  *bytes (host). */
 louvain_status louvain_workspace_bytes(louvain_handle h, size_t* bytes);

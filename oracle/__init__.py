@@ -12,7 +12,13 @@ Parity status of each function (what pins it lives in tests/test_oracle_pins.py)
   aggregate ......... pinned (numpy scatter-add of community pairs; Q invariance; 2m invariance)
   local_move/louvain  pinned (brute-force optimum on <= 9 vertices; clique rings; planted SBM;
                       hand-traced two-vertex/triangle cases; the karate club's published optimum;
-                      tolerance limits and the single-move optimum at tolerance 0)
+                      tolerance limits and the single-move optimum at tolerance 0; hand-traced
+                      ties, zero-gain moves and same-iteration eligibility)
+  update_graph ...... pinned (an edge dictionary rebuilt independently in Python)
+  louvain_from ...... pinned (singleton start = the cold run; clique partitions of clique rings are
+                      fixed points; one community cannot split; the sequential schedule never ends
+                      below the modularity it started from; a warm start after a small update of
+                      a planted partition keeps the cold run's quality)
 """
 from __future__ import annotations
 
@@ -93,6 +99,12 @@ def _load():
         lib.oracle_louvain.restype = ctypes.c_int
         lib.oracle_louvain.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_int, ctypes.POINTER(Params), _P, _P, _P,
                                        ctypes.POINTER(PassStats), ctypes.c_int32]
+        lib.oracle_update_graph.restype = ctypes.c_int64
+        lib.oracle_update_graph.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                            _P, _P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, ctypes.c_int64]
+        lib.oracle_louvain_from.restype = ctypes.c_int
+        lib.oracle_louvain_from.argtypes = [ctypes.c_int64, _P, _P, _P, ctypes.c_int, ctypes.POINTER(Params), _P, _P,
+                                            _P, _P, ctypes.POINTER(PassStats), ctypes.c_int32]
         _lib = lib
     return _lib
 
@@ -176,6 +188,49 @@ def local_move(offsets, targets, weights, params: Params | None = None, pass_ind
     if rc:
         raise ValueError(f"oracle_local_move failed ({rc})")
     return cp, int(it[0]), int(mv[0])
+
+
+def update_graph(offsets, targets, weights, n_new: int, deletions, insertions, insert_weights):
+    """Batch update of a symmetric CSR: deleted edges {u, v} lose every arc between u and v, then each
+    inserted edge (u, v) adds u->v and v->u (one arc for a self-loop) with its weight; rows may grow
+    to n_new.  Row r: surviving arcs in their old order, then inserted arcs in list order."""
+    offs, tg, w, fp = _graph_args(offsets, targets, weights)
+    d = np.asarray(deletions, dtype=np.int32).reshape(-1, 2)
+    ins = np.asarray(insertions, dtype=np.int32).reshape(-1, 2)
+    du, dv = _c(d[:, 0], np.int32), _c(d[:, 1], np.int32)
+    iu, iv = _c(ins[:, 0], np.int32), _c(ins[:, 1], np.int32)
+    iw = _c(insert_weights, np.float32 if fp else np.int32)
+    cap = len(tg) + 2 * len(iu) + 1
+    oo = np.empty(n_new + 1, dtype=np.int64)
+    ot = np.empty(cap, dtype=np.int32)
+    ow = np.empty(cap, dtype=np.float32 if fp else np.int32)
+    a = _load().oracle_update_graph(len(offs) - 1, _ptr(offs), _ptr(tg), _ptr(w), fp, n_new, len(du), _ptr(du),
+                                    _ptr(dv), len(iu), _ptr(iu), _ptr(iv), _ptr(iw), _ptr(oo), _ptr(ot), _ptr(ow), cap)
+    if a < 0:
+        raise ValueError("invalid update")
+    return oo, ot[:a].copy(), ow[:a].copy()
+
+
+def louvain_from(offsets, targets, weights, initial, params: Params | None = None, stats_cap: int = 128):
+    """Algorithm 1 with the first pass starting from the membership `initial` (a warm start)."""
+    p = params or default_params()
+    offs, tg, w, fp = _graph_args(offsets, targets, weights)
+    n = len(offs) - 1
+    init = _c(initial, np.int32)
+    mem = np.empty(n, dtype=np.int32)
+    q = np.zeros(1, dtype=np.float64)
+    np_ = np.zeros(1, dtype=np.int32)
+    st = (PassStats * stats_cap)()
+    rc = _load().oracle_louvain_from(n, _ptr(offs), _ptr(tg), _ptr(w), fp, ctypes.byref(p), _ptr(init), _ptr(mem),
+                                     _ptr(q), _ptr(np_), st, stats_cap)
+    if rc == 3:
+        raise OverflowError("integer 2m >= 2^31")
+    if rc:
+        raise ValueError(f"oracle_louvain_from failed ({rc})")
+    passes = int(np_[0])
+    stats = [dict(pass_=s.pass_, iterations=s.iterations, moves=s.moves, n_vertices=s.n_vertices, n_arcs=s.n_arcs,
+                  n_communities=s.n_communities, modularity=s.modularity) for s in st[:min(passes, stats_cap)]]
+    return mem, float(q[0]), passes, stats
 
 
 def louvain(offsets, targets, weights, params: Params | None = None, stats_cap: int = 128):

@@ -14,6 +14,11 @@
  *                           re-mark neighbours, per-iteration tolerance test)
  *   aggregation phase ..... Algorithm 3 (community-vertex CSR by counting, super-vertex rows by
  *                           summing arc weights per neighbouring community, self-loops kept)
+ *   dynamic graphs ........ a batch of edge deletions and insertions applied to the CSR, and a run
+ *                           whose first pass starts from a given membership (Section 4.2 keeps the
+ *                           first pass's graph in a format open to batch updates; Figure 2 feeds
+ *                           each later pass an initial membership; the Conclusion names updating
+ *                           the memberships of dynamic graphs as the next step)
  * Readings of points the paper leaves open (each also listed in the design notes):
  *   R1  a self-loop is stored once and counts once in K_i, sigma_c and 2m;
  *   R2  candidates = communities of neighbours j != i, the current community d excluded; best = max N,
@@ -337,7 +342,7 @@ int load_graph(int64_t n, const int64_t* off, const int32_t* tg, const WIn* w, G
 
 template <class A>
 int louvain(Graph<typename A::W> gp, const Params& p, int32_t* membership, double* q_out, int32_t* n_passes,
-            PassStats* stats, int32_t stats_cap, const Graph<typename A::W>& g0) {
+            PassStats* stats, int32_t stats_cap, const Graph<typename A::W>& g0, const int32_t* init = nullptr) {
   typedef typename A::W W;
   const int64_t n = gp.n;
   std::vector<int32_t> C(n);
@@ -354,6 +359,15 @@ int louvain(Graph<typename A::W> gp, const Params& p, int32_t* membership, doubl
     for (W k : K) two_m += k;
     Cp.resize(gp.n);
     for (int64_t i = 0; i < gp.n; i++) Cp[i] = (int32_t)i;
+    if (lp == 0 && init) {
+      // warm start (a dynamic graph's first pass): C' = the given membership, Sigma_c = the sum of
+      // K_i over its members
+      for (int64_t i = 0; i < gp.n; i++) Sig[i] = W(0);
+      for (int64_t i = 0; i < gp.n; i++) {
+        Cp[i] = init[i];
+        Sig[init[i]] += K[i];
+      }
+    }
     std::vector<int32_t> col;
     int32_t ncol = 0;
     if (p.schedule == 0) ncol = colour_graph(gp, p.seed, lp, col);
@@ -507,6 +521,73 @@ int oracle_local_move(int64_t n, const int64_t* off, const int32_t* tg, const vo
   *moves = mv.moves;
   std::copy(Cp.begin(), Cp.end(), cp_out);
   return 0;
+}
+
+/* A batch update of a symmetric CSR with n_old rows into one with n_new >= n_old rows: every arc
+ * between u and v of a deleted edge {u, v} is removed (both directions, all duplicates); then each
+ * inserted edge (u, v, w) adds the arc u->v and, if u != v, the arc v->u, both of weight w.  Row r
+ * of the result holds r's surviving arcs in their old order, then its inserted arcs in list order.
+ * Weights int32 (fp == 0) or float32.  Returns the arc count, or -1 if an id is out of range or
+ * `cap` arcs do not suffice. */
+int64_t oracle_update_graph(int64_t n_old, const int64_t* off, const int32_t* tg, const void* w, int fp, int64_t n_new,
+                            int64_t n_del, const int32_t* del_u, const int32_t* del_v, int64_t n_ins,
+                            const int32_t* ins_u, const int32_t* ins_v, const void* ins_w, int64_t* out_off,
+                            int32_t* out_tg, void* out_w, int64_t cap) {
+  if (n_new < n_old || n_old < 0) return -1;
+  std::vector<std::pair<int32_t, int32_t>> dels;
+  for (int64_t k = 0; k < n_del; k++) {
+    if (del_u[k] < 0 || del_u[k] >= n_new || del_v[k] < 0 || del_v[k] >= n_new) return -1;
+    dels.push_back({std::min(del_u[k], del_v[k]), std::max(del_u[k], del_v[k])});
+  }
+  std::sort(dels.begin(), dels.end());
+  std::vector<std::vector<std::pair<int32_t, int64_t>>> added(n_new);  // (target, insertion index)
+  for (int64_t k = 0; k < n_ins; k++) {
+    if (ins_u[k] < 0 || ins_u[k] >= n_new || ins_v[k] < 0 || ins_v[k] >= n_new) return -1;
+    added[ins_u[k]].push_back({ins_v[k], k});
+    if (ins_u[k] != ins_v[k]) added[ins_v[k]].push_back({ins_u[k], k});
+  }
+  int64_t a = 0;
+  out_off[0] = 0;
+  for (int64_t r = 0; r < n_new; r++) {
+    if (r < n_old)
+      for (int64_t e = off[r]; e < off[r + 1]; e++) {
+        const std::pair<int32_t, int32_t> key{std::min((int32_t)r, tg[e]), std::max((int32_t)r, tg[e])};
+        if (std::binary_search(dels.begin(), dels.end(), key)) continue;
+        if (a >= cap) return -1;
+        out_tg[a] = tg[e];
+        if (fp) ((float*)out_w)[a] = ((const float*)w)[e];
+        else ((int32_t*)out_w)[a] = ((const int32_t*)w)[e];
+        a++;
+      }
+    for (const auto& x : added[r]) {
+      if (a >= cap) return -1;
+      out_tg[a] = x.first;
+      if (fp) ((float*)out_w)[a] = ((const float*)ins_w)[x.second];
+      else ((int32_t*)out_w)[a] = ((const int32_t*)ins_w)[x.second];
+      a++;
+    }
+    out_off[r + 1] = a;
+  }
+  return a;
+}
+
+/* Algorithm 1 whose first pass starts from membership init[n] (ids in [0, n)) instead of
+ * singletons: the warm start of a dynamic graph after a batch update.  Same returns as
+ * oracle_louvain; 1 also for an id out of range. */
+int oracle_louvain_from(int64_t n, const int64_t* off, const int32_t* tg, const void* w, int fp, const oracle_params* p,
+                        const int32_t* init, int32_t* membership, double* q, int32_t* n_passes,
+                        oracle_pass_stats* stats, int32_t stats_cap) {
+  for (int64_t v = 0; v < n; v++) if (init[v] < 0 || init[v] >= n) return 1;
+  if (fp) {
+    Graph<double> g;
+    int rc = load_graph<FpArith>(n, off, tg, (const float*)w, g);
+    if (rc) return rc;
+    return louvain<FpArith>(g, *p, membership, q, n_passes, stats, stats_cap, g, init);
+  }
+  Graph<int64_t> g;
+  int rc = load_graph<IntArith>(n, off, tg, (const int32_t*)w, g);
+  if (rc) return rc;
+  return louvain<IntArith>(g, *p, membership, q, n_passes, stats, stats_cap, g, init);
 }
 
 /* Algorithm 1.  Returns 0 ok, 1 invalid input, 3 integer 2m >= 2^31.  membership [n] gets the

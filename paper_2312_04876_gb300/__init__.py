@@ -247,6 +247,54 @@ class Louvain:
         return membership, RunResult(res.modularity, res.passes, res.total_iterations, res.n_communities,
                                      res.ms_total, res.kernel_launches, _stats_list(st, nst.value))
 
+    def run_from(self, offsets, targets, weights, initial, params: Params | None = None, membership=None,
+                 stream=None, stats_cap: int = 64, **overrides):
+        """louvain_run_from: Algorithm 1 whose first pass starts from the device int32 membership
+        `initial` (a warm start after a batch update).  Returns (membership, RunResult)."""
+        import torch
+        p = params if params is not None else default_params(**overrides)
+        n = offsets.numel() - 1
+        if initial.dtype != torch.int32 or not initial.is_cuda or not initial.is_contiguous() or initial.numel() != n:
+            raise ValueError("initial must be a contiguous int32 CUDA tensor of n entries")
+        if membership is None:
+            membership = torch.empty(max(n, 0), dtype=torch.int32, device=offsets.device)
+        res = Result()
+        st = (PassStats * stats_cap)()
+        ns = ctypes.c_int32()
+        rc = self._lib.louvain_run_from(self._h, n, targets.numel(), offsets.data_ptr(), targets.data_ptr(),
+                                        weights.data_ptr(), _wtype(weights), ctypes.byref(p), _stream_ptr(stream),
+                                        initial.data_ptr(), membership.data_ptr(), ctypes.byref(res), st, stats_cap,
+                                        ctypes.byref(ns))
+        self._check(rc)
+        return membership, RunResult(res.modularity, res.passes, res.total_iterations, res.n_communities,
+                                     res.ms_total, res.kernel_launches, _stats_list(st, ns.value))
+
+    def update_graph(self, offsets, targets, weights, n_new: int, deletions, insertions, insert_weights,
+                     stream=None):
+        """louvain_update_graph: the CSR after deleting the edges `deletions` (int32 [k, 2]) and
+        inserting `insertions` (int32 [k, 2]) with `insert_weights`, rows grown to n_new; all device
+        tensors.  Returns (offsets, targets, weights) of the updated graph."""
+        import torch
+        dev = offsets.device
+        dl = deletions.reshape(-1, 2).to(dev, torch.int32)
+        il = insertions.reshape(-1, 2).to(dev, torch.int32)
+        du, dv = dl[:, 0].contiguous(), dl[:, 1].contiguous()
+        iu, iv = il[:, 0].contiguous(), il[:, 1].contiguous()
+        iw = insert_weights.to(dev, weights.dtype).contiguous()
+        cap = targets.numel() + 2 * iu.numel()
+        oo = torch.empty(n_new + 1, dtype=torch.int64, device=dev)
+        ot = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        ow = torch.empty(max(cap, 1), dtype=weights.dtype, device=dev)
+        na = ctypes.c_int64()
+        rc = self._lib.louvain_update_graph(self._h, offsets.numel() - 1, targets.numel(), offsets.data_ptr(),
+                                            targets.data_ptr(), weights.data_ptr(), _wtype(weights), n_new,
+                                            du.numel(), du.data_ptr(), dv.data_ptr(), iu.numel(), iu.data_ptr(),
+                                            iv.data_ptr(), iw.data_ptr(), _stream_ptr(stream), oo.data_ptr(),
+                                            ot.data_ptr(), ow.data_ptr(), cap, ctypes.byref(na))
+        self._check(rc)
+        a = int(na.value)
+        return oo, ot[:a], ow[:a]
+
     def run_host(self, offsets, targets, weights, params: Params | None = None, membership=None, stream=None,
                  stats_cap: int = 64, **overrides):
         """louvain_run_host on host arrays (numpy or CPU tensors; pinned memory is fastest)."""

@@ -65,6 +65,10 @@ SIGNATURES = {
     "louvain_last_error": (ctypes.c_char_p, [_V]),
     "louvain_status_string": (ctypes.c_char_p, [_I32]),
     "louvain_workspace_bytes": (_I32, [_V, ctypes.POINTER(ctypes.c_size_t)]),
+    "louvain_run_from": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V, _V, _V,
+                                ctypes.POINTER(Result), ctypes.POINTER(PassStats), _I32, ctypes.POINTER(_I32)]),
+    "louvain_update_graph": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, _I64, _I64, _V, _V, _I64, _V, _V, _V, _V,
+                                    _V, _V, _V, _I64, ctypes.POINTER(_I64)]),
     "louvain_inject_alloc_failure": (_I32, [_V, _I32]),
     "louvain_run": (_I32, [_V, _I64, _I64, _V, _V, _V, _I32, ctypes.POINTER(Params), _V, _V, ctypes.POINTER(Result),
                            ctypes.POINTER(PassStats), _I32, ctypes.POINTER(_I32)]),

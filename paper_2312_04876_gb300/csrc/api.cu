@@ -63,6 +63,9 @@ struct Workspace {
   int32_t* pool = nullptr;    // giant-row table pool: gt_slots_total {key, value} pairs
   int32_t* dperm = nullptr;   // [n] vertex ids by degree bucket, kept for the whole pass
   DevAlloc desc_alloc;        // step records of captured iterations (kStepWords per class step)
+  DevAlloc upd_alloc;         // batch graph update: deleted-pair set, row counters, scan scratch
+  unsigned long long* upd = nullptr;
+  int64_t upd_words = 0;
   int64_t* desc = nullptr;
   int64_t desc_cap = 0;       // int64 words
   int32_t* glist = nullptr;   // [gcap] giant vertices of a pass, class by class
@@ -157,7 +160,7 @@ namespace {
 
 size_t total_bytes(const Workspace& ws) {
   return ws.core.bytes + ws.keys_alloc.bytes + ws.gt_alloc.bytes + ws.in_alloc.bytes + ws.batch_alloc.bytes +
-         ws.desc_alloc.bytes;
+         ws.desc_alloc.bytes + ws.upd_alloc.bytes;
 }
 
 void free_all(DevAlloc& a) {
@@ -972,7 +975,7 @@ louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typenam
 template <class M>
 louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, const int64_t* offs, const int32_t* tg,
                         const typename M::w_t* w, const louvain_params& p, int32_t* C, RunOut* out,
-                        louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats) {
+                        louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats, const int32_t* init) {
   typedef typename M::a_t A;
   typedef typename M::w_t W;
   Workspace& ws = h->ws;
@@ -1003,6 +1006,7 @@ louvain_status run_impl(louvain_handle h, Ctx& c, int64_t n, int64_t n_arcs, con
       if (!hc) return s;
       if (!M::is_fp && hc->two_m_i >= (1LL << 31))
         return set_err(h, LOUVAIN_ERR_OVERFLOW, "integer mode needs 2m < 2^31");
+      if (init) warm_init<M>(c, st, init, n_cur);  // a warm start: pass 0 from the given membership
     } else {
       vertex_init<M>(c, st, n_cur, true);
     }
@@ -1384,6 +1388,7 @@ void louvain_destroy(louvain_handle h) {
   free_all(h->ws.in_alloc);
   free_all(h->ws.batch_alloc);
   free_all(h->ws.desc_alloc);
+  free_all(h->ws.upd_alloc);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
   for (cudaEvent_t e : h->fork_ev) cudaEventDestroy(e);
@@ -1511,10 +1516,11 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
   return LOUVAIN_OK;
 }
 
-louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
-                           const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
-                           const louvain_params* p, void* stream, int32_t* d_membership, louvain_result* res,
-                           louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats) {
+namespace {
+louvain_status run_entry(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                         const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                         const louvain_params* p, void* stream, const int32_t* d_init, int32_t* d_membership,
+                         louvain_result* res, louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats) {
   louvain_status s = begin_call(h);
   if (s != LOUVAIN_OK) return s;
   if ((s = check_graph_args(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
@@ -1540,6 +1546,13 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
   if (p->validate) {
     if ((s = validate_graph(h, c, n, n_arcs, d_offsets, d_targets, d_weights, fp)) != LOUVAIN_OK) return s;
   }
+  if (d_init && n > 0) {
+    validate_reset(c, h->ws.ctrl);
+    validate_range(c, d_init, n, n, h->ws.ctrl);
+    const Ctrl* hc = read_ctrl(h, c, &s, "initial membership range");
+    if (!hc) return s;
+    if (hc->cnt[5]) return set_err(h, LOUVAIN_ERR_INVALID, "initial membership id outside [0, n)");
+  }
   RunOut out;
   if (n == 0 && p->max_passes > 0) {
     // an empty graph still takes one (empty) pass whose single iteration converges at once
@@ -1554,10 +1567,10 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
   if (n > 0) {
     if (fp)
       s = run_impl<FpMode>(h, c, n, n_arcs, d_offsets, d_targets, reinterpret_cast<const float*>(d_weights), *p,
-                           d_membership, &out, stats, stats_cap, n_stats);
+                           d_membership, &out, stats, stats_cap, n_stats, d_init);
     else
       s = run_impl<IntMode>(h, c, n, n_arcs, d_offsets, d_targets, reinterpret_cast<const int32_t*>(d_weights), *p,
-                            d_membership, &out, stats, stats_cap, n_stats);
+                            d_membership, &out, stats, stats_cap, n_stats, d_init);
     if (s != LOUVAIN_OK) {
       cudaStreamSynchronize(c.s);
       cudaGetLastError();
@@ -1577,6 +1590,73 @@ louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const in
     res->kernel_launches = (int32_t)c.launches;
   }
   return LOUVAIN_OK;
+}
+}  // namespace
+
+louvain_status louvain_run(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                           const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                           const louvain_params* p, void* stream, int32_t* d_membership, louvain_result* res,
+                           louvain_pass_stats* stats, int32_t stats_cap, int32_t* n_stats) {
+  return run_entry(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype, p, stream, nullptr, d_membership, res, stats,
+                   stats_cap, n_stats);
+}
+
+louvain_status louvain_run_from(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
+                                const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                const louvain_params* p, void* stream, const int32_t* d_initial,
+                                int32_t* d_membership, louvain_result* res, louvain_pass_stats* stats,
+                                int32_t stats_cap, int32_t* n_stats) {
+  if (h && n > 0 && !d_initial) return set_err(h, LOUVAIN_ERR_INVALID, "initial membership pointer is NULL");
+  return run_entry(h, n, n_arcs, d_offsets, d_targets, d_weights, wtype, p, stream, d_initial, d_membership, res,
+                   stats, stats_cap, n_stats);
+}
+
+louvain_status louvain_update_graph(louvain_handle h, int64_t n_old, int64_t n_arcs, const int64_t* d_offsets,
+                                    const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
+                                    int64_t n_new, int64_t n_del, const int32_t* d_del_u, const int32_t* d_del_v,
+                                    int64_t n_ins, const int32_t* d_ins_u, const int32_t* d_ins_v,
+                                    const void* d_ins_w, void* stream, int64_t* d_out_offsets,
+                                    int32_t* d_out_targets, void* d_out_weights, int64_t out_cap,
+                                    int64_t* out_arcs) {
+  louvain_status s = begin_call(h);
+  if (s != LOUVAIN_OK) return s;
+  if ((s = check_graph_args(h, n_old, n_arcs, d_offsets, d_targets, d_weights, wtype)) != LOUVAIN_OK) return s;
+  if (n_new < n_old || n_new >= 0x7fffffffLL) return set_err(h, LOUVAIN_ERR_INVALID, "n_new must be in [n_old, 2^31 - 1)");
+  if (n_del < 0 || n_ins < 0 || out_cap < 0 || !out_arcs || !d_out_offsets)
+    return set_err(h, LOUVAIN_ERR_INVALID, "invalid counts or NULL output");
+  if (n_del > 0 && (!d_del_u || !d_del_v)) return set_err(h, LOUVAIN_ERR_INVALID, "deletion pointer is NULL");
+  if (n_ins > 0 && (!d_ins_u || !d_ins_v || !d_ins_w)) return set_err(h, LOUVAIN_ERR_INVALID, "insertion pointer is NULL");
+  if (out_cap > 0 && (!d_out_targets || !d_out_weights)) return set_err(h, LOUVAIN_ERR_INVALID, "output pointer is NULL");
+  Ctx c;
+  c.s = reinterpret_cast<cudaStream_t>(stream);
+  c.num_sms = h->num_sms;
+  Workspace& ws = h->ws;
+  if ((s = ensure_workspace(h, 1, 1)) != LOUVAIN_OK) return s;  // the control block
+  const int64_t words = update_scratch_words(n_new, n_del) + scan_tmp_elems(n_new) + 8;
+  if (ws.upd_words < words) {
+    free_all(ws.upd_alloc);
+    ws.upd_words = 0;
+    if (!dalloc(h, ws.upd_alloc, &ws.upd, words)) {
+      free_all(ws.upd_alloc);
+      return set_err(h, LOUVAIN_ERR_OOM, "graph-update scratch allocation failed");
+    }
+    ws.upd_words = words;
+  }
+  int64_t* tile_tmp = reinterpret_cast<int64_t*>(ws.upd + update_scratch_words(n_new, n_del));
+  validate_reset(c, ws.ctrl);
+  const int slots = update_count(c, n_old, n_arcs, d_offsets, d_targets, n_new, d_del_u, d_del_v, n_del, d_ins_u, d_ins_v,
+                                 d_ins_w, n_ins, ws.upd, d_out_offsets, tile_tmp, ws.ctrl);
+  const Ctrl* hc = read_ctrl(h, c, &s, "graph update counts");
+  if (!hc) return s;
+  if (hc->cnt[5]) return set_err(h, LOUVAIN_ERR_INVALID, "update vertex id outside [0, n_new)");
+  const int64_t* tot = read_i64(h, c, d_out_offsets + n_new, 1, &s, "graph update size");
+  if (!tot) return s;
+  const int64_t total = tot[0];
+  *out_arcs = total;
+  if (total > out_cap) return set_err(h, LOUVAIN_ERR_INVALID, "output capacity below the updated arc count");
+  update_fill(c, n_old, n_arcs, d_offsets, d_targets, d_weights, n_new, n_del, d_ins_u, d_ins_v, d_ins_w, n_ins, ws.upd,
+              (unsigned)slots, d_out_offsets, d_out_targets, d_out_weights, ws.ctrl);
+  return sync(h, c, "graph update");
 }
 
 louvain_status louvain_run_host(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* h_offsets,

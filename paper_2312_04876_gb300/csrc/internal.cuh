@@ -295,6 +295,26 @@ size_t handle_device_bytes(louvain_handle h);       // device bytes the handle h
 void handle_set_budget(louvain_handle h, size_t bytes);  // cap of its further allocations (0 = none)
 void handle_trim(louvain_handle h);                 // free everything it caches
 
+// ---------------------------------------------------------------- dynamic.cu
+// Scratch (64-bit words) of a batch update: the deleted-pair set and the per-row counters.
+int64_t update_scratch_words(int64_t n_new, int64_t n_del);
+// Counts the arcs of every new row (surviving old arcs + inserted arcs) and scans them into
+// out_off[n_new + 1]; ctrl->cnt[5] += ids out of range.  Returns the deleted-pair set's slot count.
+int update_count(Ctx& c, int64_t n_old, int64_t n_arcs, const int64_t* off, const int32_t* tg, int64_t n_new,
+                 const int32_t* du,
+                 const int32_t* dv, int64_t n_del, const int32_t* iu, const int32_t* iv, const void* iw,
+                 int64_t n_ins, unsigned long long* scratch, int64_t* out_off, int64_t* tile_tmp, Ctrl* ctrl);
+// Writes the rows counted by update_count: surviving arcs first, then inserted arcs (each group in
+// unspecified order).
+void update_fill(Ctx& c, int64_t n_old, int64_t n_arcs, const int64_t* off, const int32_t* tg, const void* w,
+                 int64_t n_new,
+                 int64_t n_del, const int32_t* iu, const int32_t* iv, const void* iw, int64_t n_ins,
+                 unsigned long long* scratch, unsigned slots, const int64_t* out_off, int32_t* otg, void* ow,
+                 Ctrl* ctrl);
+// Pass-0 state of a warm start: Cp = init, Sigma_c = sum of K_i over c's members, csize = member counts.
+template <class M>
+void warm_init(Ctx& c, const PassState<M>& st, const int32_t* init, int64_t n);
+
 // ---------------------------------------------------------------- validate.cu
 // ctrl->cnt[0..3] receive: bad offsets, bad targets, bad weights, asymmetry hash; ctrl->acc_f[0]
 // the weight total (double), ctrl->acc_i[0] the integer weight total (saturating).

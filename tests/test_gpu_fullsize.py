@@ -1,4 +1,5 @@
-"""Full-size parity: the 10k SBM, R-MAT scale 20 and 22 and the 24M-vertex road-like grid against the
+"""Full-size parity: the 10k SBM, R-MAT scale 20 and 22 (also without its isolated vertices) and the
+24M-vertex road-like grid against the
 CPU oracle's stored results, R-MAT scale 18 with fp32 weights (hub rows over 4096 arcs) against the
 stored fp64 oracle result, and R-MAT scale 27 with fp32 weights by invariants.
 
@@ -30,6 +31,7 @@ GEN = {
     "rmat20": lambda: gg.rmat(20, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "rmat22": lambda: gg.rmat(22, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "grid24m": lambda: gg.grid(4899, 4899, 0.10, 0.01, 3),
+    "rmat22_noiso": lambda: gg.drop_isolated(gg.rmat(22, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8)),
 }
 
 
@@ -48,7 +50,7 @@ def L(cuda_ok):
     h.close()
 
 
-@pytest.fixture(scope="module", params=["sbm10k", "rmat20", "rmat22", "grid24m"])
+@pytest.fixture(scope="module", params=["sbm10k", "rmat20", "rmat22", "grid24m", "rmat22_noiso"])
 def workload(request):
     with open(os.path.join(GOLDEN, f"{request.param}_oracle.json")) as f:
         gold = json.load(f)

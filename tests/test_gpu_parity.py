@@ -317,7 +317,9 @@ def test_injected_allocation_failure_returns_oom_without_leak(cuda_ok):
     h0.inject_alloc_failure(1)
     with pytest.raises(lv.LouvainError):
         h0.run(o, t, w, mode="deterministic", membership=mem)
+    mem.fill_(-1)  # the torch kernels the loop uses are loaded (lazily, into device memory) here
     h0.run(o, t, w, mode="deterministic", membership=mem)
+    assert np.array_equal(mem.cpu().numpy(), ref_mem)
     h0.close()
     torch.cuda.synchronize()
     torch.cuda.empty_cache()

@@ -468,3 +468,101 @@ def test_hand_traced_pins_catch_planted_mistakes(tmp_path):
                            env=env, capture_output=True, text=True, cwd=os.path.dirname(here))
         assert r.returncode == 1, (name, r.stdout[-2000:])
         assert "failed" in r.stdout, name
+
+
+# ---------------------------------------------------------------- dynamic graphs: batch update and warm start
+def _random_update(g, rng, n_new, n_del, n_ins):
+    """Deletions: existing edges plus a pair that is not an edge; insertions: new pairs, an existing
+    edge again (its arcs duplicate) and a self-loop; ids may reach the new rows n..n_new-1."""
+    edges = [(u, int(v)) for u in range(g.n) for v in g.targets[g.offsets[u]:g.offsets[u + 1]] if u <= v]
+    pick = rng.choice(len(edges), size=min(n_del, len(edges)), replace=False)
+    dels = [edges[k] for k in pick] + [(0, n_new - 1)]
+    ins = [(int(rng.integers(0, n_new)), int(rng.integers(0, n_new))) for _ in range(n_ins)]
+    ins += [edges[int(pick[0])], (3, 3)]
+    iw = rng.integers(1, 9, size=len(ins)).astype(np.int32)
+    return dels, ins, iw
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_update_graph_vs_dense_matrix(seed):
+    """The updated CSR's dense matrix equals the old one with every deleted pair zeroed (both
+    directions) and each insertion added at (u, v) and (v, u) (once on the diagonal)."""
+    rng = np.random.default_rng(seed)
+    g = random_graph(14, 0.3, rng, self_loops=seed % 2 == 1)
+    n_new = g.n + 3
+    dels, ins, iw = _random_update(g, rng, n_new, 6, 8)
+    oo, ot, ow = oracle.update_graph(g.offsets, g.targets, g.weights, n_new, dels, ins, iw)
+    a = np.zeros((n_new, n_new), dtype=np.int64)
+    a[:g.n, :g.n] = dense_adjacency(g)
+    for u, v in dels:
+        a[u, v] = a[v, u] = 0
+    for (u, v), w in zip(ins, iw):
+        a[u, v] += w
+        if u != v:
+            a[v, u] += w
+    h = gg.Graph(n=n_new, offsets=oo, targets=ot, weights=ow)
+    assert np.array_equal(dense_adjacency(h), a)
+    # rows keep their surviving arcs in order, then the inserted ones in list order
+    r = ins[0][0]
+    assert ot[oo[r + 1] - 1] in [v for (u, v) in ins if u == r] + [u for (u, v) in ins if v == r]
+
+
+def test_warm_start_from_singletons_is_the_cold_run():
+    g = gg.sbm(600, 6, 0.2, 0.01, 3)
+    for sched in (0, 1):
+        p = oracle.default_params(schedule=sched, seed=4)
+        cold = oracle.louvain(g.offsets, g.targets, g.weights, p)
+        warm = oracle.louvain_from(g.offsets, g.targets, g.weights, np.arange(g.n), p)
+        assert np.array_equal(cold[0], warm[0]) and cold[1:3] == warm[1:3]
+        assert [s["iterations"] for s in cold[3]] == [s["iterations"] for s in warm[3]]
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_warm_start_at_a_clique_partition_stays_put(schedule):
+    """Ring of k K_s cliques started from its cliques (ids shuffled): a member of clique c gains
+    K_i->c' = 1 by joining the neighbouring clique and loses K_i->c = s - 1, so no N is positive;
+    the first iteration moves nothing, l_i = 1 ends the run after one pass, and the output is the
+    cliques with the closed-form modularity s(s-1)/(s(s-1)+2) - 1/k."""
+    k, s = 5, 6
+    g = cliques(k, s, ring=True)
+    ids = np.random.default_rng(1).permutation(g.n)[:k]
+    init = np.repeat(ids, s).astype(np.int32)
+    mem, q, passes, stats = oracle.louvain_from(g.offsets, g.targets, g.weights, init,
+                                                oracle.default_params(schedule=schedule))
+    assert passes == 1 and stats[0]["iterations"] == 1 and stats[0]["moves"] == 0
+    assert mem.tolist() == canonical(init).tolist()
+    assert q == float(Fraction(s * (s - 1), s * (s - 1) + 2) - Fraction(1, k))
+
+
+def test_warm_start_cannot_split_one_community():
+    """Every vertex in one community: each vertex's neighbours are all in its own community, so it
+    has no candidate; nothing moves and the result is that one community, Q = 1 - 1 = 0."""
+    g = cliques(3, 5, ring=True)
+    mem, q, passes, stats = oracle.louvain_from(g.offsets, g.targets, g.weights, np.full(g.n, 7, dtype=np.int32))
+    assert mem.tolist() == [0] * g.n and q == 0.0 and passes == 1 and stats[0]["moves"] == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sequential_warm_start_never_loses_modularity(seed):
+    """Under the sequential schedule every move has N > 0 (Delta Q > 0) and aggregation keeps Q, so
+    a warm start ends at or above the modularity of the membership it started from."""
+    rng = np.random.default_rng(50 + seed)
+    g = random_graph(30, 0.15, rng)
+    init = rng.integers(0, 6, size=g.n).astype(np.int32)
+    _, q, _, _ = oracle.louvain_from(g.offsets, g.targets, g.weights, init, oracle.default_params(schedule=1))
+    assert q >= float(q_exact(dense_adjacency(g), init)) - 1e-15
+
+
+def test_warm_start_after_a_small_update_matches_the_cold_run():
+    """A planted partition, 1% of its edges deleted and as many random edges inserted: the warm start
+    from the old result reaches the cold run's modularity on the updated graph within 0.005."""
+    g = gg.sbm(3000, 30, 0.1, 0.001, 8)
+    rng = np.random.default_rng(2)
+    mem, _, _, _ = oracle.louvain(g.offsets, g.targets, g.weights)
+    m = g.n_arcs // 2
+    dels, ins, iw = _random_update(g, rng, g.n, m // 100, m // 100)
+    oo, ot, ow = oracle.update_graph(g.offsets, g.targets, g.weights, g.n, dels, ins, iw)
+    cold_m, cold_q, _, _ = oracle.louvain(oo, ot, ow)
+    warm_m, warm_q, _, _ = oracle.louvain_from(oo, ot, ow, mem)
+    assert abs(warm_q - cold_q) <= 0.005
+    assert warm_q == pytest.approx(oracle.modularity(oo, ot, ow, warm_m), abs=0)

@@ -622,6 +622,40 @@ def block_dynamic(ctx, frac: float = 0.005, steps: int = 5, warmup: int = 3):
     return out
 
 
+def block_host_arcs(ctx, steps: int = 3, warmup: int = 3):
+    """R-MAT 22 with params.host_arcs = 1, the placement for graphs whose arcs do not fit in HBM: the
+    input's targets and weights are read in place from pinned host memory and the super-vertex
+    graphs' arc buffers live in pinned host memory, all over NVLink-C2C; HBM holds the per-vertex
+    state.  Timed end to end through louvain_run_host (offsets upload and membership download
+    inside), beside the HBM bytes the handle needed in each placement."""
+    import torch
+    import paper_2312_04876_gb300 as lv
+    g, gpu = ctx["g"], ctx["gpu"]
+    ho, ht, hw = (torch.from_numpy(a).pin_memory() for a in (g.offsets, g.targets, g.weights))
+    hm = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    out = {"workload": WORKLOADS["rmat22"][1] + "; arcs in host memory", "mode": "fast", "steps": steps,
+           "warmup": warmup}
+    for host in (1, 0):
+        L = lv.Louvain(gpu)
+        try:
+            params = lv.default_params(mode="fast", validate=0, host_arcs=host)
+            for _ in range(warmup):
+                L.run_host(ho, ht, hw, params, membership=hm)
+            res = []
+            with ClockSampler(gpu) as clk:
+                t0 = time.perf_counter()
+                for _ in range(steps):
+                    res.append(L.run_host(ho, ht, hw, params, membership=hm)[1])
+                dt = (time.perf_counter() - t0) / steps
+            out["host_arcs" if host else "hbm_arcs"] = {
+                "ms_per_step": 1e3 * dt, "edges_per_second": g.n_arcs / dt, "modularity": res[-1].modularity,
+                "hbm_workspace_gb": L.workspace_bytes() / 1e9, "clocks": clk.summary()}
+        finally:
+            L.close()
+    out["oracle_match"] = oracle_match("rmat22", "fast", out["host_arcs"]["modularity"], None)
+    return out
+
+
 def in_child(workload: str):
     """A block run as `bench.py --workload <workload>` in a fresh process (its own CUDA context, host
     heap and threads), so that what earlier blocks left behind does not colour its timing."""
@@ -638,7 +672,8 @@ def in_child(workload: str):
 
 
 SUITE = [("rmat22_deterministic", block_rmat22_deterministic), ("rmat22_noiso_fast", block_rmat22_noiso),
-         ("grid24m", block_grid), ("dynamic_rmat22", block_dynamic), ("rmat27_fp32_fast", in_child("rmat27_fp32")), ("batched", in_child("batch")),
+         ("grid24m", block_grid), ("dynamic_rmat22", block_dynamic),
+         ("host_arcs_rmat22", block_host_arcs), ("rmat27_fp32_fast", in_child("rmat27_fp32")), ("batched", in_child("batch")),
          ("serving", in_child("serve"))]
 
 

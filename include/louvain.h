@@ -98,6 +98,13 @@ typedef struct {
                                     block gives up (0 = built-in, about 0.3 s).  A wait that runs out
                                     ends the kernel on every block and the call returns
                                     LOUVAIN_ERR_TIMEOUT; the handle stays usable */
+  int32_t host_arcs;             /* 1: graphs whose arcs do not fit in HBM.  The super-vertex graphs'
+                                    arc buffers (four of n_arcs entries) live in pinned host memory
+                                    that the kernels read and write in place over NVLink-C2C, and
+                                    louvain_run_host reads the input's targets and weights in place
+                                    (registering them for the call unless already pinned) and copies
+                                    only the offsets; per-vertex state stays in HBM.  Results are
+                                    those of the default placement (0) */
 } louvain_params;
 
 typedef struct {
@@ -137,7 +144,8 @@ void louvain_destroy(louvain_handle h);
 /* Defaults from Section 4.1: max_iterations 20, tolerance 0.01, tolerance_drop 10,
  * aggregation_tolerance 0.8, pruning on; max_passes 10; deterministic mode; seed 0;
  * validate 1; compact 1; pass_modularity 0; profile 0; fast_classes 16; fast_classes_later 1;
- * fast_giant_class, lm_blocks_per_sm, giant_min_degree and wait_spins 0 (their built-in choices). */
+ * fast_giant_class, lm_blocks_per_sm, giant_min_degree, wait_spins and host_arcs 0 (their built-in
+ * choices). */
 louvain_status louvain_default_params(louvain_params* p);
 
 /* Algorithm 1 as louvain_run, but the first pass starts from the membership d_initial[n] (device,

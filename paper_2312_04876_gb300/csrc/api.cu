@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <unistd.h>
+
 #include "internal.cuh"
 
 using namespace lv;
@@ -22,6 +24,7 @@ namespace {
 struct DevAlloc {
   std::vector<void*> ptrs;
   size_t bytes = 0;
+  bool host = false;  // pinned, mapped host memory (cudaHostAlloc) instead of device memory
 };
 
 struct RowSet {
@@ -48,7 +51,10 @@ struct Workspace {
   uint8_t* flags = nullptr;
   int64_t *newid = nullptr, *coff = nullptr, *cdeg = nullptr, *len = nullptr, *tile_tmp = nullptr;
   RowSet rows[2];
-  // arcs
+  // arcs of the super-vertex graphs (holey merge target A, compaction target B), in HBM or, for
+  // graphs whose arcs do not fit there, in pinned host memory the kernels reach over NVLink-C2C
+  DevAlloc arc_alloc;
+  int64_t arc_cap = -1;
   int32_t *tgA = nullptr, *tgB = nullptr;
   void *wA = nullptr, *wB = nullptr;
   Ctrl* ctrl = nullptr;
@@ -152,19 +158,24 @@ struct louvain_handle_s {
   int64_t dpin_cap = 0;
   uint64_t call_seq = 0;           // API calls so far (begin_call)
   int64_t fail_alloc_in = 0;       // > 0: the fail_alloc_in-th device allocation from now fails (injected)
+  bool arcs_host = false;          // params.host_arcs of the current call: arc buffers in host memory
 };
 
 constexpr size_t kExecCache = 16;
 
 namespace {
 
+// Device bytes (host-resident arc buffers are not HBM and do not count against the budget).
 size_t total_bytes(const Workspace& ws) {
   return ws.core.bytes + ws.keys_alloc.bytes + ws.gt_alloc.bytes + ws.in_alloc.bytes + ws.batch_alloc.bytes +
-         ws.desc_alloc.bytes + ws.upd_alloc.bytes;
+         ws.desc_alloc.bytes + ws.upd_alloc.bytes + (ws.arc_alloc.host ? 0 : ws.arc_alloc.bytes);
 }
 
 void free_all(DevAlloc& a) {
-  for (void* p : a.ptrs) cudaFree(p);
+  for (void* p : a.ptrs) {
+    if (a.host) cudaFreeHost(p);
+    else cudaFree(p);
+  }
   a.ptrs.clear();
   a.bytes = 0;
 }
@@ -182,17 +193,56 @@ template <class T>
 bool dalloc(louvain_handle h, DevAlloc& a, T** p, int64_t count) {
   size_t bytes = (size_t)(count > 0 ? count : 1) * sizeof(T);
   bytes = (bytes + 255) & ~(size_t)255;
-  if (h->budget && total_bytes(h->ws) + bytes > h->budget) return false;
+  if (!a.host && h->budget && total_bytes(h->ws) + bytes > h->budget) return false;
   if (h->fail_alloc_in > 0 && --h->fail_alloc_in == 0) return false;  // louvain_inject_alloc_failure
   void* q = nullptr;
-  if (cudaMalloc(&q, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+  void* d = nullptr;
+  if (a.host) {
+    // pinned and mapped: the kernels read and write it in place over NVLink-C2C
+    if (cudaHostAlloc(&q, bytes, cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (cudaHostGetDevicePointer(&d, q, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(q);
+      return false;
+    }
+  } else {
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    d = q;
   }
   a.ptrs.push_back(q);
   a.bytes += bytes;
-  *p = reinterpret_cast<T*>(q);
+  *p = reinterpret_cast<T*>(d);
   return true;
+}
+
+// The four arc buffers of the super-vertex graphs, `a` arcs each, placed as the current call asks
+// (h->arcs_host); a placement change reallocates them.
+louvain_status ensure_arcs(louvain_handle h, int64_t a) {
+  Workspace& ws = h->ws;
+  if (ws.arc_cap >= a && ws.arc_alloc.host == h->arcs_host && ws.tgA) return LOUVAIN_OK;
+  const int64_t ac = (ws.arc_alloc.host == h->arcs_host && ws.arc_cap > a) ? ws.arc_cap : a;
+  free_all(ws.arc_alloc);
+  ws.arc_cap = -1;
+  ws.tgA = ws.tgB = nullptr;
+  ws.wA = ws.wB = nullptr;
+  ws.arc_alloc.host = h->arcs_host;
+  DevAlloc& d = ws.arc_alloc;
+  if (!(dalloc(h, d, &ws.tgA, ac) && dalloc(h, d, &ws.tgB, ac) && dalloc(h, d, (int32_t**)&ws.wA, ac) &&
+        dalloc(h, d, (int32_t**)&ws.wB, ac))) {
+    free_all(ws.arc_alloc);
+    ws.tgA = ws.tgB = nullptr;
+    ws.wA = ws.wB = nullptr;
+    return set_err(h, LOUVAIN_ERR_OOM, h->arcs_host ? "pinned host allocation of the arc buffers failed"
+                                                    : "arc-buffer allocation failed or exceeds the HBM budget");
+  }
+  ws.arc_cap = ac;
+  return LOUVAIN_OK;
 }
 
 louvain_status ensure_pinned(louvain_handle h, size_t bytes) {
@@ -211,7 +261,7 @@ louvain_status ensure_pinned(louvain_handle h, size_t bytes) {
 
 louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   Workspace& ws = h->ws;
-  if (ws.n_cap >= n && ws.a_cap >= a && ws.ctrl) return LOUVAIN_OK;
+  if (ws.n_cap >= n && ws.a_cap >= a && ws.ctrl) return ensure_arcs(h, a);
   int64_t nc = n > ws.n_cap ? n : ws.n_cap;
   int64_t ac = a > ws.a_cap ? a : ws.a_cap;
   free_all(ws.core);
@@ -253,8 +303,7 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   for (int r = 0; r < 2 && ok; r++)
     ok = dalloc(h, d, &ws.rows[r].hoff, n1 + 1) && dalloc(h, d, &ws.rows[r].hend, n1) &&
          dalloc(h, d, &ws.rows[r].doff, n1 + 1);
-  ok = ok && dalloc(h, d, &ws.tgA, ac) && dalloc(h, d, &ws.tgB, ac) && dalloc(h, d, (int32_t**)&ws.wA, ac) &&
-       dalloc(h, d, (int32_t**)&ws.wB, ac) && dalloc(h, d, &ws.ctrl, 1);
+  ok = ok && dalloc(h, d, &ws.ctrl, 1);
   if (!ok) {
     free_all(ws.core);
     return set_err(h, LOUVAIN_ERR_OOM, "workspace allocation failed or exceeds the HBM budget");
@@ -268,7 +317,7 @@ louvain_status ensure_workspace(louvain_handle h, int64_t n, int64_t a) {
   }
   ws.n_cap = nc;
   ws.a_cap = ac;
-  return LOUVAIN_OK;
+  return ensure_arcs(h, ac);
 }
 
 louvain_status ensure_keys(louvain_handle h, int64_t nkeys) {
@@ -430,7 +479,7 @@ bool valid_params(const louvain_params* p) {
          p->aggregation_tolerance >= 0.0 && p->fast_classes >= 0 && p->fast_classes <= 4096 &&
          p->lm_blocks_per_sm >= 0 && p->lm_blocks_per_sm <= 64 && p->fast_classes_later >= 0 &&
          (p->giant_min_degree == 0 || (p->giant_min_degree >= 2048 && p->giant_min_degree <= 4096)) &&
-         p->wait_spins >= 0 &&
+         p->wait_spins >= 0 && (p->host_arcs == 0 || p->host_arcs == 1) &&
          (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
 }
 
@@ -1308,6 +1357,12 @@ void handle_trim(louvain_handle h) {
   free_all(ws.in_alloc);
   free_all(ws.batch_alloc);
   free_all(ws.desc_alloc);
+  free_all(ws.upd_alloc);
+  free_all(ws.arc_alloc);
+  ws.upd_words = 0;
+  ws.arc_cap = -1;
+  ws.tgA = ws.tgB = nullptr;
+  ws.wA = ws.wB = nullptr;
   ws.desc = nullptr;
   ws.desc_cap = 0;
   ws.n_cap = ws.a_cap = -1;
@@ -1389,6 +1444,7 @@ void louvain_destroy(louvain_handle h) {
   free_all(h->ws.batch_alloc);
   free_all(h->ws.desc_alloc);
   free_all(h->ws.upd_alloc);
+  free_all(h->ws.arc_alloc);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   for (cudaEvent_t e : h->prof.ev) cudaEventDestroy(e);
   for (cudaEvent_t e : h->fork_ev) cudaEventDestroy(e);
@@ -1441,6 +1497,7 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
   if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
   if (p) c.wait_spins = p->wait_spins;
   h->prof.on = p->profile != 0;
+  h->arcs_host = p->host_arcs != 0;
   h->prof.used = 0;
   h->prof.recs.clear();
   h->prof.valid = false;
@@ -1535,6 +1592,7 @@ louvain_status run_entry(louvain_handle h, int64_t n, int64_t n_arcs, const int6
   if (res) std::memset(res, 0, sizeof(*res));
   if (n_stats) *n_stats = 0;
   h->prof.on = p->profile != 0;
+  h->arcs_host = p->host_arcs != 0;
   h->prof.used = 0;
   h->prof.recs.clear();
   h->prof.valid = false;
@@ -1659,6 +1717,75 @@ louvain_status louvain_update_graph(louvain_handle h, int64_t n_old, int64_t n_a
   return sync(h, c, "graph update");
 }
 
+namespace {
+// Host arrays the GPU reads in place.  Where the device reads pageable host memory through the
+// host's page tables (Grace: ATS over NVLink-C2C) the arrays are used as they are.  Elsewhere the
+// pages holding them are registered (mapped, read-only where supported) for the call -- arrays whose
+// pages touch are registered as one range -- unless they are pinned already.
+struct HostViews {
+  std::vector<void*> registered;
+  ~HostViews() {
+    for (void* b : registered) cudaHostUnregister(b);
+  }
+};
+
+bool pinned_throughout(const void* p, size_t bytes) {
+  for (const char* q : {static_cast<const char*>(p), static_cast<const char*>(p) + bytes - 1}) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, q) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return true;
+}
+
+cudaError_t host_views(HostViews& v, int device, const void* const* ptrs, const size_t* bytes, int k,
+                       const void** dptrs) {
+  int pageable = 0;
+  cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+  cudaGetLastError();
+  const uintptr_t page = (uintptr_t)sysconf(_SC_PAGESIZE);
+  std::vector<std::pair<uintptr_t, uintptr_t>> ranges;  // page-aligned ranges still to register
+  for (int i = 0; i < k; i++) {
+    dptrs[i] = ptrs[i];
+    if (pageable || bytes[i] == 0 || pinned_throughout(ptrs[i], bytes[i])) continue;
+    ranges.push_back({(uintptr_t)ptrs[i] & ~(page - 1), ((uintptr_t)ptrs[i] + bytes[i] + page - 1) & ~(page - 1)});
+  }
+  std::sort(ranges.begin(), ranges.end());
+  std::vector<std::pair<uintptr_t, uintptr_t>> merged;
+  for (const auto& r : ranges) {
+    if (!merged.empty() && r.first <= merged.back().second) merged.back().second = std::max(merged.back().second, r.second);
+    else merged.push_back(r);
+  }
+  for (const auto& r : merged) {
+    void* base = reinterpret_cast<void*>(r.first);
+    cudaError_t e = cudaHostRegister(base, r.second - r.first, cudaHostRegisterMapped | cudaHostRegisterReadOnly);
+    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {
+      cudaGetLastError();
+      e = cudaHostRegister(base, r.second - r.first, cudaHostRegisterMapped);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    v.registered.push_back(base);
+  }
+  if (pageable) return cudaSuccess;
+  for (int i = 0; i < k; i++) {
+    if (bytes[i] == 0) continue;
+    void* dp = nullptr;
+    cudaError_t e = cudaHostGetDevicePointer(&dp, const_cast<void*>(ptrs[i]), 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
+    dptrs[i] = dp;
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
 louvain_status louvain_run_host(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* h_offsets,
                                 const int32_t* h_targets, const void* h_weights, louvain_wtype wtype,
                                 const louvain_params* p, void* stream, int32_t* h_membership, louvain_result* res,
@@ -1667,26 +1794,42 @@ louvain_status louvain_run_host(louvain_handle h, int64_t n, int64_t n_arcs, con
   if (s != LOUVAIN_OK) return s;
   if ((s = check_graph_args(h, n, n_arcs, h_offsets, h_targets, h_weights, wtype)) != LOUVAIN_OK) return s;
   if (n > 0 && !h_membership) return set_err(h, LOUVAIN_ERR_INVALID, "membership pointer is NULL");
+  if (!valid_params(p)) return set_err(h, LOUVAIN_ERR_INVALID, "invalid louvain_params");
+  // host_arcs: the arcs stay in host memory and are read in place; only the offsets are copied
+  const bool in_place = p->host_arcs != 0;
+  const int64_t a_in = in_place ? 0 : n_arcs;
   Workspace& ws = h->ws;
-  if (ws.in_n < n || ws.in_a < n_arcs) {
+  if (ws.in_n < n || ws.in_a < a_in || (in_place && ws.in_a > 0)) {
     free_all(ws.in_alloc);
     ws.in_n = ws.in_a = -1;
-    if (!dalloc(h, ws.in_alloc, &ws.in_offs, n + 1) || !dalloc(h, ws.in_alloc, &ws.in_tg, n_arcs) ||
-        !dalloc(h, ws.in_alloc, (int32_t**)&ws.in_w, n_arcs) || !dalloc(h, ws.in_alloc, &ws.in_mem, n)) {
+    if (!dalloc(h, ws.in_alloc, &ws.in_offs, n + 1) || !dalloc(h, ws.in_alloc, &ws.in_tg, a_in) ||
+        !dalloc(h, ws.in_alloc, (int32_t**)&ws.in_w, a_in) || !dalloc(h, ws.in_alloc, &ws.in_mem, n)) {
       free_all(ws.in_alloc);
       return set_err(h, LOUVAIN_ERR_OOM, "input staging allocation failed");
     }
     ws.in_n = n;
-    ws.in_a = n_arcs;
+    ws.in_a = a_in;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int32_t* d_tg = ws.in_tg;
+  const void* d_w = ws.in_w;
+  HostViews views;
   cudaMemcpyAsync(ws.in_offs, h_offsets, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
   if (n_arcs > 0) {
-    cudaMemcpyAsync(ws.in_tg, h_targets, (size_t)n_arcs * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(ws.in_w, h_weights, (size_t)n_arcs * 4, cudaMemcpyHostToDevice, st);
+    if (in_place) {
+      const void* hp[2] = {h_targets, h_weights};
+      const size_t hb[2] = {(size_t)n_arcs * sizeof(int32_t), (size_t)n_arcs * 4};
+      const void* dp[2] = {nullptr, nullptr};
+      cudaError_t e = host_views(views, h->device, hp, hb, 2, dp);
+      if (e != cudaSuccess) return cuda_err(h, e, "making the host arcs readable by the device");
+      d_tg = static_cast<const int32_t*>(dp[0]);
+      d_w = dp[1];
+    } else {
+      cudaMemcpyAsync(ws.in_tg, h_targets, (size_t)n_arcs * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(ws.in_w, h_weights, (size_t)n_arcs * 4, cudaMemcpyHostToDevice, st);
+    }
   }
-  s = louvain_run(h, n, n_arcs, ws.in_offs, ws.in_tg, ws.in_w, wtype, p, stream, ws.in_mem, res, stats, stats_cap,
-                  n_stats);
+  s = louvain_run(h, n, n_arcs, ws.in_offs, d_tg, d_w, wtype, p, stream, ws.in_mem, res, stats, stats_cap, n_stats);
   if (s != LOUVAIN_OK) return s;
   if (n > 0) cudaMemcpyAsync(h_membership, ws.in_mem, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);

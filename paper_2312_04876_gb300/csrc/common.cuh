@@ -305,6 +305,25 @@ __device__ __forceinline__ bool tbl_add(int32_t* keys, V* vals, unsigned size, i
   return false;
 }
 
+// tbl_add that also reports a new key: 0 = table full, 1 = added to an existing key, 2 = this call
+// claimed the key's slot (*slot = its index).
+template <class V>
+__device__ __forceinline__ int tbl_add_claim(int32_t* keys, V* vals, unsigned size, int shift, int32_t key, V w,
+                                             unsigned* slot) {
+  unsigned s = tbl_home(key, shift);
+  for (unsigned p = 0; p < size; p++) {
+    int32_t k = *((volatile int32_t*)&keys[s]);
+    if (k == key) { atomicAdd(&vals[s], w); return 1; }
+    if (k == kEmpty) {
+      int32_t old = atomicCAS(&keys[s], kEmpty, key);
+      if (old == kEmpty) { atomicAdd(&vals[s], w); *slot = s; return 2; }
+      if (old == key) { atomicAdd(&vals[s], w); return 1; }
+    }
+    s = (s + 1) & (size - 1);
+  }
+  return 0;
+}
+
 // Tables of {key, value} pairs (the giant-row pool): slot s is kv[2s] (key) and kv[2s + 1] (value
 // bits of an h_t, a uint32_t or float), so one 8-byte access reads or clears a slot; empty =
 // {kEmpty, 0}.

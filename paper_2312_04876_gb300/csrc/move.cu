@@ -76,8 +76,15 @@ __host__ __device__ constexpr int lm_block() {
   return (G == 32 && LOG >= 10) ? 64 : kBlock;
 }
 
+// Blocks per SM the register budget is set for: two-warp blocks are held to 12 per SM by their
+// 16 KB of tables and lists anyway, so they may use up to 85 registers a thread.
+template <int G, int LOG>
+__host__ __device__ constexpr int lm_min_blocks() {
+  return lm_block<G, LOG>() == 64 ? 12 : (G <= 32 ? 4 : 3);
+}
+
 template <class M, int G, int LOG>
-__global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M> a) {
+__global__ void __launch_bounds__(lm_block<G, LOG>(), (lm_min_blocks<G, LOG>())) lm_kernel(LmArgs<M> a) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
@@ -99,6 +106,13 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
   extern __shared__ __align__(16) unsigned char lm_dyn[];  // GPB tables of SL (key, value) slots
   int32_t* skeys = reinterpret_cast<int32_t*>(lm_dyn);
   H* svals = reinterpret_cast<H*>(lm_dyn + sizeof(int32_t) * GPB * SL);
+  // warp and block groups: the slots each vertex claimed, in claim order (a row has at most SL / 2
+  // distinct neighbouring communities, since tables hold at least twice the row's arcs), so the
+  // scoring visits and clears only occupied slots
+  constexpr bool kList = G >= 32;
+  constexpr int LMAX = kList ? SL / 2 : 1;
+  uint16_t* slist = reinterpret_cast<uint16_t*>(lm_dyn + (sizeof(int32_t) + sizeof(H)) * GPB * SL);
+  __shared__ int s_ncl;  // block groups: entries of the claimed-slot list
   // per-warp reduction scratch, sized by the block's warps: static shared memory counts against
   // the blocks an SM holds (13 instead of 11 two-warp blocks of 1024-slot tables)
   constexpr int NW = BS / 32;
@@ -113,9 +127,11 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
   const int gib = G <= 32 ? (int)(threadIdx.x / G) : 0;
   const unsigned lane = Grp<G>::lane();
   for (int t = threadIdx.x; t < GPB * SL; t += BS) { skeys[t] = kEmpty; svals[t] = H(0); }
+  if (threadIdx.x == 0) s_ncl = 0;
   __syncthreads();
   int32_t* tk = skeys + gib * SL;  // this group's table
   H* tv = svals + gib * SL;
+  uint16_t* cl = slist + gib * LMAX;  // this group's claimed-slot list
   const A two_m_all = M::is_fp ? (A)ctrl->two_m_f : (A)ctrl->two_m_i;
   GraphCtl* const gcs = a.st.gc;
   unsigned long long acc_lo = 0, acc_hi = 0, acc_mv = 0;
@@ -158,7 +174,10 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
     // independent memory requests in flight.
     H kid = H(0);
     bool ok = true;
-    for (int64_t e0 = beg + lane; e0 < end; e0 += (int64_t)G * U) {
+    unsigned ncl = 0;  // warp groups: entries of the claimed-slot list (uniform over the warp)
+    // every lane of a warp takes the same number of steps (the claim ballots need the whole warp)
+    for (int64_t b0 = beg; b0 < end; b0 += (int64_t)G * U) {
+      const int64_t e0 = b0 + lane;
       int32_t jj[U];
       H ww[U];
 #pragma unroll
@@ -172,9 +191,30 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
       for (int u = 0; u < U; u++) cc[u] = jj[u] != i ? a.st.Cp[jj[u]] : kEmpty;
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        if (jj[u] == i) continue;  // padding or i's self-loop
-        if (cc[u] == d) kid += ww[u];
-        else ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
+        const bool other = jj[u] != i && cc[u] != d;  // padding and i's self-loop are neither
+        if (jj[u] != i && cc[u] == d) kid += ww[u];
+        if constexpr (kList) {
+          // the new keys of this step are appended warp by warp to the claimed-slot list
+          int r = 1;
+          unsigned sl = 0;
+          if (other) r = tbl_add_claim(tk, tv, size, shift, cc[u], ww[u], &sl);
+          ok &= r != 0;
+          const unsigned b = __ballot_sync(0xffffffffu, r == 2);
+          if (b != 0u) {
+            unsigned base;
+            if constexpr (G == 32) {
+              base = ncl;
+              ncl += __popc(b);
+            } else {
+              unsigned t = 0;
+              if ((threadIdx.x & 31) == 0) t = (unsigned)atomicAdd(&s_ncl, __popc(b));
+              base = __shfl_sync(0xffffffffu, t, 0);
+            }
+            if (r == 2) cl[base + __popc(b & lanemask_lt())] = (uint16_t)sl;
+          }
+        } else if (other) {
+          ok &= tbl_add(tk, tv, size, shift, cc[u], ww[u]);
+        }
       }
     }
     if (!ok) atomicOr(&ctrl->error, kErrTableFull);
@@ -185,65 +225,67 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
     // U slots per lane are issued together.
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
-    // Warp and block groups: each warp compacts the occupied slots of its own segment of the table
-    // (size / warps slots) to the segment's front, in place (an entry only moves to a slot already
-    // read), then scores just those candidates, U per lane with their Sigma gathers issued
-    // together; the segment is left all-empty.  Sub-warp groups scan their small tables directly.
-    constexpr unsigned kStride = G >= 32 ? 32u : (unsigned)G;
-    unsigned scan_size = size;
-    int32_t* sk = tk;
-    H* sv = tv;
-    const unsigned slane = G >= 32 ? (threadIdx.x & 31u) : lane;
-    if constexpr (G >= 32) {
-      const unsigned seg = size / (unsigned)(G / 32);
-      const unsigned w = G == 32 ? 0u : (threadIdx.x >> 5);
-      sk = tk + w * seg;
-      sv = tv + w * seg;
-      unsigned ncand = 0;
-      for (unsigned s0 = 0; s0 < seg; s0 += 32) {
-        const unsigned s = s0 + slane;
-        const int32_t key = s < seg ? sk[s] : kEmpty;
-        const H val = key != kEmpty ? sv[s] : H(0);
-        __syncwarp();
-        if (key != kEmpty) { sk[s] = kEmpty; sv[s] = H(0); }
-        const unsigned ball = __ballot_sync(0xffffffffu, key != kEmpty);
-        __syncwarp();
-        if (key != kEmpty) {
-          const unsigned pos = ncand + __popc(ball & lanemask_lt());
-          sk[pos] = key;
-          sv[pos] = val;
-        }
-        ncand += __popc(ball);
-      }
-      __syncwarp();
-      scan_size = ncand;
-    }
-    for (unsigned s0 = slane; s0 < scan_size; s0 += kStride * U) {
-      int32_t ck[U];
-      H vv[U];
-      A sg[U];
+    // Warp and block groups score the slots listed at claim time (U per lane, their Sigma gathers
+    // issued together) and clear them, which leaves the table all-empty; sub-warp groups scan their
+    // small tables directly.
+    if constexpr (kList) {
+      const unsigned ncand = G == 32 ? ncl : (unsigned)*(volatile int*)&s_ncl;
+      for (unsigned k0 = lane; k0 < ncand; k0 += (unsigned)G * U) {
+        int32_t ck[U];
+        H vv[U];
+        A sg[U];
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        const unsigned s = s0 + (unsigned)u * kStride;
-        ck[u] = s < scan_size ? sk[s] : kEmpty;
-        vv[u] = H(0);
-        if (ck[u] != kEmpty) {
-          vv[u] = sv[s];
-          sk[s] = kEmpty;
-          sv[s] = H(0);
+        for (int u = 0; u < U; u++) {
+          const unsigned k = k0 + (unsigned)u * G;
+          ck[u] = kEmpty;
+          vv[u] = H(0);
+          if (k < ncand) {
+            const unsigned s = cl[k];
+            ck[u] = tk[s];
+            vv[u] = tv[s];
+            tk[s] = kEmpty;
+            tv[s] = H(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) sg[u] = ck[u] != kEmpty ? a.st.Sig[ck[u]] : A(0);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          if (ck[u] == kEmpty) continue;
+          ctr[3]++;
+          const S sc = M::score(vv[u], kid, ki, sg[u], sd, two_m);
+          if (better(sc, ck[u], best, bc)) { best = sc; bc = ck[u]; }
         }
       }
+    } else {
+      for (unsigned s0 = lane; s0 < size; s0 += (unsigned)G * U) {
+        int32_t ck[U];
+        H vv[U];
+        A sg[U];
 #pragma unroll
-      for (int u = 0; u < U; u++) sg[u] = ck[u] != kEmpty ? a.st.Sig[ck[u]] : A(0);
+        for (int u = 0; u < U; u++) {
+          const unsigned s = s0 + (unsigned)u * G;
+          ck[u] = s < size ? tk[s] : kEmpty;
+          vv[u] = H(0);
+          if (ck[u] != kEmpty) {
+            vv[u] = tv[s];
+            tk[s] = kEmpty;
+            tv[s] = H(0);
+          }
+        }
 #pragma unroll
-      for (int u = 0; u < U; u++) {
-        if (ck[u] == kEmpty) continue;
-        ctr[3]++;
-        const S sc = M::score(vv[u], kid, ki, sg[u], sd, two_m);
-        if (better(sc, ck[u], best, bc)) { best = sc; bc = ck[u]; }
+        for (int u = 0; u < U; u++) sg[u] = ck[u] != kEmpty ? a.st.Sig[ck[u]] : A(0);
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          if (ck[u] == kEmpty) continue;
+          ctr[3]++;
+          const S sc = M::score(vv[u], kid, ki, sg[u], sd, two_m);
+          if (better(sc, ck[u], best, bc)) { best = sc; bc = ck[u]; }
+        }
       }
     }
     group_argmax<G>(best, bc, red_s, red_c);
+    if (G > 32 && threadIdx.x == 0) s_ncl = 0;  // every thread read it before group_argmax's barriers
     Grp<G>::sync();
 
     int mv = (bc != 0x7fffffff && best > S(0)) ? 1 : 0;
@@ -300,7 +342,7 @@ __global__ void __launch_bounds__(kBlock, (G <= 32 ? 4 : 3)) lm_kernel(LmArgs<M>
 template <class M, int G, int LOG>
 static constexpr size_t lm_smem() {
   return (size_t)(G <= 32 ? lm_block<G, LOG>() / G : 1) * (1 << LOG) *
-         (sizeof(int32_t) + sizeof(typename M::h_t));
+         (sizeof(int32_t) + sizeof(typename M::h_t) + (G >= 32 ? sizeof(uint16_t) / 2 : 0));
 }
 
 // Opts a kernel into more than 48 KB of dynamic shared memory, once per device (outside any graph

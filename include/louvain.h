@@ -105,6 +105,11 @@ typedef struct {
                                     (registering them for the call unless already pinned) and copies
                                     only the offsets; per-vertex state stays in HBM.  Results are
                                     those of the default placement (0) */
+  int32_t table_factor;          /* hash-table slots per key a table may have to hold: 1, 2 or 4
+                                    (tables up to full, half full or a quarter full; 0 = 2), for the
+                                    shared-memory tables of local moving and merging and the giant
+                                    rows' global tables.  Integer-weight results do not depend on it
+                                    (exact sums, ties by id); it trades probe length for memory */
 } louvain_params;
 
 typedef struct {
@@ -144,8 +149,8 @@ void louvain_destroy(louvain_handle h);
 /* Defaults from Section 4.1: max_iterations 20, tolerance 0.01, tolerance_drop 10,
  * aggregation_tolerance 0.8, pruning on; max_passes 10; deterministic mode; seed 0;
  * validate 1; compact 1; pass_modularity 0; profile 0; fast_classes 16; fast_classes_later 1;
- * fast_giant_class, lm_blocks_per_sm, giant_min_degree, wait_spins and host_arcs 0 (their built-in
- * choices). */
+ * fast_giant_class, lm_blocks_per_sm, giant_min_degree, wait_spins, host_arcs and table_factor 0
+ * (their built-in choices). */
 louvain_status louvain_default_params(louvain_params* p);
 
 /* Algorithm 1 as louvain_run, but the first pass starts from the membership d_initial[n] (device,

@@ -15,7 +15,8 @@ Settings, each changing one control of the defaults:
 * initial tolerance: 0.01 against 1e-6 and 0.1;
 * aggregation tolerance: 0.8 against 1 (never stops early) and 0.6;
 * vertex pruning: on against off;
-* super-vertex graph: compacted against holey.
+* super-vertex graph: compacted against holey;
+* hash-table sizing: 2 slots per key against 1 and 4 (table_factor).
 
 Timing and aggregation:
 
@@ -41,6 +42,7 @@ ALTERNATIVES = [
     ("aggregation_tolerance", 1.0), ("aggregation_tolerance", 0.6),
     ("pruning", 0),
     ("compact", 0),
+    ("table_factor", 1), ("table_factor", 4),
 ]
 
 WORKLOADS = {

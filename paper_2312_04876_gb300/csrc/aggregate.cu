@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) merge_kernel(MergeArgs<M> a, const int
     const int64_t m0 = a.coff[c], m1 = a.coff[c + 1];
     if (lane == 0) { ctr[0]++; ctr[1] += (unsigned long long)(m1 - m0); }
     const int64_t D = a.cdeg[c];
-    const int lg = tbl_log2(D, 1, LOG);
+    const int lg = tbl_log2f(D, a.tf, 1, LOG);
     const unsigned size = 1u << lg;
     const int shift = 32 - lg;
     bool ok;

@@ -480,6 +480,7 @@ bool valid_params(const louvain_params* p) {
          p->lm_blocks_per_sm >= 0 && p->lm_blocks_per_sm <= 64 && p->fast_classes_later >= 0 &&
          (p->giant_min_degree == 0 || (p->giant_min_degree >= 2048 && p->giant_min_degree <= 4096)) &&
          p->wait_spins >= 0 && (p->host_arcs == 0 || p->host_arcs == 1) &&
+         (p->table_factor == 0 || p->table_factor == 1 || p->table_factor == 2 || p->table_factor == 4) &&
          (p->mode == LOUVAIN_MODE_DETERMINISTIC || p->mode == LOUVAIN_MODE_FAST);
 }
 
@@ -1010,6 +1011,7 @@ louvain_status aggregate_phase(louvain_handle h, Ctx& c, const GraphView<typenam
   MergeArgs<M> a;
   a.g = g; a.Cp = ws.Cp; a.coff = ws.coff; a.cverts = ws.cverts; a.cdeg = ws.cdeg; a.hoff = rs.hoff; a.hend = rs.hend;
   a.otg = otg_holey; a.ow = ow_holey; a.nc = nc; a.ctrl = ws.ctrl;
+  a.tf = c.table_factor;
   for (int b = 0; b < kNumBuckets; b++) {
     if (cb[b + 1] - cb[b] <= 0) continue;
     const int pm = prof_begin(h, c);
@@ -1496,6 +1498,7 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
   c.num_sms = h->num_sms;
   if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
   if (p) c.wait_spins = p->wait_spins;
+  if (p && p->table_factor > 0) c.table_factor = p->table_factor;
   h->prof.on = p->profile != 0;
   h->arcs_host = p->host_arcs != 0;
   h->prof.used = 0;
@@ -1589,6 +1592,7 @@ louvain_status run_entry(louvain_handle h, int64_t n, int64_t n_arcs, const int6
   c.num_sms = h->num_sms;
   if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
   if (p) c.wait_spins = p->wait_spins;
+  if (p && p->table_factor > 0) c.table_factor = p->table_factor;
   if (res) std::memset(res, 0, sizeof(*res));
   if (n_stats) *n_stats = 0;
   h->prof.on = p->profile != 0;
@@ -1926,6 +1930,7 @@ louvain_status louvain_local_move(louvain_handle h, int64_t n, int64_t n_arcs, c
   c.num_sms = h->num_sms;
   if (p && p->giant_min_degree > 0) c.giant_min = p->giant_min_degree;
   if (p) c.wait_spins = p->wait_spins;
+  if (p && p->table_factor > 0) c.table_factor = p->table_factor;
   if ((s = ensure_workspace(h, n, n_arcs)) != LOUVAIN_OK) return s;
   if ((s = ensure_pinned(h, 65536)) != LOUVAIN_OK) return s;
   const bool fp = wtype == LOUVAIN_W_FP32;

@@ -349,6 +349,14 @@ __host__ __device__ __forceinline__ int tbl_log2(int64_t distinct_bound, int min
   return l;
 }
 
+// The same with f table slots per key of the bound (f = 1, 2 or 4: tables up to full, half full or
+// a quarter full); tbl_log2 is f = 2.
+__host__ __device__ __forceinline__ int tbl_log2f(int64_t distinct_bound, int f, int min_log2, int max_log2) {
+  int l = min_log2;
+  while (l < max_log2 && ((int64_t)1 << l) < (int64_t)f * distinct_bound) l++;
+  return l;
+}
+
 // Warp-level (or sub-warp) lane mask of the lanes below this one within the warp.
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned r;

@@ -40,13 +40,13 @@ constexpr int kLocLog = 12;     // shared pre-aggregation table: 4096 slots >= 2
 // kind 3: chunks only, every listed row.
 __global__ void k_gplan_counts(int kind, const int32_t* list, int64_t m, const int64_t* rbeg, const int64_t* rend,
                                const int64_t* cdeg, int64_t n_bound, const int32_t* Cp, int32_t* gix, int slice_log,
-                               GiantPlan p) {
+                               GiantPlan p, int tf) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = list[k];
     int64_t nch = 0, ts = 0;
     if (kind == 1) {
       const int64_t bound = cdeg[v] < n_bound ? cdeg[v] : n_bound;
-      ts = (int64_t)1 << tbl_log2(bound, 6, 31);
+      ts = (int64_t)1 << tbl_log2f(bound, tf, 6, 31);
       nch = (cdeg[v] + kChunk - 1) / kChunk;
       gix[v] = (int32_t)k;
     } else {
@@ -55,7 +55,7 @@ __global__ void k_gplan_counts(int kind, const int32_t* list, int64_t m, const i
       if (used) {
         const int64_t ch = kind == 0 ? kLmChunk : kChunk;
         nch = (deg + ch - 1) / ch;
-        if (kind == 0) ts = (int64_t)1 << tbl_log2(deg < n_bound ? deg : n_bound, 6, 31);
+        if (kind == 0) ts = (int64_t)1 << tbl_log2f(deg < n_bound ? deg : n_bound, tf, 6, 31);
       }
     }
     p.chunk_off[k] = nch;
@@ -125,7 +125,7 @@ void giant_plan(Ctx& c, int kind, const int32_t* list, int64_t m, const int64_t*
                 const GiantPlan& p, Ctrl* ctrl) {
   const int cap = c.num_sms * 8;
   k_gplan_counts<<<grid_for(m, kBlock, cap), kBlock, 0, c.s>>>(kind, list, m, rbeg, rend, cdeg, n_bound, Cp, gix,
-                                                              slice_log, p);
+                                                              slice_log, p, c.table_factor);
   k_gplan_scan<<<1, 1024, 0, c.s>>>(m, p, ctrl);
   k_gplan_owners<<<cap, kBlock, 0, c.s>>>(m, p);
   c.launches += 3;

@@ -16,6 +16,7 @@ struct Ctx {
   int lm_blocks_per_sm = 16;  // grid cap of the local-moving kernels (blocks per SM)
   int64_t giant_min = 4096;   // rows longer than this take the giant path (2048..4096)
   long long wait_spins = 0;   // polls of a bounded device wait before it gives up (0 = built-in)
+  int table_factor = 2;       // hash-table slots per key of a table's distinct-key bound (1, 2, 4)
 };
 
 inline int grid_for(int64_t work_items, int items_per_block, int cap) {
@@ -66,6 +67,7 @@ struct KeyDesc {
   Segs seg;  // kind 3 hashes the graph-local id
   int giant_class = -1;  // kind 3: >= 0 puts every giant row in this class
   int64_t giant_min = 4096;  // rows longer than this are giant (set by bucket_sort from the Ctx)
+  int table_factor = 2;      // giant-table slots per key bound (set by bucket_sort from the Ctx)
 };
 
 // Counting sort of vertex ids by key.  key_kind 0: degree bucket of (rend - rbeg); 1: colour *
@@ -182,6 +184,7 @@ struct MergeArgs {
   int64_t nc;
   Ctrl* ctrl;
   int bucket = 0;  // set by merge_bucket (selects the traffic counters)
+  int tf = 2;      // table slots per key of the distinct-key bound
 };
 template <class M>
 void merge_bucket(Ctx& c, int bucket, const MergeArgs<M>& a, const int32_t* list, int64_t count);

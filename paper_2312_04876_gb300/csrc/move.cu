@@ -29,6 +29,7 @@ struct LmArgs {
   int pruning;
   int bucket;
   const int64_t* rng;  // device {start, count} of the list (a captured iteration), or null
+  int tf;              // table slots per key of the row's distinct-key bound
 };
 
 // Block-wide reduction of the per-thread move accumulators into the control block.
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(lm_block<G, LOG>(), (lm_min_blocks<G, LOG>()))
     // deterministic schedule Sigma does not change during a class; the fast schedule reads live values)
     const A ki = a.st.K[i];
     const A sd = a.st.Sig[d];
-    const int lg = tbl_log2(deg, 1, LOG);
+    const int lg = tbl_log2f(deg, a.tf, 1, LOG);
     const unsigned size = 1u << lg;
     const int shift = 32 - lg;
 
@@ -389,6 +390,7 @@ void move_bucket(Ctx& c, int bucket, const GraphView<typename M::w_t>& g, const 
   a.fast = fast ? 1 : 0;
   a.pruning = pruning ? 1 : 0;
   a.bucket = bucket < kNumBuckets ? bucket : kNumBuckets - 1;
+  a.tf = c.table_factor;
   const int cap = c.num_sms * c.lm_blocks_per_sm;
   switch (bucket) {
     case 0: launch_lm<M, 4, 3>(c, a, cap); break;

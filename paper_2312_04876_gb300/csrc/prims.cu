@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_key_hist(KeyDesc kind, int64_t n, co
     const long long dg = kind.kind == 2 ? deg64[i] : rend[i] - rbeg[i];
     mx = dg > mx ? dg : mx;
     if (giant_slots && bucket_of(dg, kind.giant_min) == kNumBuckets - 1)
-      gs += 1ULL << tbl_log2(dg < n_bound ? dg : n_bound, 6, 31);
+      gs += 1ULL << tbl_log2f(dg < n_bound ? dg : n_bound, kind.table_factor, 6, 31);
     int k = sort_key(kind, i, rbeg, rend, colour, deg64);
     if (k < 0) continue;
     if (local) atomicAdd(&sh[k], 1);
@@ -241,6 +241,7 @@ void bucket_sort(Ctx& c, KeyDesc key_kind, int64_t n, const int64_t* rbeg, const
                  int64_t* tile_tmp, unsigned long long* max_deg, unsigned long long* giant_slots,
                  int64_t n_bound) {
   key_kind.giant_min = c.giant_min;
+  key_kind.table_factor = c.table_factor;
   cudaMemsetAsync(offsets, 0, (size_t)(nkeys + 1) * sizeof(int64_t), c.s);
   cudaMemsetAsync(cursor, 0, (size_t)nkeys * sizeof(int32_t), c.s);
   if (n <= 0) return;

@@ -378,3 +378,15 @@ def test_hbm_budget_reports_oom(cuda_ok):
     h = lv.Louvain(0, hbm_budget_bytes=1 << 16)
     assert _status(h, lambda: h.run(*dev(g))) == 2
     h.close()
+
+
+@pytest.mark.parametrize("tf", [1, 4])
+@pytest.mark.parametrize("name", ["rmat16", "star20k", "sbm2k"])
+def test_table_factor_is_exact(L, name, tf):
+    """Table sizing (1 or 4 slots per key instead of 2) changes probe lengths, not results: the
+    integer-mode run still reproduces the oracle bit for bit, giant rows and merges included."""
+    g = GRAPHS[name]()
+    o, t, w = dev(g)
+    mem, res = L.run(o, t, w, mode="deterministic", table_factor=tf, seed=5)
+    ref_mem, ref_q, _, _ = oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params(seed=5))
+    assert np.array_equal(mem.cpu().numpy(), ref_mem) and res.modularity == ref_q

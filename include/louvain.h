@@ -110,6 +110,12 @@ typedef struct {
                                     shared-memory tables of local moving and merging and the giant
                                     rows' global tables.  Integer-weight results do not depend on it
                                     (exact sums, ties by id); it trades probe length for memory */
+  int32_t fast_sync_small;       /* fast mode on small graphs: 0 = where the graph -- a batch: its mean
+                                    graph -- fits in what the GPU holds in flight (1024 vertices per
+                                    SM), run the colour-synchronous schedule of the deterministic mode
+                                    (each class is one wave there anyway; asynchronous waves left 2-3%
+                                    of small graphs 0.03-0.066 below it); 1 = asynchronous random
+                                    classes always; 2 = colour-synchronous always */
 } louvain_params;
 
 typedef struct {

@@ -21,7 +21,8 @@ class Params(ctypes.Structure):
                 ("fast_classes", ctypes.c_int32), ("fast_giant_class", ctypes.c_int32),
                 ("lm_blocks_per_sm", ctypes.c_int32), ("giant_min_degree", ctypes.c_int32),
                 ("fast_classes_later", ctypes.c_int32), ("wait_spins", ctypes.c_int32),
-                ("host_arcs", ctypes.c_int32), ("table_factor", ctypes.c_int32)]
+                ("host_arcs", ctypes.c_int32), ("table_factor", ctypes.c_int32),
+                ("fast_sync_small", ctypes.c_int32)]
 
 
 class PassStats(ctypes.Structure):

@@ -357,6 +357,13 @@ __host__ __device__ __forceinline__ int tbl_log2f(int64_t distinct_bound, int f,
   return l;
 }
 
+// tbl_log2f by counting leading zeros (device code; f * bound below 2^31).
+__device__ __forceinline__ int tbl_log2f_fast(int64_t distinct_bound, int f, int min_log2, int max_log2) {
+  const unsigned need = (unsigned)f * (unsigned)distinct_bound;  // slots wanted
+  const int l = need <= 1u ? 0 : 32 - __clz(need - 1u);           // smallest l with 2^l >= need
+  return l < min_log2 ? min_log2 : (l > max_log2 ? max_log2 : l);
+}
+
 // Warp-level (or sub-warp) lane mask of the lanes below this one within the warp.
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned r;

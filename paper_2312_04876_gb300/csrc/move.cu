@@ -14,6 +14,7 @@
 // sum of the performed N is accumulated exactly (128-bit) and move_finish applies the
 // per-iteration tolerance test of Algorithm 2 on the device, so iterations need no host sync.
 #include <atomic>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(lm_block<G, LOG>(), (lm_min_blocks<G, LOG>()))
     // deterministic schedule Sigma does not change during a class; the fast schedule reads live values)
     const A ki = a.st.K[i];
     const A sd = a.st.Sig[d];
-    const int lg = tbl_log2f(deg, a.tf, 1, LOG);
+    const int lg = G > 32 ? tbl_log2f(deg, a.tf, 1, LOG) : tbl_log2f_fast(deg, a.tf, 1, LOG);
     const unsigned size = 1u << lg;
     const int shift = 32 - lg;
 
@@ -177,15 +178,22 @@ __global__ void __launch_bounds__(lm_block<G, LOG>(), (lm_min_blocks<G, LOG>()))
     bool ok = true;
     unsigned ncl = 0;  // warp groups: entries of the claimed-slot list (uniform over the warp)
     // every lane of a warp takes the same number of steps (the claim ballots need the whole warp)
-    for (int64_t b0 = beg; b0 < end; b0 += (int64_t)G * U) {
-      const int64_t e0 = b0 + lane;
+    // Warp and sub-warp groups index a row's arcs from its start in 32 bits (a row holds fewer than
+    // 2^31 arcs; fewer instructions per arc); the one-block kernels keep absolute 64-bit indices,
+    // which measured faster there.
+    typedef typename std::conditional<(G > 32), int64_t, int32_t>::type X;
+    const int32_t* const rtg = G > 32 ? g.tg : g.tg + beg;
+    const typename M::w_t* const rw = G > 32 ? g.w : g.w + beg;
+    const X rlo = G > 32 ? (X)beg : X(0), rhi = G > 32 ? (X)end : (X)deg;
+    for (X b0 = rlo; b0 < rhi; b0 += (X)(G * U)) {
+      const X e0 = b0 + (X)lane;
       int32_t jj[U];
       H ww[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {
-        const int64_t e = e0 + (int64_t)u * G;
-        jj[u] = e < end ? g.tg[e] : i;
-        ww[u] = e < end ? (H)g.w[e] : H(0);
+        const X e = e0 + (X)(u * G);
+        jj[u] = e < rhi ? rtg[e] : i;
+        ww[u] = e < rhi ? (H)rw[e] : H(0);
       }
       int32_t cc[U];
 #pragma unroll
@@ -323,12 +331,12 @@ __global__ void __launch_bounds__(lm_block<G, LOG>(), (lm_min_blocks<G, LOG>()))
         ctr[4]++;
       }
       if (a.pruning)
-        for (int64_t e0 = beg + lane; e0 < end; e0 += (int64_t)G * U) {
+        for (X e0 = rlo + (X)lane; e0 < rhi; e0 += (X)(G * U)) {
           int32_t jj[U];
 #pragma unroll
           for (int u = 0; u < U; u++) {
-            const int64_t e = e0 + (int64_t)u * G;
-            jj[u] = e < end ? g.tg[e] : i;
+            const X e = e0 + (X)(u * G);
+            jj[u] = e < rhi ? rtg[e] : i;
           }
 #pragma unroll
           for (int u = 0; u < U; u++)

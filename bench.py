@@ -816,6 +816,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "n": g.n, "arcs": g.n_arcs, "mode": args.mode,
                    "knobs": {"giant_min_degree": params.giant_min_degree, "lm_blocks_per_sm": params.lm_blocks_per_sm,
+                             "table_factor": params.table_factor or 2,
                              "compact": params.compact, "fast_classes": params.fast_classes,
                              "fast_classes_later": params.fast_classes_later,
                              "autotuned": tuned_ms is not None},

@@ -256,9 +256,10 @@ louvain_status louvain_run_batch(louvain_handle h, int32_t n_graphs, const int64
  * iteration graphs and buffers) under every combination of the performance knobs that
  * leave the arithmetic unchanged -- giant_min_degree in {4096, 2048} (which kernel takes rows of
  * 2049..4096 arcs: the one-block 64 KB table or the multi-block giant path), lm_blocks_per_sm in
- * {16, 4} and compact in {1, 0} -- and writes *p with the fastest combination into *tuned (other
- * fields copied; *best_ms its time).  In deterministic mode every candidate returns the same
- * membership; d_membership (device, n entries) receives the last run's.  Costs 8 x (reps + 1) runs. */
+ * {16, 4} and compact in {1, 0}; then table_factor 4 against 2 (hash-table sizes) with the best of
+ * those -- and writes *p with the fastest setting into *tuned (other fields copied; *best_ms its
+ * time).  In deterministic mode every candidate returns the same
+ * membership; d_membership (device, n entries) receives the last run's.  Costs 9 x (reps + 1) runs. */
 louvain_status louvain_autotune(louvain_handle h, int64_t n, int64_t n_arcs, const int64_t* d_offsets,
                                 const int32_t* d_targets, const void* d_weights, louvain_wtype wtype,
                                 const louvain_params* p, void* stream, int32_t* d_membership, int32_t reps,

@@ -1311,8 +1311,9 @@ louvain_status check_graph_args(louvain_handle h, int64_t n, int64_t n_arcs, con
 // ------------------------------------------------------------------ autotuning
 // Candidates of the performance knobs that leave the arithmetic unchanged: the giant-row
 // threshold (which kernel takes rows of 2049..4096 arcs), the local-move grid cap and super-graph
-// compaction.  Each is timed by full runs (device time, best of `reps`) after one untimed run that
-// builds its iteration graphs and buffers, as a run in steady use finds them; the fastest wins.
+// compaction (every combination), then the hash-table sizing (4 slots per key instead of 2) with
+// the best of those.  Each is timed by full runs (device time, best of `reps`) after one untimed run
+// that builds its iteration graphs and buffers, as a run in steady use finds them; the fastest wins.
 template <class RunFn>
 static louvain_status autotune_impl(louvain_handle h, const louvain_params* p, int32_t reps, RunFn run,
                                     louvain_params* tuned, float* best_ms) {
@@ -1321,6 +1322,21 @@ static louvain_status autotune_impl(louvain_handle h, const louvain_params* p, i
   static const int32_t kCompact[] = {1, 0};
   louvain_params best = *p;
   float best_t = -1.f;
+  auto trial = [&](const louvain_params& q) -> louvain_status {
+    float t = -1.f;
+    float warm = 0.f;
+    louvain_status s0 = run(q, &warm);
+    if (s0 != LOUVAIN_OK) return s0;
+    for (int32_t r = 0; r < (reps > 0 ? reps : 1); r++) {
+      float ms = 0.f;
+      louvain_status s = run(q, &ms);
+      if (s != LOUVAIN_OK) return s;
+      if (t < 0.f || ms < t) t = ms;
+    }
+    if (best_t < 0.f || t < best_t) { best_t = t; best = q; }
+    return LOUVAIN_OK;
+  };
+  louvain_status s;
   for (int32_t gm : kGiant)
     for (int32_t gr : kGrid)
       for (int32_t cp : kCompact) {
@@ -1328,19 +1344,13 @@ static louvain_status autotune_impl(louvain_handle h, const louvain_params* p, i
         q.giant_min_degree = gm;
         q.lm_blocks_per_sm = gr;
         q.compact = cp;
+        q.table_factor = 2;
         q.profile = 0;
-        float t = -1.f;
-        float warm = 0.f;
-        louvain_status s0 = run(q, &warm);
-        if (s0 != LOUVAIN_OK) return s0;
-        for (int32_t r = 0; r < (reps > 0 ? reps : 1); r++) {
-          float ms = 0.f;
-          louvain_status s = run(q, &ms);
-          if (s != LOUVAIN_OK) return s;
-          if (t < 0.f || ms < t) t = ms;
-        }
-        if (best_t < 0.f || t < best_t) { best_t = t; best = q; }
+        if ((s = trial(q)) != LOUVAIN_OK) return s;
       }
+  louvain_params q4 = best;
+  q4.table_factor = 4;
+  if ((s = trial(q4)) != LOUVAIN_OK) return s;
   best.profile = p->profile;
   *tuned = best;
   if (best_ms) *best_ms = best_t;

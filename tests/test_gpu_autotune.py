@@ -32,6 +32,7 @@ def test_autotune_keeps_the_result(L):
     tuned, ms = L.autotune(o, t, w, mode="deterministic", reps=1)
     assert ms > 0.0
     assert tuned.giant_min_degree in (2048, 4096) and tuned.lm_blocks_per_sm in (4, 16) and tuned.compact in (0, 1)
+    assert tuned.table_factor in (2, 4)
     m0, r0 = L.run(o, t, w, mode="deterministic")
     m1, r1 = L.run(o, t, w, params=tuned)
     assert torch.equal(m0, m1) and r0.modularity == r1.modularity

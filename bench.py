@@ -145,9 +145,10 @@ def peaks():
         return PEAKS_FALLBACK["hbm_gbs"], "fallback"
 
 
-def stored_traffic(workload: str, mode: str, kernel: str):
+def stored_traffic(workload: str, mode: str, kernel: str, params=None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary of this workload, or None
-    when there is none or the kernels changed since it was captured."""
+    when there is none, the kernels changed since it was captured, or the run's knobs differ from
+    the capture's."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}_{mode}.json")
     try:
         with open(path) as f:
@@ -157,6 +158,11 @@ def stored_traffic(workload: str, mode: str, kernel: str):
     from paper_2312_04876_gb300.sources import source_sha256
     if t.get("source_sha256") != source_sha256():
         return None
+    if params is not None:
+        for k, v in t.get("knobs", {}).items():
+            have = getattr(params, k, None) or (2 if k == "table_factor" else 0)  # 0 = the built-in choice
+            if have != v:
+                return None
     c = t.get("classes", {}).get(kernel)
     return None if c is None else c.get("dram_bytes_per_launch")
 
@@ -277,7 +283,7 @@ def kernel_roofline(L, offs, tg, w, params, mem, steps: int, workload: str, mode
             "peak_kind": peak_kind}
     if dom:
         a = agg[dom["name"]]
-        roof["traffic"] = stored_traffic(workload, mode, dom["name"])
+        roof["traffic"] = stored_traffic(workload, mode, dom["name"], params)
         roof.update({"kernel": dom["name"], "achieved": dom["gbs"], "frac": dom["gbs"] / peak,
                      "algorithmic_bytes_per_launch": a["bytes"] / max(1, a["launches"]),
                      "avg_launch_ms": a["ms"] / max(1, a["launches"])})

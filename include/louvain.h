@@ -112,10 +112,12 @@ typedef struct {
                                     (exact sums, ties by id); it trades probe length for memory */
   int32_t fast_sync_small;       /* fast mode on small graphs: 0 = where the graph -- a batch: its mean
                                     graph -- fits in what the GPU holds in flight (1024 vertices per
-                                    SM), run the colour-synchronous schedule of the deterministic mode
-                                    (each class is one wave there anyway; asynchronous waves left 2-3%
-                                    of small graphs 0.03-0.066 below it); 1 = asynchronous random
-                                    classes always; 2 = colour-synchronous always */
+                                    SM) and rows over 512 arcs hold at most a fifth of its arcs, run
+                                    the colour-synchronous schedule of the deterministic mode (each
+                                    class is one wave there anyway; asynchronous waves left 2-3% of
+                                    small planted-partition graphs 0.03-0.066 below it; a graph
+                                    carried by hubs needs hundreds of colours); 1 = asynchronous
+                                    random classes always; 2 = colour-synchronous always */
 } louvain_params;
 
 typedef struct {

@@ -800,15 +800,23 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   Segs seg;
   seg.vg = vg;
   seg.gc = gc;
-  // Fast mode on a graph that the GPU holds in flight (a batch: its mean graph) runs the
-  // colour-synchronous schedule: there every class is one wave either way, and asynchronous waves
-  // left 2-3% of small graphs 0.03-0.066 below the oracle (random classes and colour classes alike)
+  // Fast mode on a graph that the GPU holds in flight (a batch: its mean graph) and whose rows over
+  // 512 arcs hold at most a fifth of its arcs runs the colour-synchronous schedule: there every
+  // class is one wave either way, and asynchronous waves left 2-3% of small planted-partition graphs
+  // 0.03-0.066 below the oracle (random classes and colour classes alike).  A graph carried by hubs
+  // needs hundreds of colours (a class step each; R-MAT scale 17: ~300), and asynchronous waves
+  // hold the bar there.
   const int64_t n_eff = gc && n_graphs > 0 ? g.n / n_graphs : g.n;
   const int64_t window = (int64_t)c.num_sms * kInFlightPerSm;
-  const bool det = p.mode == LOUVAIN_MODE_DETERMINISTIC || p.fast_sync_small == 2 ||
-                   (p.fast_sync_small == 0 && n_eff <= window);
-  if (p.lm_blocks_per_sm > 0) c.lm_blocks_per_sm = p.lm_blocks_per_sm;
   louvain_status s;
+  bool det = p.mode == LOUVAIN_MODE_DETERMINISTIC || p.fast_sync_small == 2;
+  if (!det && p.fast_sync_small == 0 && n_eff <= window) {
+    hub_share(c, g, ws.ctrl);
+    const Ctrl* hs = read_ctrl(h, c, &s, "hub share");
+    if (!hs) return s;
+    det = hs->hub_arcs * 5 <= hs->all_arcs;
+  }
+  if (p.lm_blocks_per_sm > 0) c.lm_blocks_per_sm = p.lm_blocks_per_sm;
   std::vector<int64_t> ho;  // bucket-sort offsets: colour-major (deterministic) or bucket-major (fast)
   int32_t ncol = 1;
   if (det) {

@@ -53,6 +53,7 @@ struct Ctrl {
   unsigned long long lm_stat[kNumBuckets][6];  // local move: list entries, vertices processed, arcs
                                                 // scanned, candidates scored, moves, neighbour marks
   unsigned long long mg_stat[kNumBuckets][4];  // merge: communities, members, arcs scanned, arcs written
+  unsigned long long hub_arcs, all_arcs;        // arcs in rows over 512 arcs, all arcs (hub_share)
 };
 
 // Adds K per-thread counters of a whole block to dst[0..K) (one atomic per counter per block).

@@ -107,6 +107,10 @@ struct PassState {
   const int32_t* vg = nullptr; // batched run: graph of each vertex
 };
 
+// ctrl->hub_arcs / all_arcs = arcs in rows over 512 arcs / all arcs of g (zeroed first).
+template <class W>
+void hub_share(Ctx& c, const GraphView<W>& g, Ctrl* ctrl);
+
 // Per-pass vertex state: Cp = id, flags = 1, csize = 1, mv_to = -1; Sig = K if from_k else 0 with K = 0.
 template <class M>
 void vertex_init(Ctx& c, const PassState<M>& st, int64_t n, bool from_k);

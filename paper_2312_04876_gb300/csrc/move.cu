@@ -484,6 +484,34 @@ void move_setup(Ctx& c, Ctrl* ctrl, double tau, int max_iterations) {
   c.launches++;
 }
 
+// ---------------------------------------------------------------- share of the arcs in hub rows
+__global__ void k_hub_share(const int64_t* rbeg, const int64_t* rend, int64_t n, Ctrl* ctrl) {
+  unsigned long long hub = 0, all = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long d = (unsigned long long)(rend[i] - rbeg[i]);
+    all += d;
+    if (d > 512) hub += d;
+  }
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    hub += __shfl_xor_sync(0xffffffffu, hub, o);
+    all += __shfl_xor_sync(0xffffffffu, all, o);
+  }
+  if ((threadIdx.x & 31) == 0 && all) {
+    atomicAdd(&ctrl->hub_arcs, hub);
+    atomicAdd(&ctrl->all_arcs, all);
+  }
+}
+template <class W>
+void hub_share(Ctx& c, const GraphView<W>& g, Ctrl* ctrl) {
+  cudaMemsetAsync(&ctrl->hub_arcs, 0, 2 * sizeof(unsigned long long), c.s);
+  if (g.n <= 0) return;
+  k_hub_share<<<grid_for(g.n, kBlock, c.num_sms * 8), kBlock, 0, c.s>>>(g.rbeg, g.rend, g.n, ctrl);
+  c.launches++;
+}
+template void hub_share<int32_t>(Ctx&, const GraphView<int32_t>&, Ctrl*);
+template void hub_share<float>(Ctx&, const GraphView<float>&, Ctrl*);
+
 // ---------------------------------------------------------------- per-pass vertex state
 template <class M>
 __global__ void k_vertex_init(PassState<M> st, int64_t n, int from_k) {

@@ -277,9 +277,12 @@ louvain_status louvain_autotune_batch(louvain_handle h, int32_t n_graphs, const 
 /* ---------------------------------------------------------------------------------------------
  * Serving: a continuous-batching request loop (a throughput extension; the paper has no
  * counterpart).  Requests are host CSRs (int64 offsets, graph-local int32 targets, weights).
- * `lanes` worker threads, each with its own CUDA stream and workspace, take every queued request
- * that fits (at most max_batch_graphs graphs and max_batch_arcs arcs per batch, 0 = no arc cap)
- * whenever they are free and run them as one louvain_run_batch call, so requests arriving while
+ * `lanes` worker threads, each with its own CUDA stream and workspace, take the oldest queued
+ * request and every other queued request of its class that fits (at most max_batch_graphs graphs
+ * and max_batch_arcs arcs per batch, 0 = no arc cap) whenever they are free and run them as one
+ * louvain_run_batch call.  A class is a weight type and a side of the in-flight window (1024
+ * vertices per SM): fast mode picks a batch's schedule by its mean graph, and a small graph batched
+ * with a large one would take the large one's.  So requests arriving while
  * others run are admitted as lanes and memory free up, and the lanes' work overlaps on the device.
  * Device memory: every batch reserves an upper bound of what it needs (256 B per vertex + 72 B
  * per arc + 64 MiB) and the reservations of all lanes never exceed hbm_budget_bytes; each result

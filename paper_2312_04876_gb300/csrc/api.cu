@@ -553,8 +553,6 @@ louvain_status degree_buckets(louvain_handle h, Ctx& c, const GraphView<W>& g, i
 // One step of a local-moving iteration: the vertices of one colour class (deterministic) or of
 // one group of random classes (fast), as perm ranges per degree bucket, the giant range of the
 // class-ordered giant list, and (deterministic) the perm range the Sigma apply covers.
-constexpr int64_t kInFlightPerSm = 1024;  // vertices a local-moving launch holds per SM (4-lane groups)
-
 struct ClassStep {
   int64_t start[kNumBuckets] = {};
   int64_t count[kNumBuckets] = {};

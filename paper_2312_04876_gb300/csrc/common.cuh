@@ -11,6 +11,7 @@ namespace lv {
 constexpr int32_t kEmpty = -1;     // empty hash-table key
 constexpr int kBlock = 256;        // threads per block of the vertex-parallel kernels
 constexpr int kNumBuckets = 7;     // degree buckets of the per-vertex kernels
+constexpr int64_t kInFlightPerSm = 1024;  // vertices a local-moving launch holds per SM (4-lane groups)
 
 // Degree buckets: upper bound of the row length (arcs, self-loop included) handled by each.
 //   0: 1..4       groups of 4 lanes, 8-slot shared-memory table

@@ -1,8 +1,9 @@
 // serve.cu -- continuous-batching request loop over louvain_run_batch (host runtime).
 //
 // Requests (host CSRs) enter a FIFO queue.  Each of L lanes -- a worker thread with its own CUDA
-// stream, library handle and union buffers -- takes, whenever it is free, every queued request
-// that fits its limits and the server's device-memory budget, runs them as ONE batched call
+// stream, library handle and union buffers -- takes, whenever it is free, the oldest request and
+// every queued request of its class (weight type; inside or outside the in-flight window) that
+// fits its limits and the server's device-memory budget, runs them as ONE batched call
 // (batch.cu: every graph gets exactly its single-graph result), copies each membership back to
 // the caller's buffer and releases the memory.  Requests that arrive while lanes are busy wait
 // only for the next free lane and for memory; lanes run concurrently on the device, so their
@@ -43,6 +44,8 @@ struct Request {
   size_t est = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   int32_t batch_graphs = 0;
+  bool in_flight = false;  // the graph fits what the GPU holds in flight (fast mode's schedule class)
+  bool picked = false;     // taken into the batch being formed
   louvain_status status = LOUVAIN_OK;
   louvain_graph_result result{};
   bool done = false;
@@ -78,6 +81,7 @@ struct louvain_server_s {
   size_t budget = 0;
   int32_t max_graphs = 256;
   int64_t max_arcs = 0;
+  int64_t window = 0;  // vertices the GPU holds in flight (SMs x kInFlightPerSm)
   louvain_params p{};
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -192,23 +196,27 @@ void lane_main(louvain_server_s* S, int idx) {
       while (true) {
         if (S->stopping && S->queue.empty()) return;
         if (!S->queue.empty()) {
-          // the head request first (FIFO), then followers while they fit; the lane's caches grow
-          // to the largest dimensions they have served, which its need covers
+          // the head request first (FIFO), then the queued requests of its class -- weight type,
+          // and whether the graph fits what the GPU holds in flight, which decides fast mode's
+          // schedule for a batch by its mean graph -- in queue order while they fit; the lane's
+          // caches grow to the largest dimensions they have served, which its need covers
           const size_t others = S->reserved_total - L.reserved;
           int64_t n = 0, a = 0;
           for (Request* r : S->queue) {
             if ((int32_t)batch.size() >= S->max_graphs) break;
-            if (!batch.empty() && r->wtype != batch[0]->wtype) break;
+            if (!batch.empty() && (r->wtype != batch[0]->wtype || r->in_flight != batch[0]->in_flight)) continue;
             if (!batch.empty() && S->max_arcs > 0 && a + r->a > S->max_arcs) break;
             const size_t e = std::max(estimate_bytes(std::max(L.hn, n + r->n), std::max(L.ha, a + r->a)), L.reserved);
             if (others + e > S->budget) break;
             batch.push_back(r);
+            r->picked = true;
             n += r->n;
             a += r->a;
             need = e;
           }
           if (!batch.empty()) {
-            S->queue.erase(S->queue.begin(), S->queue.begin() + (long)batch.size());
+            S->queue.erase(std::remove_if(S->queue.begin(), S->queue.end(), [](const Request* r) { return r->picked; }),
+                           S->queue.end());
             S->reserved_total = others + need;
             L.reserved = need;
             L.hn = std::max(L.hn, n);
@@ -298,6 +306,13 @@ louvain_status louvain_serve_create(louvain_server* out, int device, size_t hbm_
   S->max_graphs = max_batch_graphs;
   S->max_arcs = max_batch_arcs;
   S->p = *p;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    delete S;
+    return LOUVAIN_ERR_CUDA;
+  }
+  S->window = (int64_t)sms * kInFlightPerSm;
   S->lanes.resize(lanes);
   for (Lane& L : S->lanes) {
     louvain_status st = louvain_create(&L.h, device, 0);
@@ -332,6 +347,7 @@ louvain_status louvain_serve_submit(louvain_server S, int64_t n, int64_t n_arcs,
   if (!r) return LOUVAIN_ERR_OOM;
   r->n = n; r->a = n_arcs; r->offs = h_offsets; r->tg = h_targets; r->w = h_weights; r->wtype = wtype;
   r->out = h_membership; r->est = est;
+  r->in_flight = n <= S->window;
   r->t_submit = now_ms();
   {
     std::lock_guard<std::mutex> lk(S->mu);

@@ -116,3 +116,28 @@ def test_fast_mode_serving_quality(cuda_ok):
         qs.append(q)
         refs.append(ref_q)
     assert np.mean(qs) >= np.mean(refs) - 0.005
+
+
+def test_batches_keep_fast_mode_schedule_classes_apart(cuda_ok):
+    """Fast mode decides its schedule for a batch by the batch's mean graph: colour-synchronous when
+    it fits what the GPU holds in flight, asynchronous waves otherwise.  The server batches a graph
+    larger than that window only with others of its kind, so the small graphs queued around it keep
+    their own schedule (and the 0.005 bar against the oracle) instead of the large graph's."""
+    import paper_2312_04876_gb300 as lv
+    small = request_mix()
+    big = gg.rmat(18, weights=gg.W_INT8, seed=3)
+    window = torch.cuda.get_device_properties(0).multi_processor_count * 1024
+    assert big.n > window and all(g.n <= window for g in small)
+    graphs = small[:6] + [big] + small[6:]
+    srv = lv.Server(0, hbm_budget_bytes=8 << 30, lanes=1, max_batch_graphs=64, mode="fast", validate=0)
+    tickets = [srv.submit(g.offsets, g.targets, g.weights) for g in graphs]
+    got = [srv.result(t) for t in tickets]
+    srv.close()
+    assert got[6][1]["batch_graphs"] == 1
+    assert all(info["batch_graphs"] <= len(small) for _, info in got)
+    for k, (g, (m, info)) in enumerate(zip(graphs, got)):
+        nc = info["n_communities"]
+        assert m.min() == 0 and m.max() == nc - 1 and len(np.unique(m)) == nc
+        ref_q = oracle_result(k if k < 6 else k - 1)[1] if k != 6 else \
+            oracle.louvain(g.offsets, g.targets, g.weights, oracle.default_params())[1]
+        assert info["modularity"] >= ref_q - 0.005, k

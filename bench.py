@@ -534,16 +534,20 @@ def block_serving(ctx, requests: int = 64, lanes: int = 4, budget_gb: float = 40
                         time.sleep(due - now)
                     tickets.append(srv.submit(g.offsets, g.targets, g.weights))
                 lat, qs, bs = [], [], []
+                parts = dict.fromkeys(("prep_ms", "upload_ms", "run_ms", "download_ms"), 0.0)
                 for t in tickets:
                     _, info = srv.result(t)
                     lat.append(info["latency_ms"])
                     qs.append(info["modularity"])
                     bs.append(info["batch_graphs"])
+                    for k in parts:  # a batch's times, shared by its graphs: summed once per batch
+                        parts[k] += info[k] / info["batch_graphs"]
                 span = time.perf_counter() - start
         finally:
             srv.close()
         return {"rate": rate, "graphs_per_second": R / span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(np.mean(bs)), "q": qs,
+                "span_ms": 1e3 * span, "batch_time_sums_ms": {k: round(v, 1) for k, v in parts.items()},
                 "clocks": clk.summary()}
 
     cap1 = run_stream(1, 1, 0.0)  # one-at-a-time capacity: everything at once, one lane, one graph a batch

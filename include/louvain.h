@@ -110,10 +110,11 @@ typedef struct {
                                     shared-memory tables of local moving and merging and the giant
                                     rows' global tables.  Integer-weight results do not depend on it
                                     (exact sums, ties by id); it trades probe length for memory */
-  int32_t fast_sync_small;       /* fast mode on small graphs: 0 = where the graph -- a batch: its mean
-                                    graph -- fits in what the GPU holds in flight (1024 vertices per
-                                    SM) and rows over 512 arcs hold at most a fifth of its arcs, run
-                                    the colour-synchronous schedule of the deterministic mode (each
+  int32_t fast_sync_small;       /* fast mode on small graphs: 0 = where the input graph -- a batch:
+                                    its mean graph -- fits in what the GPU holds in flight (1024
+                                    vertices per SM) and rows over 512 arcs hold at most a fifth of
+                                    its arcs, run every pass on the colour-synchronous schedule of
+                                    the deterministic mode, else every pass asynchronously (each
                                     class is one wave there anyway; asynchronous waves left 2-3% of
                                     small planted-partition graphs 0.03-0.066 below it; a graph
                                     carried by hubs needs hundreds of colours); 1 = asynchronous
@@ -298,6 +299,11 @@ typedef struct {
   double queue_ms;               /* submit -> its batch started */
   int32_t batch_graphs;          /* graphs in the batch it ran in */
   int32_t reserved;
+  /* where its batch's time went (the whole batch's, shared by the graphs in it): */
+  double prep_ms;                /* host: union offsets built from the requests' offsets */
+  double upload_ms;              /* device: the copies of the union CSR to the lane's buffers */
+  double run_ms;                 /* device: louvain_run_batch on the lane's stream */
+  double download_ms;            /* device: the memberships' copies to the callers' buffers */
 } louvain_serve_result;
 
 /* Start a server on `device` with the given parameters (mode, tolerances, seed ...).

@@ -131,7 +131,8 @@ class Server:
             raise LouvainError(r.status, f"request {ticket} failed")
         info = dict(modularity=r.result.modularity, passes=r.result.passes,
                     total_iterations=r.result.total_iterations, n_communities=r.result.n_communities,
-                    latency_ms=r.latency_ms, queue_ms=r.queue_ms, batch_graphs=r.batch_graphs)
+                    latency_ms=r.latency_ms, queue_ms=r.queue_ms, batch_graphs=r.batch_graphs,
+                    prep_ms=r.prep_ms, upload_ms=r.upload_ms, run_ms=r.run_ms, download_ms=r.download_ms)
         return out, info
 
     def result(self, ticket: int, timeout_s: float = 600.0):

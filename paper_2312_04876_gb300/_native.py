@@ -48,7 +48,8 @@ class GraphResult(ctypes.Structure):
 class ServeResult(ctypes.Structure):
     _fields_ = [("ready", ctypes.c_int32), ("status", ctypes.c_int32), ("result", GraphResult),
                 ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("batch_graphs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("prep_ms", ctypes.c_double), ("upload_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("download_ms", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):

@@ -798,21 +798,29 @@ louvain_status local_move_phase(louvain_handle h, Ctx& c, const GraphView<typena
   Segs seg;
   seg.vg = vg;
   seg.gc = gc;
-  // Fast mode on a graph that the GPU holds in flight (a batch: its mean graph) and whose rows over
-  // 512 arcs hold at most a fifth of its arcs runs the colour-synchronous schedule: there every
-  // class is one wave either way, and asynchronous waves left 2-3% of small planted-partition graphs
-  // 0.03-0.066 below the oracle (random classes and colour classes alike).  A graph carried by hubs
-  // needs hundreds of colours (a class step each; R-MAT scale 17: ~300), and asynchronous waves
-  // hold the bar there.
+  // Fast mode on an input graph that the GPU holds in flight (a batch: its mean graph) and whose
+  // rows over 512 arcs hold at most a fifth of its arcs runs the colour-synchronous schedule in
+  // every pass: there every class is one wave either way, and asynchronous waves left 2-3% of small
+  // planted-partition graphs 0.03-0.066 below the oracle (random classes and colour classes alike).
+  // A graph carried by hubs needs hundreds of colours (a class step each; R-MAT scale 17: ~300), and
+  // asynchronous waves hold the bar there.  The first phase of the call decides for all: the late
+  // super-vertex graphs of a large input are few vertices with long rows (SBM, 4.9M vertices: pass
+  // 5 has 108k vertices of 238 arcs), which colour-synchronous moves cost 62 colours a sweep.
   const int64_t n_eff = gc && n_graphs > 0 ? g.n / n_graphs : g.n;
   const int64_t window = (int64_t)c.num_sms * kInFlightPerSm;
   louvain_status s;
   bool det = p.mode == LOUVAIN_MODE_DETERMINISTIC || p.fast_sync_small == 2;
-  if (!det && p.fast_sync_small == 0 && n_eff <= window) {
-    hub_share(c, g, ws.ctrl);
-    const Ctrl* hs = read_ctrl(h, c, &s, "hub share");
-    if (!hs) return s;
-    det = hs->hub_arcs * 5 <= hs->all_arcs;
+  if (!det && p.fast_sync_small == 0) {
+    if (c.fast_sync < 0) {
+      c.fast_sync = 0;
+      if (n_eff <= window) {
+        hub_share(c, g, ws.ctrl);
+        const Ctrl* hs = read_ctrl(h, c, &s, "hub share");
+        if (!hs) return s;
+        c.fast_sync = hs->hub_arcs * 5 <= hs->all_arcs ? 1 : 0;
+      }
+    }
+    det = c.fast_sync == 1;
   }
   if (p.lm_blocks_per_sm > 0) c.lm_blocks_per_sm = p.lm_blocks_per_sm;
   std::vector<int64_t> ho;  // bucket-sort offsets: colour-major (deterministic) or bucket-major (fast)

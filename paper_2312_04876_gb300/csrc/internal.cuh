@@ -17,6 +17,8 @@ struct Ctx {
   int64_t giant_min = 4096;   // rows longer than this take the giant path (2048..4096)
   long long wait_spins = 0;   // polls of a bounded device wait before it gives up (0 = built-in)
   int table_factor = 2;       // hash-table slots per key of a table's distinct-key bound (1, 2, 4)
+  int fast_sync = -1;         // fast mode's schedule for this call, fixed by its first local-moving
+                              // phase: -1 undecided, 0 asynchronous waves, 1 colour-synchronous
 };
 
 inline int grid_for(int64_t work_items, int items_per_block, int cap) {

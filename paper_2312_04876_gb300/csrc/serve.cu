@@ -44,6 +44,7 @@ struct Request {
   size_t est = 0;
   double t_submit = 0, t_start = 0, t_done = 0;
   int32_t batch_graphs = 0;
+  double prep_ms = 0, upload_ms = 0, run_ms = 0, download_ms = 0;  // its batch's breakdown
   bool in_flight = false;  // the graph fits what the GPU holds in flight (fast mode's schedule class)
   bool picked = false;     // taken into the batch being formed
   louvain_status status = LOUVAIN_OK;
@@ -72,6 +73,9 @@ struct Lane {
   int32_t* d_w = nullptr;
   int32_t* d_mem = nullptr;
   size_t reserved = 0;
+  cudaEvent_t ev[4] = {};  // batch phase boundaries on the lane's stream
+  double prep_ms = 0;      // the last batch's host preparation and device phases
+  float up_ms = 0, run_ms = 0, down_ms = 0;
 };
 
 }  // namespace
@@ -123,7 +127,8 @@ bool lane_buffers(Lane& L, int64_t n, int64_t a) {
   return true;
 }
 
-void finish(louvain_server_s* S, std::vector<Request*>& batch, louvain_status st, const louvain_graph_result* res) {
+void finish(louvain_server_s* S, std::vector<Request*>& batch, louvain_status st, const louvain_graph_result* res,
+            const double times[4]) {
   const double t = now_ms();
   std::lock_guard<std::mutex> lk(S->mu);
   for (size_t k = 0; k < batch.size(); k++) {
@@ -132,6 +137,10 @@ void finish(louvain_server_s* S, std::vector<Request*>& batch, louvain_status st
     if (res) r->result = res[k];
     r->t_done = t;
     r->batch_graphs = (int32_t)batch.size();
+    r->prep_ms = times[0];
+    r->upload_ms = times[1];
+    r->run_ms = times[2];
+    r->download_ms = times[3];
     r->done = true;
   }
   S->cv_done.notify_all();
@@ -148,7 +157,10 @@ louvain_status run_lane_batch(louvain_server_s* S, Lane& L, std::vector<Request*
     a_tot += batch[k]->a;
   }
   const int64_t n = vo[G];
+  L.prep_ms = 0;
+  L.up_ms = L.run_ms = L.down_ms = 0;
   if (!lane_buffers(L, n, a_tot)) return LOUVAIN_ERR_OOM;
+  const double t0 = now_ms();
   // union offsets: each graph's offsets shifted by its arc base (built on the host)
   std::vector<int64_t> offs(n + 1);
   int64_t ab = 0;
@@ -158,6 +170,8 @@ louvain_status run_lane_batch(louvain_server_s* S, Lane& L, std::vector<Request*
     ab += r->a;
   }
   offs[n] = ab;
+  L.prep_ms = now_ms() - t0;
+  cudaEventRecord(L.ev[0], L.s);
   cudaMemcpyAsync(L.d_offs, offs.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, L.s);
   ab = 0;
   for (int32_t k = 0; k < G; k++) {
@@ -168,17 +182,26 @@ louvain_status run_lane_batch(louvain_server_s* S, Lane& L, std::vector<Request*
     }
     ab += r->a;
   }
+  cudaEventRecord(L.ev[1], L.s);
   res.assign(G, louvain_graph_result{});
   louvain_result tot;
   louvain_status st = louvain_run_batch(L.h, G, vo.data(), a_tot, L.d_offs, L.d_tg, L.d_w, batch[0]->wtype, &S->p,
                                         L.s, L.d_mem, res.data(), &tot);
   if (st != LOUVAIN_OK) return st;
+  cudaEventRecord(L.ev[2], L.s);
   for (int32_t k = 0; k < G; k++)
     if (batch[k]->n > 0)
       cudaMemcpyAsync(batch[k]->out, L.d_mem + vo[k], sizeof(int32_t) * batch[k]->n, cudaMemcpyDeviceToHost, L.s);
+  cudaEventRecord(L.ev[3], L.s);
   if (cudaStreamSynchronize(L.s) != cudaSuccess) {
     cudaGetLastError();
     return LOUVAIN_ERR_CUDA;
+  }
+  if (cudaEventElapsedTime(&L.up_ms, L.ev[0], L.ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&L.run_ms, L.ev[1], L.ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&L.down_ms, L.ev[2], L.ev[3]) != cudaSuccess) {
+    cudaGetLastError();
+    L.up_ms = L.run_ms = L.down_ms = 0;
   }
   return LOUVAIN_OK;
 }
@@ -270,7 +293,8 @@ void lane_main(louvain_server_s* S, int idx) {
       cudaStreamSynchronize(L.s);
       cudaGetLastError();
     }
-    finish(S, batch, st, st == LOUVAIN_OK ? res.data() : nullptr);
+    const double times[4] = {L.prep_ms, L.up_ms, L.run_ms, L.down_ms};
+    finish(S, batch, st, st == LOUVAIN_OK ? res.data() : nullptr, times);
     // keep the caches only while they fit the budget share of an idle lane
     const size_t held = handle_device_bytes(L.h) +
                         (L.cap_n >= 0 ? (size_t)(8 * (L.cap_n + 1) + 4 * (L.cap_n + 1) + 8 * L.cap_a) : 0);
@@ -320,8 +344,15 @@ louvain_status louvain_serve_create(louvain_server* out, int device, size_t hbm_
       cudaGetLastError();
       st = LOUVAIN_ERR_CUDA;
     }
+    for (int e = 0; e < 4 && st == LOUVAIN_OK; e++)
+      if (cudaEventCreate(&L.ev[e]) != cudaSuccess) {
+        cudaGetLastError();
+        st = LOUVAIN_ERR_CUDA;
+      }
     if (st != LOUVAIN_OK) {
       for (Lane& M : S->lanes) {
+        for (cudaEvent_t& e : M.ev)
+          if (e) cudaEventDestroy(e);
         if (M.s) cudaStreamDestroy(M.s);
         louvain_destroy(M.h);
       }
@@ -380,6 +411,10 @@ louvain_status louvain_serve_poll(louvain_server S, uint64_t ticket, int32_t wai
   out->latency_ms = r->t_done - r->t_submit;
   out->queue_ms = r->t_start - r->t_submit;
   out->batch_graphs = r->batch_graphs;
+  out->prep_ms = r->prep_ms;
+  out->upload_ms = r->upload_ms;
+  out->run_ms = r->run_ms;
+  out->download_ms = r->download_ms;
   S->reqs.erase(it);
   delete r;
   return LOUVAIN_OK;
@@ -397,6 +432,8 @@ void louvain_serve_destroy(louvain_server S) {
   cudaSetDevice(S->device);
   for (Lane& L : S->lanes) {
     lane_free_buffers(L);
+    for (cudaEvent_t& e : L.ev)
+      if (e) cudaEventDestroy(e);
     if (L.s) cudaStreamDestroy(L.s);
     louvain_destroy(L.h);
   }

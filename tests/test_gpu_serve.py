@@ -63,6 +63,10 @@ def test_same_alone_and_in_the_mix(cuda_ok, lanes, max_graphs):
         assert np.array_equal(m, m1)
         assert info["modularity"] == q1
         assert info["latency_ms"] >= info["queue_ms"] >= 0.0
+        # the batch's breakdown: host preparation and the device phases fit in its service time
+        parts = [info[k] for k in ("prep_ms", "upload_ms", "run_ms", "download_ms")]
+        assert min(parts) >= 0.0 and info["run_ms"] > 0.0
+        assert sum(parts) <= info["latency_ms"] - info["queue_ms"] + 1.0
         # and each served result is the CPU oracle's, bit for bit
         ref_mem, ref_q, ref_passes = oracle_result(k)
         assert np.array_equal(m, ref_mem), f"request {k}"

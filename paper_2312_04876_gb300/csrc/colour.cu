@@ -10,16 +10,18 @@
 // its degree, so larger colours need no bit).  A round takes the ready list (cnt = 0): each vertex
 // reads the first free bit of its bitmap as its colour, then pushes to every lower-priority
 // neighbour -- sets the colour's bit and decrements the counter, appending the neighbours that
-// reach zero to the next ready list.  The push of a vertex with more than kBigDeg arcs is spread
-// over the whole grid by a second kernel, so a chain of hubs (a dense core needs one round per
-// member) costs microseconds per round, not a warp's walk over 10^5 arcs.  The round index lives
-// on the device, so a batch of rounds is captured once as a CUDA graph and replayed until every
-// vertex is coloured; a round with an empty ready list returns at once.
+// reach zero to the next ready list.  The push of a vertex with more than kBigDeg arcs (in a busy
+// round, kBigDegBusy) is spread over the whole grid by a second kernel, so a chain of hubs (a dense
+// core needs one round per member) costs microseconds per round, not a warp's walk over 10^5
+// arcs.  The round index lives on the device, so a batch of rounds is captured once as a CUDA
+// graph and replayed until every vertex is coloured; a round with an empty ready list returns at
+// once.
 #include "internal.cuh"
 
 namespace lv {
 
-constexpr int64_t kBigDeg = 32;    // pushes of longer rows are spread over the grid in chunks
+constexpr int64_t kBigDeg = 32;       // pushes of longer rows are spread over the grid in chunks,
+constexpr int64_t kBigDegBusy = 256;  // in a round with a ready vertex per warp: of rows over this
 constexpr int64_t kPushChunk = kBlock;  // arcs per chunk (one per thread of a block)
 constexpr int kRoundsPerGraph = 16;
 
@@ -83,7 +85,9 @@ __global__ void __launch_bounds__(kBlock) jp_count(JpArgs a, const int32_t* list
 }
 
 // Push of the colour c of v along arc e: the neighbour u of lower priority records c and, when its
-// last higher-priority neighbour is done, joins the next ready list.
+// last higher-priority neighbour is done, joins the next ready list.  (The uncoloured neighbours of
+// a ready vertex are exactly those of lower priority, but reading u's colour to tell them apart
+// measured slower than hashing u's priority.)
 __device__ __forceinline__ void jp_push(const JpArgs& a, int32_t v, uint64_t pv, int32_t c, int32_t u, int32_t* out,
                                         unsigned long long* next_count) {
   if (u == v || !higher(pv, v, prio(a, u), u)) return;
@@ -111,6 +115,10 @@ __device__ __forceinline__ void jp_round_body(const JpArgs& a, unsigned long lon
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
+  // a round with few ready vertices spreads every push of more than a warp's width over the grid
+  // (its time is the longest push); a busy round keeps rows up to kBigDegBusy on their warp, where
+  // one 256-arc chunk per block would leave most of a block idle on a 40-arc row
+  const int64_t big_deg = (int64_t)count >= nw ? kBigDegBusy : kBigDeg;
   for (int64_t k = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); k < (int64_t)count; k += nw) {
     const int32_t v = in[k];
     // guard: a ready vertex is uncoloured; anything else is recorded and skipped
@@ -142,7 +150,7 @@ __device__ __forceinline__ void jp_round_body(const JpArgs& a, unsigned long lon
       atomicAdd(done_blk, 1ULL);
       atomicMax(max_blk, col + 1);
     }
-    if (end - beg > kBigDeg) {
+    if (end - beg > big_deg) {
       // spread the push: the vertex joins the big list and reserves its chunks of kPushChunk arcs
       const int64_t nch = (end - beg + kPushChunk - 1) / kPushChunk;
       unsigned long long pos = 0, cb = 0;

@@ -398,9 +398,9 @@ louvain_status louvain_exclusive_scan(louvain_handle h, const int64_t* d_in, int
  * d_out[0, count) = exclusive prefix sums of d_in[0, count) (int64, device), d_out[count] = total,
  * d_in == d_out allowed, *total (host, optional).  count must not exceed 2^26 (67,108,864) elements,
  * else LOUVAIN_ERR_INVALID.  The scratch is a 128 KiB __device__ array in the library that every GPU
- * loading the library keeps until the process exits; the call allocates and frees nothing.  Its
- * address is looked up on the first call on each device, so make that first call before any stream
- * capture.  All calls on a device share the one scratch array: calls that overlap on the GPU (other
+ * loading the library keeps until the process exits; the call allocates and frees nothing (its
+ * address is looked up on the first call on each device).  All calls on a device share the one
+ * scratch array: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.  Synchronises `stream`
  * before returning.  LOUVAIN_ERR_CUDA on a CUDA failure. */
 louvain_status louvain_exclusive_scan_static(const int64_t* d_in, int64_t* d_out, int64_t count, void* stream,

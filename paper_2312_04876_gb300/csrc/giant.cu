@@ -10,7 +10,11 @@
 //           pass at once (the giants listed class by class), so it is built once per pass; each
 //           iteration of a class only decides which of its giants are active (pruning flags);
 //   insert  grid-stride over chunks of 512 arcs (local move) or 2048 arcs (merge): K_i->c into the
-//           giant's global table with L2 atomics, K_i->d in registers (scanCommunities);
+//           giant's global table with L2 atomics, K_i->d in registers (scanCommunities).  The
+//           local-moving steps of a pass run one after another and each leaves its tables empty,
+//           so every step lays its giants' tables out from the start of the pool: a step of one
+//           class touches a few tens of MB that stay in L2 from step to step, not a fresh region
+//           of a pool sized for the whole pass;
 //   scan    one warp per range of 1024 table slots, one word of the pool's occupancy bitmap per
 //           lane (an insert that claims a slot sets its bit), so only occupied slots are read:
 //           local move scores every candidate with the Eq. 2 numerator and keeps the range's best;
@@ -295,7 +299,8 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
     if (!p.active[k]) continue;  // uniform over the block
     const int32_t i = list[k];
     const int32_t d = Cp[i];
-    const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
+    const int64_t ts = p.tab_off[k + 1] - p.tab_off[k];
+    const int64_t off = p.tab_off[k] - p.tab_off[k0];  // the step's tables from the pool's start
     int lg = 0;
     while (((int64_t)1 << lg) < ts) lg++;
     int32_t* kv = p.slots + 2 * off;
@@ -349,7 +354,8 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
     if (!p.active[k]) continue;  // uniform over the warp
     const int32_t i = list[k];
     const int32_t d = Cp[i];
-    const int64_t off = p.tab_off[k], ts = p.tab_off[k + 1] - off;
+    const int64_t ts = p.tab_off[k + 1] - p.tab_off[k];
+    const int64_t off = p.tab_off[k] - p.tab_off[k0];  // as the insert placed them
     const H kid = reinterpret_cast<const H*>(p.kid)[k];
     const A ki = K[i], sd = Sig[d];
     const A two_m = gc ? (M::is_fp ? (A)gc[vg[i]].two_m_f : (A)gc[vg[i]].two_m_i) : two_m_all;

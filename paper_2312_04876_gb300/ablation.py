@@ -99,7 +99,8 @@ def markdown(results: dict, mode: str, command: str) -> str:
     wls = list(results)
     out = [f"# Parameter study, {mode} mode", "", "Command:", "", "```", command, "```", "",
            "Runtime relative to the defaults (geometric mean over workloads) and modularity relative to the "
-           "defaults (arithmetic mean); per workload the median ms and the mean Q.", "",
+           "defaults (arithmetic mean); per workload the median ms and the mean Q.  The defaults are measured "
+           "before and after the other settings and the faster median is the reference.", "",
            "| setting | rel. runtime | rel. modularity | " + " | ".join(f"{w} ms | {w} Q" for w in wls) + " |",
            "|---|---:|---:|" + "---:|---:|" * len(wls)]
     for lab, rt, rq in rows:
@@ -112,10 +113,16 @@ def markdown(results: dict, mode: str, command: str) -> str:
 
 
 def study(graphs: dict, make_timed_run, reps: int) -> dict:
-    """graphs[name] = device CSR; make_timed_run(graph, overrides) -> timed_run for measure()."""
+    """graphs[name] = device CSR; make_timed_run(graph, overrides) -> timed_run for measure().
+    The defaults are measured first and again after the other settings; the faster of the two
+    medians is the reference (a one-off stall of the host or the box in the first calls of a
+    process once put the defaults 7x above every other setting of a workload)."""
     results = {}
     for wl, graph in graphs.items():
         results[wl] = {lab: measure(make_timed_run(graph, ov), reps) for lab, ov in settings()}
+        again = measure(make_timed_run(graph, {}), reps)
+        if again["ms"] < results[wl]["defaults"]["ms"]:
+            results[wl]["defaults"] = again
     return results
 
 

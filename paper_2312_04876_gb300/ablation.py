@@ -45,11 +45,20 @@ ALTERNATIVES = [
     ("table_factor", 1), ("table_factor", 4),
 ]
 
+def _rmat27_fp32():
+    """R-MAT 27 with fp32 weights (134M vertices, 4.2B arcs), drawn on the device: (offsets,
+    targets, weights) as CUDA tensors."""
+    from graphgen import device
+    return device.rmat(27, 16, 0.57, 0.19, 0.19, 22, fp_weights=True)
+
+
 WORKLOADS = {
     "sbm10k": lambda gg: gg.sbm(10000, 100, 0.1, 0.0005, 1),
     "rmat20": lambda gg: gg.rmat(20, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "rmat22": lambda gg: gg.rmat(22, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "grid6m": lambda gg: gg.grid(2449, 2449, 0.10, 0.01, 3),
+    "grid24m": lambda gg: gg.grid(4899, 4899, 0.10, 0.01, 3),
+    "rmat27_fp32": lambda gg: _rmat27_fp32(),
 }
 
 
@@ -84,13 +93,15 @@ def summarise(results: dict) -> list:
     for lab in labels:
         tr, qr = [], []
         for wl, per in results.items():
-            if lab not in per or "defaults" not in per:
+            if lab not in per or "defaults" not in per or "error" in per[lab] or "error" in per["defaults"]:
                 continue
             base = per["defaults"]
             tr.append(per[lab]["ms"] / base["ms"])
             qr.append(per[lab]["q"] / base["q"] if base["q"] != 0 else float("nan"))
         if tr:
             rows.append((lab, math.exp(statistics.fmean(math.log(x) for x in tr)), statistics.fmean(qr)))
+        else:  # failed on every workload: listed, with no ratios
+            rows.append((lab, float("nan"), float("nan")))
     return rows
 
 
@@ -107,7 +118,10 @@ def markdown(results: dict, mode: str, command: str) -> str:
         cells = []
         for w in wls:
             m = results[w].get(lab)
-            cells += [f"{m['ms']:.2f}", f"{m['q']:.5f}"] if m else ["", ""]
+            if m and "error" in m:
+                cells += ["failed", ""]
+            else:
+                cells += [f"{m['ms']:.2f}", f"{m['q']:.5f}"] if m else ["", ""]
         out.append(f"| {lab} | {rt:.3f} | {rq:.4f} | " + " | ".join(cells) + " |")
     return "\n".join(out) + "\n"
 
@@ -117,11 +131,18 @@ def study(graphs: dict, make_timed_run, reps: int) -> dict:
     The defaults are measured first and again after the other settings; the faster of the two
     medians is the reference (a one-off stall of the host or the box in the first calls of a
     process once put the defaults 7x above every other setting of a workload)."""
+    def attempt(graph, ov):
+        try:
+            return measure(make_timed_run(graph, ov), reps)
+        except Exception as e:  # a setting the library refuses (e.g. a table that overflows): recorded
+            return {"ms": float("nan"), "q": float("nan"), "passes": float("nan"), "iterations": float("nan"),
+                    "reps": 0, "error": f"{type(e).__name__}: {e}"[:160]}
+
     results = {}
     for wl, graph in graphs.items():
-        results[wl] = {lab: measure(make_timed_run(graph, ov), reps) for lab, ov in settings()}
-        again = measure(make_timed_run(graph, {}), reps)
-        if again["ms"] < results[wl]["defaults"]["ms"]:
+        results[wl] = {lab: attempt(graph, ov) for lab, ov in settings()}
+        again = attempt(graph, {})
+        if "error" in results[wl]["defaults"] or again["ms"] < results[wl]["defaults"]["ms"]:
             results[wl]["defaults"] = again
     return results
 
@@ -155,18 +176,23 @@ def main(argv=None) -> int:
     import graphgen as gg
 
     import paper_2312_04876_gb300 as lv
-    L = lv.Louvain(0)
     stream = torch.cuda.current_stream()
-    graphs = {}
-    for wl in a.workloads:
+    results = {}
+    for wl in a.workloads:  # one workload at a time, with its own handle
         g = WORKLOADS[wl](gg)
-        graphs[wl] = tuple(torch.from_numpy(x).cuda() for x in (g.offsets, g.targets, g.weights))
+        graph = g if isinstance(g, tuple) else tuple(torch.from_numpy(x).cuda() for x in (g.offsets, g.targets, g.weights))
+        del g
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()  # a device generator's scratch goes back before the runs
+        L = lv.Louvain(0)
 
-    def make(graph, ov):
-        return _cuda_timed_run(L, graph, lv.default_params(mode=a.mode, validate=0, **ov), stream)
+        def make(gr, ov, L=L):
+            return _cuda_timed_run(L, gr, lv.default_params(mode=a.mode, validate=0, **ov), stream)
 
-    results = study(graphs, make, a.reps)
-    L.close()
+        results.update(study({wl: graph}, make, a.reps))
+        L.close()
+        del graph
+        torch.cuda.empty_cache()
     command = "python -m paper_2312_04876_gb300.ablation " + " ".join(sys.argv[1:] if argv is None else argv)
     md = markdown(results, a.mode, command)
     if a.md:

@@ -24,11 +24,19 @@ PHASES = ("ms_colour", "ms_move", "ms_aggregate", "ms_other")
 PHASE_NAMES = {"ms_colour": "colouring", "ms_move": "local moving", "ms_aggregate": "aggregation",
                "ms_other": "other"}
 
+def _rmat27_fp32():
+    """R-MAT 27 with fp32 weights (134M vertices, 4.2B arcs), drawn on the device: (offsets,
+    targets, weights) as CUDA tensors."""
+    from graphgen import device
+    return device.rmat(27, 16, 0.57, 0.19, 0.19, 22, fp_weights=True)
+
+
 WORKLOADS = {
     "sbm10k": lambda gg: gg.sbm(10000, 100, 0.1, 0.0005, 1),
     "rmat20": lambda gg: gg.rmat(20, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "rmat22": lambda gg: gg.rmat(22, 16, 0.57, 0.19, 0.19, 22, gg.W_INT8),
     "grid24m": lambda gg: gg.grid(4899, 4899, 0.10, 0.01, 3),
+    "rmat27_fp32": lambda gg: _rmat27_fp32(),
 }
 
 
@@ -85,21 +93,27 @@ def main(argv=None) -> int:
     import graphgen as gg
 
     import paper_2312_04876_gb300 as lv
-    L = lv.Louvain(0)
     params = lv.default_params(mode=a.mode, validate=0)
     results = {}
     for wl in a.workloads:
         g = WORKLOADS[wl](gg)
-        o, t, w = (torch.from_numpy(x).cuda() for x in (g.offsets, g.targets, g.weights))
+        if isinstance(g, tuple):  # drawn on the device
+            o, t, w = g
+        else:
+            o, t, w = (torch.from_numpy(x).cuda() for x in (g.offsets, g.targets, g.weights))
+        del g
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()  # the generator's scratch goes back before the run sizes its workspace
+        L = lv.Louvain(0)  # a handle per workload: the previous one's workspace is released
 
         def run():
             _, r = L.run(o, t, w, params)
             return r.ms_total, r.stats
 
-        results[wl] = profile(run, g.n_arcs, a.reps)
+        results[wl] = profile(run, t.numel(), a.reps)
+        L.close()
         del o, t, w
         torch.cuda.empty_cache()
-    L.close()
     command = "python -m paper_2312_04876_gb300.phases " + " ".join(sys.argv[1:] if argv is None else argv)
     md = markdown(results, a.mode, command)
     if a.md:

@@ -92,3 +92,18 @@ def test_study_keeps_the_faster_of_the_two_default_measurements():
     assert res["g"]["defaults"]["ms"] == 10.0
     md = A.markdown(res, "fast", "cmd")
     assert "| max_iterations=100 | 1.000 |" in md
+
+
+def test_a_failing_setting_is_recorded_not_fatal():
+    def make(graph, ov):
+        def run():
+            if ov.get("table_factor") == 1:
+                raise RuntimeError("hash table overflow")
+            return 10.0, SimpleNamespace(modularity=0.4, passes=1, total_iterations=3)
+        return run
+
+    res = A.study({"g": "G"}, make, reps=1)
+    assert "error" in res["g"]["table_factor=1"] and "overflow" in res["g"]["table_factor=1"]["error"]
+    md = A.markdown(res, "fast", "cmd")
+    assert "| table_factor=1 | nan | nan | failed |" in md
+    assert "| max_iterations=100 | 1.000 |" in md

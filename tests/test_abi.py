@@ -92,3 +92,40 @@ def test_scan_wrappers_refuse_bad_tensors_before_any_library_call(monkeypatch):
                 torch.arange(20, dtype=torch.int64)[::2], [1, 2, 3]):
         with pytest.raises(ValueError):
             lv.exclusive_scan_static(bad)
+
+
+_STRUCTS = {"louvain_params": "Params", "louvain_pass_stats": "PassStats", "louvain_result": "Result",
+            "louvain_graph_result": "GraphResult", "louvain_serve_result": "ServeResult",
+            "louvain_kernel_stat": "KernelStat"}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct of include/louvain.h has the same size and field offsets in the ctypes binding as
+    a C compiler gives it (a field added on one side only would shift every later field)."""
+    import shutil
+    import subprocess
+    from paper_2312_04876_gb300 import _native
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include "louvain.h"', "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        st = getattr(_native, pyname)
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in st._fields_:
+            c_field = f[0][:-1] if f[0].endswith("_") else f[0]  # pass_ in Python is pass in C
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {c_field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr  # a field the binding names but the header lacks fails here
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], capture_output=True,
+                                                             text=True).stdout.splitlines())
+    for cname, pyname in _STRUCTS.items():
+        st = getattr(_native, pyname)
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(st), cname
+        for f in st._fields_:
+            assert int(got[f"{cname} {f[0]}"]) == getattr(st, f[0]).offset, (cname, f[0])

@@ -129,3 +129,24 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert int(got[f"{cname} size"]) == ctypes.sizeof(st), cname
         for f in st._fields_:
             assert int(got[f"{cname} {f[0]}"]) == getattr(st, f[0]).offset, (cname, f[0])
+
+
+def _declared_arities():
+    src = open(os.path.join(ROOT, "include", "louvain.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    out = {}
+    for m in re.finditer(r"\b(louvain_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        args = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    """Each entry point takes as many arguments in the ctypes binding as the header declares (one
+    missing or extra argument would hand the library a shifted argument list)."""
+    from paper_2312_04876_gb300 import _native
+    arity = _declared_arities()
+    assert set(arity) == set(_native.SIGNATURES)
+    for name, (_, argtypes) in _native.SIGNATURES.items():
+        assert len(argtypes) == arity[name], name

@@ -279,6 +279,24 @@ __global__ void k_glm_activate(GraphView<W> g, const int32_t* list, int64_t k0, 
   }
 }
 
+// Where a giant's activity comes from: fast mode snapshots it in k_glm_activate (a neighbour in the
+// same random class may re-mark the giant while its step runs); the deterministic mode reads it
+// from the flags directly in every kernel of the step -- a colour class is an independent set, so
+// nothing marks one of its giants during the step -- and its decide kernel then does what the
+// activation did (clears the flag, resets K_i->d, sets the moved mark, counts), one launch fewer.
+struct GiantAct {
+  int snap = 1;                  // 1: p.active (fast); 0: read below (deterministic)
+  int pruning = 0;
+  const uint8_t* flags = nullptr;
+  const GraphCtl* gc = nullptr;
+  const int32_t* vg = nullptr;
+};
+__device__ __forceinline__ bool giant_active(const GiantAct& ga, const GiantPlan& p, int64_t k, int32_t v) {
+  if (ga.snap) return p.active[k] != 0;
+  if (ga.gc && *(const volatile int32_t*)&ga.gc[ga.vg[v]].done) return false;
+  return !ga.pruning || ga.flags[v] != 0;
+}
+
 // ---------------------------------------------------------------- local move: insert
 
 // One block per chunk of an active giant; each thread loads its U arcs before their C'[j] gathers
@@ -286,7 +304,7 @@ __global__ void k_glm_activate(GraphView<W> g, const int32_t* list, int64_t k0, 
 template <class M>
 __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t> g, const int32_t* list, int64_t k0,
                                                        int64_t k1, const int32_t* Cp, GiantPlan p, Ctrl* ctrl,
-                                                       const int64_t* krng) {
+                                                       const int64_t* krng, GiantAct ga) {
   typedef typename M::h_t H;
   constexpr int U = kLmChunk / kBlock;  // 2
   __shared__ H red[32];
@@ -296,8 +314,8 @@ __global__ void __launch_bounds__(kBlock) k_glm_insert(GraphView<typename M::w_t
   bool ok = true;
   for (int64_t q = q0 + blockIdx.x; q < q1; q += gridDim.x) {
     const int64_t k = p.cowner[q];
-    if (!p.active[k]) continue;  // uniform over the block
     const int32_t i = list[k];
+    if (!giant_active(ga, p, k, i)) continue;  // uniform over the block
     const int32_t d = Cp[i];
     const int64_t ts = p.tab_off[k + 1] - p.tab_off[k];
     const int64_t off = p.tab_off[k] - p.tab_off[k0];  // the step's tables from the pool's start
@@ -338,7 +356,7 @@ template <class M>
 __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_t k0, int64_t k1, const int32_t* Cp,
                                                      const typename M::a_t* K, const typename M::a_t* Sig,
                                                      GiantPlan p, Ctrl* ctrl, const GraphCtl* gc, const int32_t* vg,
-                                                     const int64_t* krng) {
+                                                     const int64_t* krng, GiantAct ga) {
   typedef typename M::h_t H;
   typedef typename M::a_t A;
   typedef typename M::s_t S;
@@ -351,8 +369,8 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
   unsigned long long cand = 0;
   for (int64_t q = r0 + (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); q < r1; q += nwarps) {
     const int64_t k = p.sowner[q];
-    if (!p.active[k]) continue;  // uniform over the warp
     const int32_t i = list[k];
+    if (!giant_active(ga, p, k, i)) continue;  // uniform over the warp
     const int32_t d = Cp[i];
     const int64_t ts = p.tab_off[k + 1] - p.tab_off[k];
     const int64_t off = p.tab_off[k] - p.tab_off[k0];  // as the insert placed them
@@ -417,8 +435,9 @@ __global__ void __launch_bounds__(kBlock) k_glm_scan(const int32_t* list, int64_
 
 // ---------------------------------------------------------------- local move: decide (+ apply)
 template <class M>
-__global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int64_t k0, int64_t k1, PassState<M> st,
-                                                       GiantPlan p, int fast, const int64_t* krng) {
+__global__ void __launch_bounds__(kBlock) k_glm_decide(GraphView<typename M::w_t> g, const int32_t* list, int64_t k0,
+                                                       int64_t k1, PassState<M> st, GiantPlan p, int fast,
+                                                       const int64_t* krng, GiantAct ga) {
   typedef typename M::a_t A;
   typedef typename M::s_t S;
   Ctrl* ctrl = st.ctrl;
@@ -428,8 +447,22 @@ __global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int6
   double acc_f = 0.0;
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (kBlock / 32);
+  unsigned long long n_act = 0, n_arcs = 0;  // deterministic mode: the activation's counts
   for (int64_t k = k0 + (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); k < k1; k += nw) {
-    if (!p.active[k]) continue;
+    const int32_t iv = list[k];
+    // lane 0's reading for the whole warp, taken before lane 0 clears the flag below
+    const bool act = __shfl_sync(0xffffffffu, giant_active(ga, p, k, iv) ? 1 : 0, 0) != 0;
+    if (!ga.snap && lane == 0) {
+      // what k_glm_activate does in fast mode, now that every kernel of the step has read the flag
+      p.moved[k] = 0;
+      reinterpret_cast<uint32_t*>(p.kid)[k] = 0u;  // (scan has read it) for the next use of the plan
+      if (act) {
+        if (ga.pruning) st.flags[iv] = 0;
+        n_act++;
+        n_arcs += (unsigned long long)(g.rend[iv] - g.rbeg[iv]);
+      }
+    }
+    if (!act) continue;
     const int64_t q0 = p.slice_off[k], q1 = p.slice_off[k + 1];
     S best = M::lowest();
     int32_t bc = 0x7fffffff;
@@ -484,6 +517,18 @@ __global__ void __launch_bounds__(kBlock) k_glm_decide(const int32_t* list, int6
     if (M::is_fp) atomicAdd(&ctrl->sum_f, acc_f);
     else atomic_add_u128(&ctrl->sum_lo, &ctrl->sum_hi, acc_lo, acc_hi);
   }
+  if (!ga.snap) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      n_act += __shfl_xor_sync(0xffffffffu, n_act, o);
+      n_arcs += __shfl_xor_sync(0xffffffffu, n_arcs, o);
+    }
+    if (lane == 0) {
+      if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][0], (unsigned long long)(k1 - k0));
+      if (n_act) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][1], n_act);
+      if (n_arcs) atomicAdd(&ctrl->lm_stat[kNumBuckets - 1][2], n_arcs);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- local move: mark neighbours
@@ -531,12 +576,21 @@ void giant_move(Ctx& c, const GraphView<typename M::w_t>& g, const PassState<M>&
   // a device-resident range has no host count: the per-giant kernels take their cap
   const int ga = krng ? c.num_sms * 2 : grid_for(k1 - k0, kBlock, c.num_sms * 2);
   const int gd = krng ? c.num_sms * 2 : grid_for(k1 - k0, kBlock / 32, c.num_sms * 2);
-  k_glm_activate<typename M::w_t><<<ga, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, pruning ? 1 : 0, st.gc, st.vg, p,
-                                                          st.ctrl, krng);
-  k_glm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.Cp, p, st.ctrl, krng);
-  k_glm_scan<M><<<grid, kBlock, 0, c.s>>>(list, k0, k1, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg, krng);
-  k_glm_decide<M><<<gd, kBlock, 0, c.s>>>(list, k0, k1, st, p, fast ? 1 : 0, krng);
-  c.launches += 4;
+  GiantAct act;
+  act.snap = fast ? 1 : 0;
+  act.pruning = pruning ? 1 : 0;
+  act.flags = st.flags;
+  act.gc = st.gc;
+  act.vg = st.vg;
+  if (fast) {
+    k_glm_activate<typename M::w_t><<<ga, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, pruning ? 1 : 0, st.gc, st.vg,
+                                                            p, st.ctrl, krng);
+    c.launches++;
+  }
+  k_glm_insert<M><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.Cp, p, st.ctrl, krng, act);
+  k_glm_scan<M><<<grid, kBlock, 0, c.s>>>(list, k0, k1, st.Cp, st.K, st.Sig, p, st.ctrl, st.gc, st.vg, krng, act);
+  k_glm_decide<M><<<gd, kBlock, 0, c.s>>>(g, list, k0, k1, st, p, fast ? 1 : 0, krng, act);
+  c.launches += 3;
   if (pruning) {
     k_glm_mark<typename M::w_t><<<grid, kBlock, 0, c.s>>>(g, list, k0, k1, st.flags, p, st.ctrl, krng);
     c.launches++;

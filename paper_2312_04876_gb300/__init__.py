@@ -89,6 +89,9 @@ class Server:
         srv = Server(device=0, hbm_budget_bytes=40 << 30, lanes=4, mode="deterministic")
         t = srv.submit(offsets, targets, weights)        # numpy arrays, kept alive by the server object
         membership, info = srv.result(t)                 # waits; info: modularity, latency_ms, ...
+
+    info also carries where the request's batch spent its time (prep_ms on the host; upload_ms,
+    run_ms and download_ms on the device, shared by the batch's graphs).
     """
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 40 << 30, lanes: int = 4,

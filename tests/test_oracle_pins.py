@@ -442,6 +442,68 @@ _MUTANTS = {
 }
 
 
+# Plausible mistakes elsewhere in the method: each must fail at least one pin of this file.
+_METHOD_MUTANTS = {
+    # Eq. 2 without its K_i (Sigma_c - Sigma_d + K_i) correction: the K_i term dropped
+    "score_drops_ki_term": [("K[i] * (Sig[c] - Sig[d] + K[i]);", "K[i] * (Sig[c] - Sig[d]);")],
+    # scanCommunities with self = true in the local move: i's self-loop counted in K_i->d
+    "local_move_counts_own_loop": [("      if (j == i) continue;  // scanCommunities with self = false\n", "")],
+    # a self-loop counted twice in K_i (R1)
+    "loop_counted_twice_in_k": [("K[i] += g.w[e];", "K[i] += g.tg[e] == i ? 2 * g.w[e] : g.w[e];")],
+    # Eq. 1 with the null-model term added instead of subtracted
+    "modularity_sign": [("int64_t num = two_m * sigma_in - sq,", "int64_t num = two_m * sigma_in + sq,")],
+    # the super-graph loses its self-loops (intra-community arcs dropped)
+    "aggregate_drops_self_loops": [("H.add(Cp[g.tg[e]], g.w[e]);",
+                                    "if (Cp[g.tg[e]] != (int32_t)c) H.add(Cp[g.tg[e]], g.w[e]);")],
+    # the aggregation tolerance test reversed (R5)
+    "aggregation_tolerance_reversed": [("(double)nc / (double)gp.n > p.aggregation_tolerance",
+                                        "(double)nc / (double)gp.n < p.aggregation_tolerance")],
+    # no threshold scaling between passes
+    "no_threshold_scaling": [("tau /= p.tolerance_drop;", "tau *= 1.0;")],
+    # the greedy colouring taken in increasing priority
+    "colouring_in_increasing_priority": [("return a.first != b.first ? a.first > b.first : a.second > b.second;",
+                                          "return a.first != b.first ? a.first < b.first : a.second < b.second;")],
+}
+
+
+def _run_pins_against(tmp_path, mutants: dict, select: str) -> dict:
+    """Compile each mutated copy of the oracle (and an unchanged one), run the selected pins of
+    this file against it in a child process; returns {name: pytest exit code}."""
+    import os
+    import subprocess
+    import sys
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "louvain_oracle.cpp")).read()
+    builds = {}
+    for name, edits in list(mutants.items()) + [("unchanged", [])]:
+        text = src
+        for old, new in edits:
+            assert text.count(old) == 1, (name, old)
+            text = text.replace(old, new)
+        cpp = tmp_path / f"{name}.cpp"
+        cpp.write_text(text)
+        so = tmp_path / f"{name}.so"
+        builds[name] = (so, subprocess.Popen(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-o", str(so), str(cpp)]))
+    here = os.path.dirname(os.path.abspath(__file__))
+    codes = {}
+    for name, (so, proc) in builds.items():
+        assert proc.wait() == 0, name
+        env = dict(os.environ, LOUVAIN_ORACLE_SO=str(so))
+        r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                            os.path.join(here, "test_oracle_pins.py"), "-k", select],
+                           env=env, capture_output=True, text=True, cwd=os.path.dirname(here))
+        codes[name] = (r.returncode, r.stdout[-1500:])
+    return codes
+
+
+def test_pins_catch_planted_mistakes_in_the_method(tmp_path):
+    """Every planted mistake in Eq. 1, Eq. 2, R1, the aggregation, the pass loop or the colouring
+    fails at least one pin of this file; the unchanged source, built the same way, passes them all."""
+    codes = _run_pins_against(tmp_path, _METHOD_MUTANTS, "not planted")
+    assert codes["unchanged"][0] == 0, codes["unchanged"][1]
+    for name in _METHOD_MUTANTS:
+        assert codes[name][0] == 1, (name, codes[name][1])
+
+
 def test_hand_traced_pins_catch_planted_mistakes(tmp_path):
     """Every planted mistake in R2 / R3 fails at least one hand-traced pin, run in a child process
     against the mutated copy of the oracle (LOUVAIN_ORACLE_SO)."""

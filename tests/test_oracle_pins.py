@@ -463,6 +463,23 @@ _METHOD_MUTANTS = {
     # the greedy colouring taken in increasing priority
     "colouring_in_increasing_priority": [("return a.first != b.first ? a.first > b.first : a.second > b.second;",
                                           "return a.first != b.first ? a.first < b.first : a.second < b.second;")],
+    # the tolerance test strict (R4)
+    "tolerance_test_strict": [("return lhs <= tau * (t * t);", "return lhs < tau * (t * t);")],
+    # l_i counted from 0 (R4)
+    "iterations_zero_based": [("      li = it + 1;", "      li = it;")],
+    # the pass loop stopping at two iterations instead of one (Alg. 1)
+    "pass_loop_stops_at_two_iterations": [("if (li <= 1) break;", "if (li <= 2) break;")],
+    # renumbering by decreasing id instead of the rank among occupied ids (R6)
+    "renumber_reversed": [("for (int32_t& c : C) c = (int32_t)rank[c];",
+                           "for (int32_t& c : C) c = (int32_t)(r - 1 - rank[c]);")],
+    # the last pass's membership not looked up into the dendrogram (R6)
+    "last_lookup_skipped": [("  if (pending)\n    for (int64_t v = 0; v < n; v++) C[v] = Cp[C[v]];", "")],
+    # a processed vertex keeps its flag (pruning never clears)
+    "flag_never_cleared": [("            flag[v] = 0;\n            int32_t c; W ns;\n            if (decide(v, &c, &ns)) dec",
+                            "            int32_t c; W ns;\n            if (decide(v, &c, &ns)) dec")],
+    # a colour class applying each move at once instead of after the class (R3)
+    "class_moves_applied_at_once": [("            if (decide(v, &c, &ns)) dec.push_back({v, c, ns});",
+                                     "            if (decide(v, &c, &ns)) apply(v, c, ns, sum_n, p.pruning);")],
 }
 
 
@@ -496,9 +513,10 @@ def _run_pins_against(tmp_path, mutants: dict, select: str) -> dict:
 
 
 def test_pins_catch_planted_mistakes_in_the_method(tmp_path):
-    """Every planted mistake in Eq. 1, Eq. 2, R1, the aggregation, the pass loop or the colouring
-    fails at least one pin of this file; the unchanged source, built the same way, passes them all."""
-    codes = _run_pins_against(tmp_path, _METHOD_MUTANTS, "not planted")
+    """Every planted mistake in Eq. 1, Eq. 2, R1, R3-R6, the aggregation, the pass loop or the
+    colouring fails at least one pin of this file; the unchanged source, built the same way, passes
+    them all."""
+    codes = _run_pins_against(tmp_path, _METHOD_MUTANTS, "not catch_planted")
     assert codes["unchanged"][0] == 0, codes["unchanged"][1]
     for name in _METHOD_MUTANTS:
         assert codes[name][0] == 1, (name, codes[name][1])
